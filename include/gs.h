@@ -1,0 +1,247 @@
+/*
+ * gs.h -- C ABI of libgs, a GB300 (sm_103a) implementation of the
+ * differentiable tile-based Gaussian rasterizer described in
+ * "gsplat: An Open-Source Library for Gaussian Splatting" (arXiv 2409.06765),
+ * App. C (forward), App. D (backward), App. E (conventions), App. A
+ * (anti-aliasing, depth, absgrad).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array arguments are DEVICE pointers to contiguous, row-major data
+ *    (float32 / int32 / uint64) owned and allocated by the caller, except the
+ *    camera array, the parameter struct and `background`, which live in HOST
+ *    memory and are read during the call only.  The library never allocates
+ *    device memory and never synchronises the stream: every call enqueues
+ *    kernels on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ *    returns.  Device-side results (such as the intersection count) are valid
+ *    once the stream reaches them.
+ *  - Cameras: C cameras of possibly different sizes are rendered in one call.
+ *    Per-(camera, Gaussian) arrays are laid out [C, N, ...].  Per-pixel arrays
+ *    pack the cameras' images one after the other: camera c starts at pixel
+ *    sum_{c'<c} H_c' * W_c', then rows of W_c pixels (y-major), then channels.
+ *    Tiles are numbered globally: camera by camera, row-major within a camera.
+ *  - Errors: host-side validation (NULL pointers, sizes, unsupported options)
+ *    returns a negative gs_status and enqueues nothing.  A failed kernel launch
+ *    returns GS_ERR_CUDA; gs_last_error() then describes it (per thread).
+ *  - Gradient outputs of gs_rasterize_bwd are ACCUMULATED (+=) with atomics:
+ *    the caller zeroes them first.  The per-Gaussian backward helpers state
+ *    their own write/accumulate rule below.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+typedef int32_t gs_status;
+#define GS_OK 0
+#define GS_ERR_ARG -1         /* invalid argument (NULL pointer, size, option) */
+#define GS_ERR_CUDA -2        /* a CUDA launch or query failed; see gs_last_error() */
+#define GS_ERR_CAPACITY -3    /* a caller-provided buffer is too small */
+#define GS_ERR_UNSUPPORTED -5 /* option combination not compiled into this library */
+
+#define GS_MAX_CAMERAS 32     /* cameras per call */
+#define GS_MAX_CHANNELS 64    /* feature channels per Gaussian */
+
+/* Pinhole camera [App. C.1, App. E].  viewmat maps world to camera coordinates
+ * (x right, y down, z forward), row-major 4x4; its last row is ignored.  A camera
+ * point t projects to the continuous pixel position (fx tx/tz + cx, fy ty/tz + cy),
+ * pixel (i, j) having its centre at (i + 0.5, j + 0.5). */
+typedef struct gs_camera {
+    int32_t width, height;
+    float viewmat[16];
+    float fx, fy, cx, cy;
+} gs_camera;
+
+/* Rasterizer options.  gs_default_params() fills the values used throughout the
+ * paper's classic mode: 16x16 tiles [App. C.2], low-pass s = 0.3 [App. A],
+ * near plane 0.01, alpha in [1/255, 0.99], transmittance floor 1e-4. */
+typedef struct gs_params {
+    int32_t tile;         /* tile edge in pixels: 8, 16 or 32 */
+    int32_t batch_depth;  /* Gaussians staged in shared memory per batch: 32..256, multiple of 32 */
+    int32_t antialiased;  /* 0: classic mode; 1: opacity * sqrt(|S'| / |S' + sI|) [App. A] */
+    int32_t reserved;     /* must be 0 */
+    float eps2d;          /* low-pass s added to the 2D covariance [App. A] */
+    float near_plane;     /* a Gaussian is culled when its camera depth t_z < near_plane */
+    float alpha_min;      /* a (pixel, Gaussian) pair with alpha < alpha_min is skipped */
+    float alpha_max;      /* alpha = min(alpha_max, o * exp(-sigma)) */
+    float T_min;          /* a Gaussian that would bring T below T_min is excluded and ends the pixel */
+} gs_params;
+
+GS_API void gs_default_params(gs_params *params);
+
+/* Human-readable name of a status code (static storage). */
+GS_API const char *gs_status_string(gs_status status);
+
+/* Last CUDA error text recorded by a call of this thread ("" when none). */
+GS_API const char *gs_last_error(void);
+
+/* Number of tiles of C cameras at the given tile size (sum of ceil(W/t) ceil(H/t)). */
+GS_API int64_t gs_num_tiles(const gs_camera *cams, int32_t C, int32_t tile);
+
+/* Kernels this library has launched in this process so far (all threads, all devices):
+ * a counter the host increments at every launch, for accounting only. */
+GS_API uint64_t gs_kernel_launches(void);
+
+/* Number of pixels of C cameras (sum of W * H). */
+GS_API int64_t gs_num_pixels(const gs_camera *cams, int32_t C);
+
+/* ------------------------------------------------------------------------ */
+/* gs_project -- App. C.1 (projection, EWA splatting), App. E (quaternion,   */
+/* pixel coordinates), App. A (low-pass / anti-aliasing).                    */
+/*                                                                          */
+/* For each camera c and Gaussian n: s = exp(log_scales), o = sigmoid(logit),*/
+/* R = R(q/|q|), Sigma = R diag(s)^2 R^T, t = R_cw mu + t_cw (cull when      */
+/* t_z < near), mu' = (fx tx/tz + cx, fy ty/tz + cy), J the pinhole Jacobian */
+/* [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]], Sigma' = J R_cw Sigma */
+/* R_cw^T J^T + eps2d I, conic = Sigma'^-1, radius r = ceil(3 sqrt(lambda_max)),*/
+/* and the pixel box [ceil(mu'x - r - 0.5), floor(mu'x + r - 0.5)] x (same in */
+/* y) clipped to the image.  A Gaussian is invisible (radius 0, no tiles) if  */
+/* culled or if the box is empty.                                            */
+/*                                                                          */
+/* in : means [N,3], quats [N,4] (w,x,y,z, any norm > 0), log_scales [N,3],  */
+/*      opacity_logits [N]                                                   */
+/* out: means2d [C,N,2], depths [C,N] (= t_z), conics [C,N,3] (a,b,c of       */
+/*      [[a,b],[b,c]]), radii [C,N] int32, tiles_touched [C,N] int32 (tiles   */
+/*      containing a pixel of the box), opacities [C,N] (o, times the          */
+/*      anti-aliasing factor when enabled).  Entries of invisible Gaussians     */
+/*      are zero.                                                             */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_project(const gs_camera *cams, int32_t C, int32_t N, const float *means, const float *quats,
+                     const float *log_scales, const float *opacity_logits, const gs_params *params,
+                     float *means2d, float *depths, float *conics, int32_t *radii, int32_t *tiles_touched,
+                     float *opacities, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_sh_eval -- App. C.1: colour c = SH(dir), dir = (mu - centre)/|mu -     */
+/* centre|, centre = -R_cw^T t_cw.  Real spherical harmonics of degree <= 3,  */
+/* orthonormal, Condon-Shortley phase, coefficients ordered m = -l..l per l;  */
+/* colour = max(0, sum_k Y_k(dir) coeff_k + 0.5).                             */
+/*                                                                          */
+/* in : sh [N, (degree+1)^2, 3], means [N,3], radii [C,N] (colours of         */
+/*      invisible Gaussians are written as 0)                                 */
+/* out: colors [C,N,3]                                                       */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                     const float *means, const int32_t *radii, float *colors, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_tile_bin_sort -- App. C.2: bin every visible Gaussian into the tiles   */
+/* its pixel box touches and sort each tile's list by depth.                 */
+/*                                                                          */
+/* The result is the list of (tile, Gaussian) pairs in the order of the key  */
+/* (global_tile << 32) | float_bits(depth), ties broken by the flat index     */
+/* c*N + n.  The pixel box is recomputed here from means2d and radii with the */
+/* rule of gs_project (in float64 from the float32 inputs).                  */
+/*                                                                          */
+/* in : means2d [C,N,2], depths [C,N], radii [C,N]                           */
+/* out: values [K] int32 (flat index c*N + n), tile_ranges [T,2] int32        */
+/*      ([start, end) into values; (0,0) for an empty tile; T = gs_num_tiles),*/
+/*      keys [K] uint64 (optional, NULL to skip), K_out [1] int64 on the      */
+/*      device = the number of pairs K.  When K > K_capacity only the first   */
+/*      K_capacity slots are written, the lists are incomplete, and the       */
+/*      caller must reallocate (K_out tells by how much) and call again.      */
+/* workspace: device scratch of at least gs_tile_bin_sort_workspace() bytes,  */
+/*      256-byte aligned; its content on entry is ignored.                    */
+/* ------------------------------------------------------------------------ */
+GS_API int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                                   int64_t K_capacity);
+GS_API gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                           const float *means2d, const float *depths, const int32_t *radii, int64_t K_capacity,
+                           uint64_t *keys, int32_t *values, int32_t *tile_ranges, int64_t *K_out,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_rasterize_fwd -- App. C.2: for each pixel p (centre i+0.5, j+0.5) walk */
+/* its tile's sorted list front to back; a Gaussian counts at p only if p is */
+/* inside its pixel box; sigma = 1/2 D^T conic D with D = p - mu';           */
+/* alpha = min(alpha_max, o exp(-sigma)); pairs with sigma < 0 or alpha <     */
+/* alpha_min are skipped; if T (1 - alpha) < T_min the pixel stops without    */
+/* that Gaussian; otherwise C += c alpha T and T *= 1 - alpha.  Finally       */
+/* C += T * background.                                                      */
+/*                                                                          */
+/* in : tile_ranges, values (from gs_tile_bin_sort), radii [C,N],             */
+/*      means2d [C,N,2], conics [C,N,3], opacities [C,N], colors [C,N,ch],    */
+/*      background: host array of `channels` floats or NULL (zeros)          */
+/* out: image [pixels, channels], final_T [pixels] (alpha = 1 - final_T),     */
+/*      last_contrib [pixels] int32 = number of list entries of the pixel's   */
+/*      tile up to and including its last contributor (read by the backward),*/
+/*      blend_count (optional device int64, NULL to skip): += the number of   */
+/*      (pixel, Gaussian) pairs whose alpha was evaluated.                    */
+/* channels: 1..GS_MAX_CHANNELS; 1,2,3,4,8,16,32,64 use specialised kernels.  */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                           int32_t channels, const int32_t *tile_ranges, const int32_t *values,
+                           const int32_t *radii, const float *means2d, const float *conics, const float *opacities,
+                           const float *colors, const float *background, float *image, float *final_T,
+                           int32_t *last_contrib, int64_t *blend_count, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_rasterize_bwd -- App. D.1: replay each pixel back to front from its    */
+/* last contributor, recovering T_n = T_{n+1} / (1 - alpha_n) from final_T,  */
+/* and accumulate per (camera, Gaussian):                                    */
+/*   dL/dc_n     += alpha_n T_n dL/dC                                         */
+/*   dL/dalpha_n  = <dL/dC, c_n T_n - S_n/(1 - alpha_n)> + dL/dA T_N/(1-alpha_n),*/
+/*                  S_n = sum_{m>n} c_m alpha_m T_m + T_N background          */
+/*                  (0 where alpha was clamped to alpha_max)                  */
+/*   dL/do_n     += exp(-sigma) dL/dalpha_n                                   */
+/*   dL/dmu'_n   += -dL/dsigma conic D,  dL/dsigma = -o exp(-sigma) dL/dalpha */
+/*   dL/dconic_n += dL/dsigma (D_x^2/2, D_x D_y, D_y^2/2)  (for a, b, c)      */
+/*   absgrad_n   += (|per-pixel dL/dmu'_x|, |per-pixel dL/dmu'_y|) [App. A]    */
+/*                                                                          */
+/* in : as gs_rasterize_fwd plus final_T, last_contrib from it, d_image       */
+/*      [pixels, channels], d_alpha [pixels] or NULL                         */
+/* out (accumulated, caller zeroes): d_means2d [C,N,2], d_conics [C,N,3],     */
+/*      d_opacities [C,N], d_colors [C,N,channels], absgrad [C,N,2] or NULL   */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                           int32_t channels, const int32_t *tile_ranges, const int32_t *values,
+                           const int32_t *radii, const float *means2d, const float *conics, const float *opacities,
+                           const float *colors, const float *background, const float *final_T,
+                           const int32_t *last_contrib, const float *d_image, const float *d_alpha,
+                           float *d_means2d, float *d_conics, float *d_opacities, float *d_colors,
+                           float *absgrad, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_sh_eval_bwd -- backward of gs_sh_eval: d_sh[n] = sum_c Y(dir_c) *      */
+/* d_colors[c,n] (masked where the clamp at 0 was active), and the gradient  */
+/* through dir into the mean, d_means[n] = sum_c (I - dir dir^T)/|mu - centre|*/
+/* sum_k grad Y_k(dir) <coeff_k, d_colors>.  Both outputs are OVERWRITTEN for */
+/* every Gaussian (zeros where invisible in all cameras).                    */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                         const float *means, const int32_t *radii, const float *d_colors, float *d_sh,
+                         float *d_means, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_project_bwd -- App. D.2 / D.3 and the gradient-flow figure: from        */
+/* d_means2d, d_conics, d_opacities (and optional d_depths, for depth         */
+/* rendering) of every camera to the leaves: dSigma' = -Y dY Y,              */
+/* dSigma = T^T dSigma' T and dT = dSigma' T Sigma^T + dSigma'^T T Sigma      */
+/* (T = J R_cw), dJ -> dt, d mu = R_cw^T dt, dM = dSigma M + dSigma^T M,      */
+/* dR = dM S, dS = diag(R^T dM), dq through dR/dq and the normalisation,     */
+/* d log_scale = dS s, d logit = d o * o (1 - o).  Sums over the C cameras.   */
+/* d_means is ACCUMULATED (+=, so the SH term from gs_sh_eval_bwd adds up);   */
+/* d_quats, d_log_scales and d_opacity_logits are OVERWRITTEN.               */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const float *means, const float *quats,
+                         const float *log_scales, const float *opacity_logits, const gs_params *params,
+                         const int32_t *radii, const float *d_means2d, const float *d_conics,
+                         const float *d_opacities, const float *d_depths, float *d_means, float *d_quats,
+                         float *d_log_scales, float *d_opacity_logits, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -1,0 +1,354 @@
+// The extern "C" entry points declared in include/gs.h: argument validation, packing of
+// the host camera array into the by-value kernel parameter block, and dispatch.
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+cudaError_t launch_project_fwd(const CamSet &, const RasterConsts &, int, const float *, const float *, const float *,
+                               const float *, float *, float *, float *, int *, int *, float *, cudaStream_t);
+cudaError_t launch_project_bwd(const CamSet &, const RasterConsts &, int, const float *, const float *, const float *,
+                               const float *, const int *, const float *, const float *, const float *, const float *,
+                               float *, float *, float *, float *, cudaStream_t);
+cudaError_t launch_sh_fwd(const CamSet &, int, int, const float *, const float *, const int *, float *, cudaStream_t);
+cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *, const int *, const float *, float *,
+                          float *, cudaStream_t);
+BinSortLayout binsort_layout(long long CN, long long Kcap, int G);
+cudaError_t launch_binsort(const CamSet &, int, const float *, const float *, const int *, long long,
+                           unsigned long long *, int *, int *, long long *, void *, cudaStream_t);
+cudaError_t launch_raster_fwd(const CamSet &, const RasterConsts &, int, int, const int *, const int *, const int *,
+                              const float *, const float *, const float *, const float *, const float *, float *,
+                              float *, int *, unsigned long long *, cudaStream_t);
+cudaError_t launch_raster_bwd(const CamSet &, const RasterConsts &, int, int, const int *, const int *, const int *,
+                              const float *, const float *, const float *, const float *, const float *,
+                              const float *, const int *, const float *, const float *, float *, float *, float *,
+                              float *, float *, cudaStream_t);
+int raster_channel_capacity(int tile, int ch, bool restricted);
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// CTAs of the sort kernels: 4 per SM of the current device (cached per device).
+int sort_grid_blocks() {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4 * 148;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+        cache[dev] = 4 * sms;
+    }
+    return cache[dev];
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+static thread_local char g_last_error[512] = "";
+
+static gs_status fail_cuda(cudaError_t e, const char *where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return GS_ERR_CUDA;
+}
+
+static gs_status fail_arg(const char *what) {
+    snprintf(g_last_error, sizeof(g_last_error), "invalid argument: %s", what);
+    return GS_ERR_ARG;
+}
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static gs_status make_camset(const gs_camera *cams, int C, int tile, CamSet &cs) {
+    if (!cams) return fail_arg("cams is NULL");
+    if (C < 1 || C > GS_MAX_CAMERAS) return fail_arg("C must be in [1, GS_MAX_CAMERAS]");
+    if (tile != 8 && tile != 16 && tile != 32) return fail_arg("tile must be 8, 16 or 32");
+    memset(&cs, 0, sizeof(cs));
+    cs.C = C;
+    cs.tile = tile;
+    long long tiles = 0, pixels = 0;
+    for (int c = 0; c < C; ++c) {
+        const gs_camera &g = cams[c];
+        if (g.width < 1 || g.height < 1 || g.width > 32768 || g.height > 32768)
+            return fail_arg("camera width/height must be in [1, 32768]");
+        CamDev &d = cs.cam[c];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = g.viewmat[4 * i + j];
+            d.t[i] = g.viewmat[4 * i + 3];
+        }
+        d.fx = g.fx;
+        d.fy = g.fy;
+        d.cx = g.cx;
+        d.cy = g.cy;
+        d.W = g.width;
+        d.H = g.height;
+        d.tiles_x = (g.width + tile - 1) / tile;
+        d.tiles_y = (g.height + tile - 1) / tile;
+        d.tile_offset = (int)tiles;
+        d.pix_offset = (int)pixels;
+        tiles += (long long)d.tiles_x * d.tiles_y;
+        pixels += (long long)g.width * g.height;
+        if (tiles >= (1ll << 31) || pixels >= (1ll << 31)) return fail_arg("too many tiles or pixels in one call");
+    }
+    cs.total_tiles = (int)tiles;
+    cs.total_pixels = (int)pixels;
+    return GS_OK;
+}
+
+static gs_status check_params(const gs_params *p, RasterConsts &rc) {
+    if (!p) return fail_arg("params is NULL");
+    if (p->reserved != 0) return fail_arg("params.reserved must be 0");
+    if (p->batch_depth < 32 || p->batch_depth > 256 || (p->batch_depth % 32) != 0)
+        return fail_arg("batch_depth must be a multiple of 32 in [32, 256]");
+    if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return fail_arg("alpha_max must be in (0, 1)");
+    if (!(p->alpha_min >= 0.f && p->alpha_min <= p->alpha_max)) return fail_arg("alpha_min must be in [0, alpha_max]");
+    if (!(p->T_min > 0.f && p->T_min < 1.f)) return fail_arg("T_min must be in (0, 1)");
+    if (!(p->eps2d >= 0.f)) return fail_arg("eps2d must be >= 0");
+    if (!(p->near_plane > 0.f)) return fail_arg("near_plane must be > 0");
+    rc.eps2d = p->eps2d;
+    rc.near_plane = p->near_plane;
+    rc.alpha_min = p->alpha_min;
+    rc.alpha_max = p->alpha_max;
+    rc.T_min = p->T_min;
+    rc.antialiased = p->antialiased ? 1 : 0;
+    return GS_OK;
+}
+
+static gs_status check_cn(int C, int N) {
+    if (N < 0) return fail_arg("N must be >= 0");
+    if ((long long)C * N >= (1ll << 31)) return fail_arg("C * N must be < 2^31");
+    return GS_OK;
+}
+
+#define GS_TRY(x)                         \
+    do {                                  \
+        gs_status _s = (x);               \
+        if (_s != GS_OK) return _s;       \
+    } while (0)
+#define GS_NONNULL(p)                              \
+    do {                                           \
+        if (!(p)) return fail_arg(#p " is NULL");  \
+    } while (0)
+
+extern "C" {
+
+void gs_default_params(gs_params *p) {
+    if (!p) return;
+    p->tile = 16;
+    p->batch_depth = 256;
+    p->antialiased = 0;
+    p->reserved = 0;
+    p->eps2d = 0.3f;
+    p->near_plane = 0.01f;
+    p->alpha_min = 1.f / 255.f;
+    p->alpha_max = 0.99f;
+    p->T_min = 1e-4f;
+}
+
+const char *gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "GS_OK";
+        case GS_ERR_ARG: return "GS_ERR_ARG";
+        case GS_ERR_CUDA: return "GS_ERR_CUDA";
+        case GS_ERR_CAPACITY: return "GS_ERR_CAPACITY";
+        case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+        default: return "GS_ERR_UNKNOWN";
+    }
+}
+
+const char *gs_last_error(void) { return g_last_error; }
+
+uint64_t gs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t gs_num_tiles(const gs_camera *cams, int32_t C, int32_t tile) {
+    CamSet cs;
+    if (make_camset(cams, C, tile, cs) != GS_OK) return -1;
+    return cs.total_tiles;
+}
+
+int64_t gs_num_pixels(const gs_camera *cams, int32_t C) {
+    CamSet cs;
+    if (make_camset(cams, C, 16, cs) != GS_OK) return -1;
+    return cs.total_pixels;
+}
+
+gs_status gs_project(const gs_camera *cams, int32_t C, int32_t N, const float *means, const float *quats,
+                     const float *log_scales, const float *opacity_logits, const gs_params *params, float *means2d,
+                     float *depths, float *conics, int32_t *radii, int32_t *tiles_touched, float *opacities,
+                     void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (N == 0) return GS_OK;
+    GS_NONNULL(means); GS_NONNULL(quats); GS_NONNULL(log_scales); GS_NONNULL(opacity_logits);
+    GS_NONNULL(means2d); GS_NONNULL(depths); GS_NONNULL(conics); GS_NONNULL(radii); GS_NONNULL(tiles_touched);
+    GS_NONNULL(opacities);
+    if (!aligned(quats, 16)) return fail_arg("quats must be 16-byte aligned");
+    if (!aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
+    cudaError_t e = launch_project_fwd(cs, rc, N, means, quats, log_scales, opacity_logits, means2d, depths, conics,
+                                       radii, tiles_touched, opacities, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project");
+}
+
+gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                     const float *means, const int32_t *radii, float *colors, void *stream) {
+    CamSet cs;
+    GS_TRY(make_camset(cams, C, 16, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(colors);
+    cudaError_t e = launch_sh_fwd(cs, sh_degree, N, sh, means, radii, colors, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval");
+}
+
+int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                                   int64_t K_capacity) {
+    CamSet cs;
+    if (!params || make_camset(cams, C, params->tile, cs) != GS_OK) return -1;
+    if (N < 0 || K_capacity < 0 || K_capacity >= (1ll << 31) || (long long)C * N >= (1ll << 31)) return -1;
+    return (int64_t)binsort_layout((long long)C * N, K_capacity, sort_grid_blocks()).total;
+}
+
+gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                           const float *means2d, const float *depths, const int32_t *radii, int64_t K_capacity,
+                           uint64_t *keys, int32_t *values, int32_t *tile_ranges, int64_t *K_out, void *workspace,
+                           size_t workspace_bytes, void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (K_capacity < 0 || K_capacity >= (1ll << 31)) return fail_arg("K_capacity must be in [0, 2^31)");
+    GS_NONNULL(tile_ranges); GS_NONNULL(K_out); GS_NONNULL(workspace);
+    if (N > 0) {
+        GS_NONNULL(means2d); GS_NONNULL(depths); GS_NONNULL(radii);
+    }
+    if (K_capacity > 0) GS_NONNULL(values);
+    if (!aligned(workspace, 256)) return fail_arg("workspace must be 256-byte aligned");
+    if (N > 0 && !aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
+    if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
+    if (keys && !aligned(keys, 8)) return fail_arg("keys must be 8-byte aligned");
+    size_t need = binsort_layout((long long)C * N, K_capacity, sort_grid_blocks()).total;
+    if (workspace_bytes < need) {
+        snprintf(g_last_error, sizeof(g_last_error), "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+        return GS_ERR_CAPACITY;
+    }
+    cudaError_t e = launch_binsort(cs, N, means2d, depths, radii, K_capacity, (unsigned long long *)keys, values,
+                                   tile_ranges, (long long *)K_out, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_tile_bin_sort");
+}
+
+gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params, int32_t channels,
+                           const int32_t *tile_ranges, const int32_t *values, const int32_t *radii,
+                           const float *means2d, const float *conics, const float *opacities, const float *colors,
+                           const float *background, float *image, float *final_T, int32_t *last_contrib,
+                           int64_t *blend_count, void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (channels < 1 || channels > GS_MAX_CHANNELS) return fail_arg("channels must be in [1, GS_MAX_CHANNELS]");
+    if (raster_channel_capacity(params->tile, channels, blend_count != nullptr) == 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "no kernel for tile %d with %d channels%s", params->tile,
+                 channels, blend_count ? " and blend counting" : "");
+        return GS_ERR_UNSUPPORTED;
+    }
+    GS_NONNULL(tile_ranges); GS_NONNULL(image); GS_NONNULL(final_T); GS_NONNULL(last_contrib);
+    if (N > 0) {
+        GS_NONNULL(values); GS_NONNULL(radii); GS_NONNULL(means2d); GS_NONNULL(conics); GS_NONNULL(opacities);
+        GS_NONNULL(colors);
+        if (!aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
+    }
+    if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
+    if (blend_count && !aligned(blend_count, 8)) return fail_arg("blend_count must be 8-byte aligned");
+    cudaError_t e = launch_raster_fwd(cs, rc, channels, params->batch_depth, tile_ranges, values, radii, means2d,
+                                      conics, opacities, colors, background, image, final_T, last_contrib,
+                                      (unsigned long long *)blend_count, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_rasterize_fwd");
+}
+
+gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params, int32_t channels,
+                           const int32_t *tile_ranges, const int32_t *values, const int32_t *radii,
+                           const float *means2d, const float *conics, const float *opacities, const float *colors,
+                           const float *background, const float *final_T, const int32_t *last_contrib,
+                           const float *d_image, const float *d_alpha, float *d_means2d, float *d_conics,
+                           float *d_opacities, float *d_colors, float *absgrad, void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (channels < 1 || channels > GS_MAX_CHANNELS) return fail_arg("channels must be in [1, GS_MAX_CHANNELS]");
+    if (raster_channel_capacity(params->tile, channels, absgrad != nullptr) == 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "no backward kernel for tile %d with %d channels%s",
+                 params->tile, channels, absgrad ? " and absgrad" : "");
+        return GS_ERR_UNSUPPORTED;
+    }
+    if (N == 0) return GS_OK;
+    GS_NONNULL(tile_ranges); GS_NONNULL(values); GS_NONNULL(radii); GS_NONNULL(means2d); GS_NONNULL(conics);
+    GS_NONNULL(opacities); GS_NONNULL(colors); GS_NONNULL(final_T); GS_NONNULL(last_contrib); GS_NONNULL(d_image);
+    GS_NONNULL(d_means2d); GS_NONNULL(d_conics); GS_NONNULL(d_opacities); GS_NONNULL(d_colors);
+    if (!aligned(means2d, 8) || !aligned(d_means2d, 8)) return fail_arg("means2d/d_means2d must be 8-byte aligned");
+    if (absgrad && !aligned(absgrad, 8)) return fail_arg("absgrad must be 8-byte aligned");
+    if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
+    cudaError_t e = launch_raster_bwd(cs, rc, channels, params->batch_depth, tile_ranges, values, radii, means2d,
+                                      conics, opacities, colors, background, final_T, last_contrib, d_image, d_alpha,
+                                      d_means2d, d_conics, d_opacities, d_colors, absgrad, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_rasterize_bwd");
+}
+
+gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                         const float *means, const int32_t *radii, const float *d_colors, float *d_sh,
+                         float *d_means, void *stream) {
+    CamSet cs;
+    GS_TRY(make_camset(cams, C, 16, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(d_colors); GS_NONNULL(d_sh);
+    GS_NONNULL(d_means);
+    cudaError_t e = launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors, d_sh, d_means, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_bwd");
+}
+
+gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const float *means, const float *quats,
+                         const float *log_scales, const float *opacity_logits, const gs_params *params,
+                         const int32_t *radii, const float *d_means2d, const float *d_conics, const float *d_opacities,
+                         const float *d_depths, float *d_means, float *d_quats, float *d_log_scales,
+                         float *d_opacity_logits, void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (N == 0) return GS_OK;
+    GS_NONNULL(means); GS_NONNULL(quats); GS_NONNULL(log_scales); GS_NONNULL(opacity_logits); GS_NONNULL(radii);
+    GS_NONNULL(d_means2d); GS_NONNULL(d_conics); GS_NONNULL(d_opacities); GS_NONNULL(d_means); GS_NONNULL(d_quats);
+    GS_NONNULL(d_log_scales); GS_NONNULL(d_opacity_logits);
+    if (!aligned(quats, 16) || !aligned(d_quats, 16)) return fail_arg("quats/d_quats must be 16-byte aligned");
+    if (!aligned(d_means2d, 8)) return fail_arg("d_means2d must be 8-byte aligned");
+    cudaError_t e = launch_project_bwd(cs, rc, N, means, quats, log_scales, opacity_logits, radii, d_means2d, d_conics,
+                                       d_opacities, d_depths, d_means, d_quats, d_log_scales, d_opacity_logits,
+                                       (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project_bwd");
+}
+
+}  // extern "C"

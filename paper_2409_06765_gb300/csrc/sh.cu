@@ -1,0 +1,308 @@
+// View-dependent colour from real spherical harmonics (App. C.1: c = SH(dir)) and its
+// backward.  A CTA of 256 threads owns 256 consecutive Gaussians: their coefficients
+// ([256, K, 3] floats, contiguous in HBM) are copied with 16-byte loads into shared
+// memory at an odd row stride (no bank conflicts when each thread then reads its own
+// row), and every thread loops over the cameras of the call.
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Orthonormal real SH normalisation constants, from the closed form
+// K_l^m = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times sqrt(2) for m != 0, folded
+// with the Legendre polynomial coefficients.  Computed on the host in double.
+struct ShConsts {
+    float k0;                        // l = 0
+    float k1;                        // l = 1
+    float k2a, k2b, k2c;             // l = 2: m = +-1,-2 / 0 / 2
+    float k3a, k3b, k3c, k3d, k3e;   // l = 3: +-3 / -2 / +-1 / 0 / 2
+};
+
+static ShConsts make_sh_consts() {
+    const double pi = 3.14159265358979323846;
+    ShConsts k;
+    k.k0 = (float)(0.5 * sqrt(1.0 / pi));
+    k.k1 = (float)sqrt(3.0 / (4.0 * pi));
+    k.k2a = (float)(0.5 * sqrt(15.0 / pi));
+    k.k2b = (float)(0.25 * sqrt(5.0 / pi));
+    k.k2c = (float)(0.25 * sqrt(15.0 / pi));
+    k.k3a = (float)(0.25 * sqrt(35.0 / (2.0 * pi)));
+    k.k3b = (float)(0.5 * sqrt(105.0 / pi));
+    k.k3c = (float)(0.25 * sqrt(21.0 / (2.0 * pi)));
+    k.k3d = (float)(0.25 * sqrt(7.0 / pi));
+    k.k3e = (float)(0.25 * sqrt(105.0 / pi));
+    return k;
+}
+
+// Basis values, order m = -l..l within each degree (Condon-Shortley phase).
+template <int DEG>
+__device__ __forceinline__ void sh_eval_basis(const ShConsts &k, float x, float y, float z, float *Y) {
+    Y[0] = k.k0;
+    if (DEG >= 1) {
+        Y[1] = -k.k1 * y;
+        Y[2] = k.k1 * z;
+        Y[3] = -k.k1 * x;
+    }
+    if (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = k.k2a * x * y;
+        Y[5] = -k.k2a * y * z;
+        Y[6] = k.k2b * (2.f * zz - xx - yy);
+        Y[7] = -k.k2a * x * z;
+        Y[8] = k.k2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -k.k3a * y * (3.f * xx - yy);
+            Y[10] = k.k3b * x * y * z;
+            Y[11] = -k.k3c * y * (4.f * zz - xx - yy);
+            Y[12] = k.k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -k.k3c * x * (4.f * zz - xx - yy);
+            Y[14] = k.k3e * z * (xx - yy);
+            Y[15] = -k.k3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// Accumulates g[k] * grad_{x,y,z} Y_k into d (the basis is a polynomial in x, y, z).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_vjp(const ShConsts &k, float x, float y, float z, const float *g,
+                                             float d[3]) {
+    if (DEG >= 1) {
+        d[1] += -k.k1 * g[1];
+        d[2] += k.k1 * g[2];
+        d[0] += -k.k1 * g[3];
+    }
+    if (DEG >= 2) {
+        d[0] += k.k2a * y * g[4];
+        d[1] += k.k2a * x * g[4];
+        d[1] += -k.k2a * z * g[5];
+        d[2] += -k.k2a * y * g[5];
+        d[0] += -2.f * k.k2b * x * g[6];
+        d[1] += -2.f * k.k2b * y * g[6];
+        d[2] += 4.f * k.k2b * z * g[6];
+        d[0] += -k.k2a * z * g[7];
+        d[2] += -k.k2a * x * g[7];
+        d[0] += 2.f * k.k2c * x * g[8];
+        d[1] += -2.f * k.k2c * y * g[8];
+        if (DEG >= 3) {
+            float xx = x * x, yy = y * y, zz = z * z;
+            d[0] += -k.k3a * 6.f * x * y * g[9];
+            d[1] += -k.k3a * 3.f * (xx - yy) * g[9];
+            d[0] += k.k3b * y * z * g[10];
+            d[1] += k.k3b * x * z * g[10];
+            d[2] += k.k3b * x * y * g[10];
+            d[0] += k.k3c * 2.f * x * y * g[11];
+            d[1] += -k.k3c * (4.f * zz - xx - 3.f * yy) * g[11];
+            d[2] += -k.k3c * 8.f * y * z * g[11];
+            d[0] += -k.k3d * 6.f * x * z * g[12];
+            d[1] += -k.k3d * 6.f * y * z * g[12];
+            d[2] += k.k3d * (6.f * zz - 3.f * xx - 3.f * yy) * g[12];
+            d[0] += -k.k3c * (4.f * zz - 3.f * xx - yy) * g[13];
+            d[1] += k.k3c * 2.f * x * y * g[13];
+            d[2] += -k.k3c * 8.f * x * z * g[13];
+            d[0] += k.k3e * 2.f * x * z * g[14];
+            d[1] += -k.k3e * 2.f * y * z * g[14];
+            d[2] += k.k3e * (xx - yy) * g[14];
+            d[0] += -k.k3a * 3.f * (xx - yy) * g[15];
+            d[1] += k.k3a * 6.f * x * y * g[15];
+        }
+    }
+}
+
+// Copies the coefficient rows of Gaussians [n0, n0+cnt) into shared memory at row stride STRIDE.
+template <int F, int STRIDE>
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cnt, float *s, bool vec_ok) {
+    int total = cnt * F;
+    if (vec_ok) {
+        int nvec = total / 4;
+        const float4 *src4 = reinterpret_cast<const float4 *>(src);
+        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+            float4 q = src4[v];
+            int e = 4 * v;
+            s[(e / F) * STRIDE + e % F] = q.x;
+            ++e;
+            s[(e / F) * STRIDE + e % F] = q.y;
+            ++e;
+            s[(e / F) * STRIDE + e % F] = q.z;
+            ++e;
+            s[(e / F) * STRIDE + e % F] = q.w;
+        }
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += blockDim.x) s[(e / F) * STRIDE + e % F] = src[e];
+    } else {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) s[(e / F) * STRIDE + e % F] = src[e];
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restrict__ sh,
+                                                     const float *__restrict__ means, const int *__restrict__ radii,
+                                                     const __grid_constant__ CamSet cs, ShConsts kc,
+                                                     float *__restrict__ colors) {
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    extern __shared__ float s_coef[];
+    int n0 = blockIdx.x * 256;
+    int cnt = min(256, N - n0);
+    const float *src = sh + (size_t)n0 * F;
+    stage_rows<F, STRIDE>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    __syncthreads();
+    int n = n0 + threadIdx.x;
+    if (n >= N) return;
+    const float *cf = s_coef + threadIdx.x * STRIDE;
+    float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
+    for (int c = 0; c < cs.C; ++c) {
+        size_t idx = (size_t)c * N + n;
+        float *out = colors + 3 * idx;
+        if (radii[idx] <= 0) {
+            out[0] = 0.f;
+            out[1] = 0.f;
+            out[2] = 0.f;
+            continue;
+        }
+        const float *R = cs.cam[c].R, *t = cs.cam[c].t;
+        // camera centre = -R^T t
+        float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+        float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+        float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+        float vx = mx - ox, vy = my - oy, vz = mz - oz;
+        float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+        float Y[K];
+        sh_eval_basis<DEG>(kc, vx * il, vy * il, vz * il, Y);
+        float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            r += Y[k] * cf[3 * k];
+            g += Y[k] * cf[3 * k + 1];
+            b += Y[k] * cf[3 * k + 2];
+        }
+        out[0] = fmaxf(r, 0.f);
+        out[1] = fmaxf(g, 0.f);
+        out[2] = fmaxf(b, 0.f);
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) sh_bwd_kernel(int N, const float *__restrict__ sh,
+                                                     const float *__restrict__ means, const int *__restrict__ radii,
+                                                     const __grid_constant__ CamSet cs, ShConsts kc,
+                                                     const float *__restrict__ d_colors, float *__restrict__ d_sh,
+                                                     float *__restrict__ d_means) {
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    extern __shared__ float s_coef[];
+    int n0 = blockIdx.x * 256;
+    int cnt = min(256, N - n0);
+    const float *src = sh + (size_t)n0 * F;
+    stage_rows<F, STRIDE>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    __syncthreads();
+    int n = n0 + threadIdx.x;
+    float dc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) dc[f] = 0.f;
+    float dm[3] = {0.f, 0.f, 0.f};
+    if (n < N) {
+        const float *cf = s_coef + threadIdx.x * STRIDE;
+        float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
+        for (int c = 0; c < cs.C; ++c) {
+            size_t idx = (size_t)c * N + n;
+            if (radii[idx] <= 0) continue;
+            const float *R = cs.cam[c].R, *t = cs.cam[c].t;
+            float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+            float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+            float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+            float vx = mx - ox, vy = my - oy, vz = mz - oz;
+            float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+            float x = vx * il, y = vy * il, z = vz * il;
+            float Y[K];
+            sh_eval_basis<DEG>(kc, x, y, z, Y);
+            float g[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float raw = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) raw += Y[k] * cf[3 * k + ch];
+                g[ch] = raw > 0.f ? d_colors[3 * idx + ch] : 0.f;  // the clamp at 0 passes no gradient
+            }
+            float w[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                dc[3 * k] += Y[k] * g[0];
+                dc[3 * k + 1] += Y[k] * g[1];
+                dc[3 * k + 2] += Y[k] * g[2];
+                w[k] = cf[3 * k] * g[0] + cf[3 * k + 1] * g[1] + cf[3 * k + 2] * g[2];
+            }
+            if (DEG > 0) {
+                float dd[3] = {0.f, 0.f, 0.f};
+                sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
+                // dir = v / |v|:  d v = (I - dir dir^T) d dir / |v|
+                float p = x * dd[0] + y * dd[1] + z * dd[2];
+                dm[0] += (dd[0] - x * p) * il;
+                dm[1] += (dd[1] - y * p) * il;
+                dm[2] += (dd[2] - z * p) * il;
+            }
+        }
+        d_means[3 * n] = dm[0];
+        d_means[3 * n + 1] = dm[1];
+        d_means[3 * n + 2] = dm[2];
+    }
+    // write d_sh through shared memory so the global stores are contiguous
+    __syncthreads();
+    float *row = s_coef + threadIdx.x * STRIDE;
+#pragma unroll
+    for (int f = 0; f < F; ++f) row[f] = dc[f];
+    __syncthreads();
+    float *dst = d_sh + (size_t)n0 * F;
+    int total = cnt * F;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = s_coef[(e / F) * STRIDE + e % F];
+}
+
+template <int DEG>
+static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
+                                   float *colors, cudaStream_t st) {
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    size_t smem = 256 * STRIDE * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sh_fwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sh_fwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), colors);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int DEG>
+static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
+                                   const float *d_colors, float *d_sh, float *d_means, cudaStream_t st) {
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    size_t smem = 256 * STRIDE * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sh_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sh_bwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
+                                                            d_sh, d_means);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sh_fwd(const CamSet &cs, int deg, int N, const float *sh, const float *means, const int *radii,
+                          float *colors, cudaStream_t st) {
+    switch (deg) {
+        case 0: return launch_sh_fwd_t<0>(cs, N, sh, means, radii, colors, st);
+        case 1: return launch_sh_fwd_t<1>(cs, N, sh, means, radii, colors, st);
+        case 2: return launch_sh_fwd_t<2>(cs, N, sh, means, radii, colors, st);
+        default: return launch_sh_fwd_t<3>(cs, N, sh, means, radii, colors, st);
+    }
+}
+
+cudaError_t launch_sh_bwd(const CamSet &cs, int deg, int N, const float *sh, const float *means, const int *radii,
+                          const float *d_colors, float *d_sh, float *d_means, cudaStream_t st) {
+    switch (deg) {
+        case 0: return launch_sh_bwd_t<0>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
+        case 1: return launch_sh_bwd_t<1>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
+        case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
+        default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
+    }
+}
+
+}  // namespace gs

@@ -1,0 +1,223 @@
+"""Differentiable rasterization built on the libgs C ABI.
+
+``rasterization(...)`` mirrors the paper's user call (Design section, Fig. 1):
+Gaussians and C cameras in, images and alphas out, differentiable with respect to
+means, quaternions, log-scales, opacity logits and SH coefficients (or raw
+N-dimensional features).  Every stage runs in libgs kernels; PyTorch only provides
+the device buffers, the stream and autograd.
+
+Memory: the forward keeps, per pixel, only the final transmittance and the index of
+the last contributor (App. D.1 replays the compositing from them), so the saved
+state is O(pixels + Gaussians + intersections).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib
+
+__all__ = ["RasterSettings", "RasterState", "project", "sh_eval", "bin_sort", "rasterize_fwd", "forward_pass",
+           "rasterization", "RasterizeGaussians"]
+
+
+@dataclass
+class RasterSettings:
+    tile: int = 16
+    batch_depth: int = 256
+    antialiased: bool = False
+    eps2d: float = 0.3
+    near_plane: float = 0.01
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+    background: tuple | None = None
+    absgrad: bool = False
+
+    def params(self) -> _lib.GsParams:
+        return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
+                                self.alpha_min, self.alpha_max, self.T_min)
+
+
+@dataclass
+class RasterState:
+    """Reusable intersection buffers: grown (x1.25) when a frame needs more than they hold."""
+    capacity: int = 0
+    values: torch.Tensor | None = None
+    workspace: torch.Tensor | None = None
+    ws_key: tuple = field(default_factory=tuple)
+
+    def ensure(self, cams, N, params, K, device):
+        if K > self.capacity or self.values is None:
+            self.capacity = max(int(K * 1.25) + 1024, 1 << 16)
+            self.values = torch.empty(self.capacity, dtype=torch.int32, device=device)
+            self.ws_key = ()
+        key = (cams.C, N, self.capacity, params.tile)
+        if key != self.ws_key:
+            nbytes = _lib.gs_tile_bin_sort_workspace(cams, N, params, self.capacity)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self.ws_key = key
+
+
+def project(cams, means, quats, log_scales, opacity_logits, params):
+    C, N, dev = cams.C, means.shape[0], means.device
+    out = dict(means2d=torch.empty(C, N, 2, device=dev), depths=torch.empty(C, N, device=dev),
+               conics=torch.empty(C, N, 3, device=dev), radii=torch.empty(C, N, dtype=torch.int32, device=dev),
+               tiles_touched=torch.empty(C, N, dtype=torch.int32, device=dev),
+               opacities=torch.empty(C, N, device=dev))
+    _lib.gs_project(cams, means, quats, log_scales, opacity_logits, params, out["means2d"], out["depths"],
+                    out["conics"], out["radii"], out["tiles_touched"], out["opacities"])
+    return out
+
+
+def sh_eval(cams, sh_degree, sh, means, radii):
+    colors = torch.empty(cams.C, means.shape[0], 3, device=means.device)
+    _lib.gs_sh_eval(cams, sh_degree, sh, means, radii, colors)
+    return colors
+
+
+def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None = None, want_keys=False):
+    """Intersection list and tile ranges.  Reads K back to the host (one sync) to size the buffers."""
+    dev = means2d.device
+    state = state or RasterState()
+    if state.values is None:
+        state.ensure(cams, N, params, max(4 * cams.C * N, 1 << 16), dev)
+    else:
+        state.ensure(cams, N, params, 0, dev)
+    T = cams.num_tiles(params.tile)
+    ranges = torch.empty(T, 2, dtype=torch.int32, device=dev)
+    K_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        keys = torch.empty(state.capacity, dtype=torch.int64, device=dev) if want_keys else None
+        _lib.gs_tile_bin_sort(cams, N, params, means2d, depths, radii, state.capacity, keys, state.values, ranges,
+                              K_out, state.workspace)
+        K = int(K_out.item())
+        if K <= state.capacity:
+            break
+        state.ensure(cams, N, params, K, dev)
+    values = state.values[:K]
+    return dict(values=values, ranges=ranges, K=K, keys=None if keys is None else keys[:K])
+
+
+def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, conics, opacities, colors, background,
+                  count_blends=False):
+    dev = means2d.device
+    P = cams.num_pixels
+    image = torch.empty(P, channels, device=dev)
+    final_T = torch.empty(P, device=dev)
+    last = torch.empty(P, dtype=torch.int32, device=dev)
+    blends = torch.zeros(1, dtype=torch.int64, device=dev) if count_blends else None
+    if values.numel() == 0:
+        values = torch.empty(1, dtype=torch.int32, device=dev)
+    _lib.gs_rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, conics, opacities, colors,
+                          background, image, final_T, last, blends)
+    return image, final_T, last, blends
+
+
+def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_degree=0, features=None,
+                 settings: RasterSettings | None = None, state: RasterState | None = None, count_blends=False):
+    """Project, colour, bin/sort and composite.  Returns a dict of every intermediate."""
+    settings = settings or RasterSettings()
+    params = settings.params()
+    N = means.shape[0]
+    sp = project(cams, means, quats, log_scales, opacity_logits, params)
+    if features is None:
+        colors = sh_eval(cams, sh_degree, sh, means, sp["radii"])
+    else:
+        colors = features
+    ch = colors.shape[-1]
+    bs = bin_sort(cams, N, params, sp["means2d"], sp["depths"], sp["radii"], state)
+    image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
+                                                 sp["means2d"], sp["conics"], sp["opacities"], colors,
+                                                 settings.background, count_blends)
+    return dict(sp, colors=colors, values=bs["values"], ranges=bs["ranges"], K=bs["K"], image=image,
+                final_T=final_T, last_contrib=last, blends=blends, params=params)
+
+
+class RasterizeGaussians(torch.autograd.Function):
+    """image [P, ch], alpha [P] = f(means, quats, log_scales, opacity_logits, sh | features)."""
+
+    @staticmethod
+    def forward(ctx, means, quats, log_scales, opacity_logits, sh_or_features, cams, sh_degree, settings, state):
+        use_sh = sh_degree is not None
+        feats = None
+        if not use_sh:
+            f = sh_or_features
+            feats = (f.unsqueeze(0).expand(cams.C, *f.shape) if f.dim() == 2 else f).contiguous()
+        out = forward_pass(cams, means, quats, log_scales, opacity_logits, sh=sh_or_features if use_sh else None,
+                           sh_degree=sh_degree if use_sh else 0, features=feats, settings=settings, state=state)
+        ctx.cams, ctx.settings, ctx.sh_degree, ctx.use_sh = cams, settings, sh_degree, use_sh
+        ctx.feat_dim = None if use_sh else sh_or_features.dim()
+        ctx.save_for_backward(means, quats, log_scales, opacity_logits, sh_or_features, out["radii"], out["means2d"],
+                              out["conics"], out["opacities"], out["colors"], out["values"], out["ranges"],
+                              out["final_T"], out["last_contrib"])
+        ctx.mark_non_differentiable(out["radii"])
+        alpha = 1.0 - out["final_T"]
+        return out["image"], alpha, out["radii"]
+
+    @staticmethod
+    def backward(ctx, d_image, d_alpha, _d_radii):
+        (means, quats, log_scales, logits, shf, radii, means2d, conics, opac, colors, values, ranges, final_T,
+         last) = ctx.saved_tensors
+        cams, settings = ctx.cams, ctx.settings
+        params = settings.params()
+        C, N = cams.C, means.shape[0]
+        ch = colors.shape[-1]
+        dev = means.device
+        d_means2d = torch.zeros(C, N, 2, device=dev)
+        d_conics = torch.zeros(C, N, 3, device=dev)
+        d_opac = torch.zeros(C, N, device=dev)
+        d_colors = torch.zeros(C, N, ch, device=dev)
+        absgrad = torch.zeros(C, N, 2, device=dev) if settings.absgrad else None
+        d_image = d_image.contiguous() if d_image is not None else torch.zeros(cams.num_pixels, ch, device=dev)
+        d_alpha = d_alpha.contiguous() if d_alpha is not None else None
+        vals = values if values.numel() else torch.empty(1, dtype=torch.int32, device=dev)
+        _lib.gs_rasterize_bwd(cams, N, params, ch, ranges, vals, radii, means2d, conics, opac, colors,
+                              settings.background, final_T, last, d_image, d_alpha, d_means2d, d_conics, d_opac,
+                              d_colors, absgrad)
+        if absgrad is not None:
+            RasterizeGaussians.last_absgrad = absgrad
+        d_means = torch.empty(N, 3, device=dev)
+        if ctx.use_sh:
+            d_sh = torch.empty_like(shf)
+            _lib.gs_sh_eval_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means)
+            d_feat = d_sh
+        else:
+            d_means.zero_()
+            d_feat = d_colors.sum(0) if ctx.feat_dim == 2 else d_colors
+        d_quats = torch.empty(N, 4, device=dev)
+        d_log_scales = torch.empty(N, 3, device=dev)
+        d_logits = torch.empty(N, device=dev)
+        _lib.gs_project_bwd(cams, means, quats, log_scales, logits, params, radii, d_means2d, d_conics, d_opac, None,
+                            d_means, d_quats, d_log_scales, d_logits)
+        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None
+
+
+def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=None, *, features=None,
+                  sh_degree=None, settings: RasterSettings | None = None, state: RasterState | None = None):
+    """Render C cameras.  Returns (images, alphas, meta) with one [H, W, ch] / [H, W] tensor per camera.
+
+    Pass SH coefficients ``sh`` [N, K, 3] (degree inferred from K) or N-dimensional
+    ``features`` [N, D] / [C, N, D].  Parameters are the leaves of the paper's
+    gradient-flow figure: log-scales and opacity logits.
+    """
+    if cameras is None:
+        raise ValueError("cameras are required")
+    cams = cameras if isinstance(cameras, _lib.CameraArray) else _lib.CameraArray(cameras)
+    settings = settings or RasterSettings()
+    if features is None:
+        if sh is None:
+            raise ValueError("give sh or features")
+        K = sh.shape[1]
+        sh_degree = {1: 0, 4: 1, 9: 2, 16: 3}[K] if sh_degree is None else sh_degree
+        img, alpha, radii = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, sh, cams, sh_degree,
+                                                     settings, state)
+    else:
+        img, alpha, radii = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, features, cams, None,
+                                                     settings, state)
+    images, alphas = [], []
+    for (w, h), off in zip(cams.sizes, cams.pixel_offsets()):
+        images.append(img[off:off + w * h].view(h, w, -1))
+        alphas.append(alpha[off:off + w * h].view(h, w))
+    return images, alphas, dict(radii=radii, cameras=cams)

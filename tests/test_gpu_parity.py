@@ -1,0 +1,360 @@
+"""Parity of every CUDA stage with the FP64 oracle, through the C ABI, at sizes the oracle
+finishes in seconds (several tiles, ragged image edges, multiple cameras)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_06765_gb300 import _lib, raster, synth
+
+from gpu_helpers import (IMG_MEANABS, assert_grad_parity, assert_image_parity, dev_scene, flipped_pixels, gpu_grads,
+                         gpu_render, image_stats, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+
+def _mid_scene(n=20000, seed=7, deg=3):
+    sc = synth.clustered_scene(n, seed, sh_degree=deg, log_scale_mu=-3.2)
+    cam = synth.sphere_cameras(seed, [(203, 157)])[0]
+    return sc, cam
+
+
+# --------------------------------------------------------------------------- #
+# projection and SH                                                           #
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("aa", [False, True])
+def test_project_matches_oracle(aa):
+    sc, cam = _mid_scene()
+    out, _, _ = gpu_render(sc, [cam], settings=raster.RasterSettings(antialiased=aa))
+    ref = oracle.project(sc, cam, antialiased=aa)
+    r_gpu = out["radii"][0].cpu().numpy()
+    r_ref = ref["radii"]
+    both = (r_gpu > 0) & (r_ref > 0)
+    assert both.sum() > 0.5 * (r_ref > 0).sum()
+    mismatch = (r_gpu != r_ref)
+    assert mismatch.sum() <= max(2, 1e-3 * len(r_ref)), mismatch.sum()
+    assert np.abs(r_gpu[both] - r_ref[both]).max() <= 1
+    m = out["means2d"][0].cpu().numpy()[both]
+    np.testing.assert_allclose(m, ref["means2d"][both], atol=2e-3, rtol=0)
+    np.testing.assert_allclose(out["depths"][0].cpu().numpy()[both], ref["depths"][both], rtol=2e-6)
+    con = out["conics"][0].cpu().numpy()[both]
+    scale = np.abs(ref["conics"][both]).max(1, keepdims=True)
+    assert (np.abs(con - ref["conics"][both]) / scale).max() < 2e-4
+    # anti-aliased opacity carries sqrt(det(S')/det(S'+sI)): float32 cancellation in ac - b^2 scales its
+    # error by the condition number of S', so it gets a relative bar
+    np.testing.assert_allclose(out["opacities"][0].cpu().numpy()[both], ref["opacities"][both],
+                               atol=2e-6, rtol=5e-5 if aa else 0)
+    # tiles_touched agrees with the pixel box of the projected (float32) mean
+    tt = out["tiles_touched"][0].cpu().numpy()
+    assert (tt[r_gpu == 0] == 0).all() and (tt[r_gpu > 0] > 0).all()
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_sh_matches_oracle(deg):
+    sc, cam = _mid_scene(n=5000, seed=deg, deg=deg)
+    out, _, _ = gpu_render(sc, [cam])
+    col, _ = oracle.sh_colors(sc, cam)
+    vis = out["radii"][0].cpu().numpy() > 0
+    np.testing.assert_allclose(out["colors"][0].cpu().numpy()[vis], col[vis], atol=3e-6, rtol=1e-5)
+    assert (out["colors"][0].cpu().numpy()[~vis] == 0).all()
+
+
+# --------------------------------------------------------------------------- #
+# binning + sorting: bit-exact when fed the oracle's projection               #
+# --------------------------------------------------------------------------- #
+
+def _gpu_bin_sort(cams, means2d, depths, radii, tile, capacity=None):
+    ca = _lib.CameraArray(cams)
+    C, N = depths.shape
+    p = _lib.make_params(tile=tile)
+    dev = "cuda"
+    m = torch.as_tensor(np.ascontiguousarray(means2d, np.float32), device=dev)
+    d = torch.as_tensor(np.ascontiguousarray(depths, np.float32), device=dev)
+    r = torch.as_tensor(np.ascontiguousarray(radii, np.int32), device=dev)
+    Kcap = capacity if capacity is not None else int(32 * C * N + 1024)
+    keys = torch.empty(max(Kcap, 1), dtype=torch.int64, device=dev)
+    values = torch.empty(max(Kcap, 1), dtype=torch.int32, device=dev)
+    T = ca.num_tiles(tile)
+    ranges = torch.full((T, 2), -7, dtype=torch.int32, device=dev)
+    K_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(_lib.gs_tile_bin_sort_workspace(ca, N, p, Kcap), dtype=torch.uint8, device=dev)
+    _lib.gs_tile_bin_sort(ca, N, p, m, d, r, Kcap, keys, values, ranges, K_out, ws)
+    torch.cuda.synchronize()
+    K = int(K_out.item())
+    return K, keys[:min(K, Kcap)].cpu().numpy().view(np.uint64), values[:min(K, Kcap)].cpu().numpy(), \
+        ranges.cpu().numpy()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_sort_bit_exact_single_camera(tile):
+    sc, cam = _mid_scene(n=30000, seed=11)
+    ref = oracle.project(sc, cam)
+    m = ref["means2d"].astype(np.float32)[None]
+    d = ref["depths"].astype(np.float32)[None]
+    r = ref["radii"][None]
+    keys_r, vals_r, ranges_r = oracle.bin_sort(m, d, r, [cam.width], [cam.height], tile)
+    K, keys, vals, ranges = _gpu_bin_sort([cam], m, d, r, tile)
+    assert K == len(keys_r)
+    np.testing.assert_array_equal(keys, keys_r)
+    np.testing.assert_array_equal(vals, vals_r)
+    np.testing.assert_array_equal(ranges, ranges_r)
+
+
+def test_bin_sort_bit_exact_uneven_cameras_and_ties():
+    sc = synth.clustered_scene(8000, 3, sh_degree=0, log_scale_mu=-3.0)
+    cams = synth.sphere_cameras(5, [(97, 61), (160, 90), (33, 200)])
+    ms, ds, rs = [], [], []
+    for cam in cams:
+        p = oracle.project(sc, cam)
+        ms.append(p["means2d"])
+        ds.append(p["depths"])
+        rs.append(p["radii"])
+    m = np.stack(ms).astype(np.float32)
+    d = np.stack(ds).astype(np.float32)
+    d[:, ::7] = d[:, 3:4]  # exact depth ties inside tiles
+    r = np.stack(rs)
+    for tile in (8, 16):
+        keys_r, vals_r, ranges_r = oracle.bin_sort(m, d, r, [c.width for c in cams], [c.height for c in cams], tile)
+        K, keys, vals, ranges = _gpu_bin_sort(cams, m, d, r, tile)
+        assert K == len(keys_r)
+        np.testing.assert_array_equal(keys, keys_r)
+        np.testing.assert_array_equal(vals, vals_r)
+        np.testing.assert_array_equal(ranges, ranges_r)
+
+
+def test_bin_sort_capacity_overflow_reports_K_and_stays_in_bounds():
+    sc, cam = _mid_scene(n=5000, seed=12)
+    ref = oracle.project(sc, cam)
+    m, d, r = ref["means2d"].astype(np.float32)[None], ref["depths"].astype(np.float32)[None], ref["radii"][None]
+    keys_r, _, _ = oracle.bin_sort(m, d, r, [cam.width], [cam.height], 16)
+    K, _, _, _ = _gpu_bin_sort([cam], m, d, r, 16, capacity=len(keys_r) // 3)
+    assert K == len(keys_r)
+
+
+def test_bin_sort_empty_inputs():
+    cam = synth.make_camera(40, 30, (0, 0, 4))
+    K, _, _, ranges = _gpu_bin_sort([cam], np.zeros((1, 0, 2)), np.zeros((1, 0)), np.zeros((1, 0), np.int32), 16)
+    assert K == 0 and (ranges == 0).all()
+    # all Gaussians invisible
+    K, _, _, ranges = _gpu_bin_sort([cam], np.zeros((1, 50, 2)), np.ones((1, 50)), np.zeros((1, 50), np.int32), 16)
+    assert K == 0 and (ranges == 0).all()
+
+
+# --------------------------------------------------------------------------- #
+# forward image                                                                #
+# --------------------------------------------------------------------------- #
+
+def test_tiny_config_forward_matches_oracle():
+    sc, cam, _ = synth.tiny_scene()
+    out, _, _ = gpu_render(sc, [cam])
+    ref = oracle.render(sc, cam)
+    img = out["image"].cpu().numpy()
+    assert_image_parity(img, ref["image"].reshape(-1, 3))
+    assert_image_parity((1 - out["final_T"]).cpu().numpy()[:, None], ref["alpha"].reshape(-1, 1), "alpha")
+    assert ref["image"].max() > 0.3
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("batch", [64, 256])
+def test_clustered_forward_matches_oracle(tile, batch):
+    sc, cam = _mid_scene()
+    out, _, _ = gpu_render(sc, [cam], settings=raster.RasterSettings(tile=tile, batch_depth=batch))
+    ref = oracle.render(sc, cam)
+    assert_image_parity(out["image"].cpu().numpy(), ref["image"].reshape(-1, 3))
+    assert_image_parity((1 - out["final_T"]).cpu().numpy()[:, None], ref["alpha"].reshape(-1, 1), "alpha")
+
+
+def test_image_is_bit_identical_across_tile_sizes():
+    """The support rule is per pixel, so the tile size changes nothing but the schedule."""
+    sc, cam = _mid_scene(n=10000, seed=3)
+    imgs = [gpu_render(sc, [cam], settings=raster.RasterSettings(tile=t))[0]["image"].cpu().numpy()
+            for t in (8, 16, 32)]
+    np.testing.assert_array_equal(imgs[0], imgs[1])
+    np.testing.assert_array_equal(imgs[0], imgs[2])
+
+
+def test_multi_camera_uneven_sizes_and_background():
+    sc = synth.clustered_scene(15000, 9, sh_degree=2, log_scale_mu=-3.3)
+    cams = synth.sphere_cameras(9, [(64, 48), (131, 77), (40, 90)])
+    bg = (0.1, 0.7, 0.3)
+    out, _, ca = gpu_render(sc, cams, settings=raster.RasterSettings(background=bg))
+    img = out["image"].cpu().numpy()
+    for cam, off in zip(cams, ca.pixel_offsets()):
+        ref = oracle.render(sc, cam, bg=np.array(bg))
+        P = cam.width * cam.height
+        assert_image_parity(img[off:off + P], ref["image"].reshape(-1, 3), f"camera {cam.width}x{cam.height}")
+
+
+def test_forward_fed_oracle_splats_isolates_compositing():
+    """gs_rasterize_fwd on the oracle's (float32-rounded) 2D splats and colours vs the oracle
+    compositing of exactly those values promoted to float64."""
+    sc, cam = _mid_scene(n=20000, seed=21)
+    sp = oracle.project(sc, cam)
+    col, _ = oracle.sh_colors(sc, cam)
+    f32 = {k: sp[k].astype(np.float32) for k in ("means2d", "depths", "conics", "opacities")}
+    sp32 = dict(sp, **{k: v.astype(np.float64) for k, v in f32.items()})
+    # recompute the boxes from the float32 means exactly like the kernels
+    for n in np.nonzero(sp["radii"] > 0)[0]:
+        r = int(sp["radii"][n])
+        mx, my = (float(v) for v in f32["means2d"][n])
+        x0, x1 = int(np.ceil(mx - r - 0.5)), int(np.floor(mx + r - 0.5))
+        y0, y1 = int(np.ceil(my - r - 0.5)), int(np.floor(my + r - 0.5))
+        sp32["boxes"][n] = [max(x0, 0), min(x1, cam.width - 1), max(y0, 0), min(y1, cam.height - 1)]
+        if sp32["boxes"][n][0] > sp32["boxes"][n][1] or sp32["boxes"][n][2] > sp32["boxes"][n][3]:
+            sp32["radii"][n] = 0
+    col32 = col.astype(np.float32)
+    ref = oracle.render_splats(sp32, col32.astype(np.float64), cam.width, cam.height)
+    ca = _lib.CameraArray([cam])
+    p = _lib.make_params()
+    t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    m, d, r = t(f32["means2d"][None]), t(f32["depths"][None]), t(sp32["radii"][None], torch.int32)
+    bs = raster.bin_sort(ca, sc.n, p, m, d, r)
+    image, final_T, _, _ = raster.rasterize_fwd(ca, sc.n, p, 3, bs["ranges"], bs["values"], r, m,
+                                                t(f32["conics"][None]), t(f32["opacities"][None]), t(col32[None]),
+                                                None)
+    frac, mean_abs, max_abs, _ = image_stats(image.cpu().numpy(), ref["color"])
+    assert frac >= 0.9999 and mean_abs <= 2e-6, (frac, mean_abs, max_abs)
+    np.testing.assert_allclose(final_T.cpu().numpy(), ref["T"], atol=5e-4)
+
+
+def test_blend_count_matches_oracle():
+    sc, cam, _ = synth.tiny_scene()
+    d = dev_scene(sc)
+    ca = _lib.CameraArray([cam])
+    out = raster.forward_pass(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], sh=d["sh"],
+                              sh_degree=0, count_blends=True)
+    ref = oracle.render(sc, cam)
+    b_gpu = int(out["blends"].item())
+    b_ref = int(ref["blends"].sum())
+    assert abs(b_gpu - b_ref) <= 1e-3 * b_ref, (b_gpu, b_ref)
+
+
+def test_empty_scene_renders_background():
+    cam = synth.make_camera(50, 35, (0, 0, 4))
+    sc = synth.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32), np.zeros((0, 3), np.float32),
+                     np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    out, _, _ = gpu_render(sc, [cam], settings=raster.RasterSettings(background=(0.2, 0.4, 0.6)))
+    img = out["image"].cpu().numpy()
+    np.testing.assert_allclose(img, np.tile([0.2, 0.4, 0.6], (50 * 35, 1)), atol=1e-7)
+    assert (out["final_T"].cpu().numpy() == 1).all()
+
+
+def test_all_culled_scene():
+    sc, cam = _mid_scene(n=1000, seed=2)
+    sc.means[:] = np.asarray(cam.viewmat, np.float64)[:3, :3].T @ np.array([0, 0, -5.0]) - \
+        np.asarray(cam.viewmat, np.float64)[:3, :3].T @ np.asarray(cam.viewmat, np.float64)[:3, 3]
+    out, _, _ = gpu_render(sc, [cam])
+    assert out["K"] == 0
+    assert (out["radii"].cpu().numpy() == 0).all()
+    assert (out["image"].cpu().numpy() == 0).all()
+
+
+# --------------------------------------------------------------------------- #
+# backward                                                                     #
+# --------------------------------------------------------------------------- #
+
+def _masked_upstream(sc, cams_ref_renders, out_img, out_alpha, rng, P):
+    d_img = rng.uniform(-1, 1, (P, 3)) / P
+    d_alpha = rng.uniform(-1, 1, P) / P
+    ref_img, ref_alpha = cams_ref_renders
+    flips = flipped_pixels(out_img, out_alpha, ref_img, ref_alpha)
+    assert flips.mean() <= 1e-4 or flips.sum() <= 1, f"{flips.sum()} threshold flips"
+    d_img[flips] = 0
+    d_alpha[flips] = 0
+    return d_img, d_alpha, int(flips.sum())
+
+
+@pytest.mark.parametrize("deg,aa", [(0, False), (3, False), (3, True)])
+def test_backward_matches_oracle(deg, aa):
+    sc, cam = _mid_scene(n=8000, seed=31 + deg, deg=deg)
+    settings = raster.RasterSettings(antialiased=aa, background=(0.3, 0.2, 0.1))
+    bg = np.array([0.3, 0.2, 0.1])
+    ref_f = oracle.render(sc, cam, bg=bg, antialiased=aa)
+    P = cam.width * cam.height
+    rng = np.random.default_rng(5)
+    out, _, _ = gpu_render(sc, [cam], settings=settings)
+    d_img, d_alpha, nflip = _masked_upstream(sc, (ref_f["image"].reshape(P, 3), ref_f["alpha"].reshape(P)),
+                                             out["image"].cpu().numpy(), (1 - out["final_T"]).cpu().numpy(), rng, P)
+    g_gpu, _, _ = gpu_grads(sc, [cam], d_img, d_alpha, settings=settings)
+    g_ref = oracle.render_grads(sc, cam, d_img, d_alpha=d_alpha, bg=bg, antialiased=aa)
+    assert_grad_parity(g_gpu, g_ref)
+
+
+def test_tiny_config_l1_loss_backward():
+    """Config 1: forward + backward of the mean L1 loss against a U[0,1] target."""
+    sc, cam, target = synth.tiny_scene()
+    out, _, _ = gpu_render(sc, [cam])
+    img = out["image"].cpu().numpy().reshape(64, 64, 3)
+    ref_f = oracle.render(sc, cam)
+    flips = flipped_pixels(img.reshape(-1, 3), (1 - out["final_T"]).cpu().numpy(), ref_f["image"].reshape(-1, 3),
+                           ref_f["alpha"].reshape(-1))
+    d_img = (np.sign(img - target) / img.size).reshape(-1, 3)
+    d_img[flips] = 0
+    g_gpu, _, _ = gpu_grads(sc, [cam], d_img)
+    g_ref = oracle.render_grads(sc, cam, d_img)
+    assert_grad_parity(g_gpu, g_ref)
+
+
+def test_backward_multi_camera_sums_over_views():
+    sc = synth.clustered_scene(6000, 17, sh_degree=1, log_scale_mu=-3.2)
+    cams = synth.sphere_cameras(17, [(96, 64), (57, 80)])
+    rng = np.random.default_rng(3)
+    out, _, ca = gpu_render(sc, cams)
+    img = out["image"].cpu().numpy()
+    alpha = (1 - out["final_T"]).cpu().numpy()
+    d_img = np.zeros_like(img, dtype=np.float64)
+    g_ref = None
+    for cam, off in zip(cams, ca.pixel_offsets()):
+        P = cam.width * cam.height
+        ref_f = oracle.render(sc, cam)
+        di, _, _ = _masked_upstream(sc, (ref_f["image"].reshape(P, 3), ref_f["alpha"].reshape(P)), img[off:off + P],
+                                    alpha[off:off + P], rng, P)
+        d_img[off:off + P] = di
+        g = oracle.render_grads(sc, cam, di)
+        g_ref = g if g_ref is None else {k: g_ref[k] + g[k] for k in g_ref if k.startswith("d_")}
+    g_gpu, _, _ = gpu_grads(sc, cams, d_img)
+    assert_grad_parity(g_gpu, g_ref)
+
+
+def test_nd_features_forward_and_backward():
+    """N-dimensional features instead of SH colour (App. C: c may be any N-vector)."""
+    sc, cam = _mid_scene(n=4000, seed=41, deg=0)
+    D = 8
+    rng = np.random.default_rng(4)
+    feats = rng.uniform(0, 1, (sc.n, D)).astype(np.float32)
+    sp = oracle.project(sc, cam)
+    ref = oracle.render_splats(sp, feats.astype(np.float64), cam.width, cam.height)
+    d = dev_scene(sc)
+    leaves = [d["means"], d["quats"], d["log_scales"], d["opacity_logits"],
+              torch.as_tensor(feats, device="cuda")]
+    for x in leaves:
+        x.requires_grad_(True)
+    imgs, alphas, _ = raster.rasterization(*leaves[:4], cameras=[cam], features=leaves[4])
+    img = imgs[0].reshape(-1, D).detach().cpu().numpy()
+    assert_image_parity(img, ref["color"], "features")
+    P = cam.width * cam.height
+    gimg = rng.uniform(-1, 1, (P, D)) / P
+    g = torch.autograd.grad([imgs[0]], leaves, [torch.as_tensor(gimg.reshape(cam.height, cam.width, D),
+                                                                dtype=torch.float32, device="cuda")])
+    g2 = oracle.render_splats_bwd(sp, feats.astype(np.float64), cam.width, cam.height, gimg)
+    assert rel_l2(g[4].cpu().numpy(), g2["d_colors"]) < 1e-3
+    g3 = oracle.project_bwd(sc, cam, g2["d_means2d"], g2["d_conics"], g2["d_opacities"])
+    assert rel_l2(g[0].cpu().numpy(), g3["d_means"]) < 1e-3
+    assert rel_l2(g[3].cpu().numpy(), g3["d_opacity_logits"]) < 1e-3
+
+
+def test_absgrad_matches_oracle():
+    sc, cam = _mid_scene(n=5000, seed=51, deg=0)
+    settings = raster.RasterSettings(absgrad=True)
+    P = cam.width * cam.height
+    rng = np.random.default_rng(6)
+    out, _, _ = gpu_render(sc, [cam])
+    ref_f = oracle.render(sc, cam)
+    d_img, _, _ = _masked_upstream(sc, (ref_f["image"].reshape(P, 3), ref_f["alpha"].reshape(P)),
+                                   out["image"].cpu().numpy(), (1 - out["final_T"]).cpu().numpy(), rng, P)
+    gpu_grads(sc, [cam], d_img, settings=settings)
+    ag = raster.RasterizeGaussians.last_absgrad[0].cpu().numpy()
+    sp = ref_f["splats"]
+    g2 = oracle.render_splats_bwd(sp, ref_f["colors"], cam.width, cam.height, d_img, want_absgrad=True)
+    assert rel_l2(ag, g2["absgrad"]) < 1e-3
