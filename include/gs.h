@@ -162,6 +162,31 @@ GS_API gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, c
                            void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* gs_tile_bin_sort_noalloc -- the same binning and sorting as               */
+/* gs_tile_bin_sort, for callers that cannot allocate device memory (a       */
+/* plug-in inside an application whose allocator owns all device memory, a   */
+/* real-time loop that must not stall on an allocation, a binding with no    */
+/* device allocator).  The paper has no counterpart: this is an interface    */
+/* variant, not a step of the method.                                        */
+/*                                                                          */
+/* Same arguments, outputs and errors as gs_tile_bin_sort minus the           */
+/* workspace: the scratch comes from a fixed array of                         */
+/* GS_NOALLOC_SCRATCH_BYTES inside libgs, reserved on every GPU that loads   */
+/* the library until the process exits.  A call whose scratch need           */
+/* (gs_tile_bin_sort_workspace) exceeds it returns GS_ERR_CAPACITY and        */
+/* launches nothing.  The first call on a device looks up the array's device */
+/* address (cudaGetSymbolAddress); make that first call before any stream    */
+/* capture.  All calls share the array: calls that overlap on the GPU (other */
+/* streams, other host threads) race on it and must be serialised.  Nothing  */
+/* in it needs clearing between calls.  Nothing is allocated by this call.   */
+/* ------------------------------------------------------------------------ */
+#define GS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                                          const float *means2d, const float *depths, const int32_t *radii,
+                                          int64_t K_capacity, uint64_t *keys, int32_t *values,
+                                          int32_t *tile_ranges, int64_t *K_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* gs_rasterize_fwd -- App. C.2: for each pixel p (centre i+0.5, j+0.5) walk */
 /* its tile's sorted list front to back; a Gaussian counts at p only if p is */
 /* inside its pixel box; sigma = 1/2 D^T conic D with D = p - mu';           */

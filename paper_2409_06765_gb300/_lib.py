@@ -27,8 +27,9 @@ GS_MAX_CHANNELS = 64
 EXPORTED = (
     "gs_default_params", "gs_status_string", "gs_last_error", "gs_num_tiles", "gs_num_pixels", "gs_project",
     "gs_sh_eval", "gs_tile_bin_sort_workspace", "gs_tile_bin_sort", "gs_rasterize_fwd", "gs_rasterize_bwd",
-    "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches",
+    "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc",
 )
+GS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class GsError(RuntimeError):
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_tile_bin_sort_workspace": (_I64, [_CAM, _I32, _I32, _PAR, _I64]),
             "gs_tile_bin_sort": (_I32, [_CAM, _I32, _I32, _PAR, _P, _P, _P, _I64, _P, _P, _P, _P, _P, ctypes.c_size_t,
                                         _P]),
+            "gs_tile_bin_sort_noalloc": (_I32, [_CAM, _I32, _I32, _PAR, _P, _P, _P, _I64, _P, _P, _P, _P, _P]),
             "gs_rasterize_fwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                         _P]),
             "gs_rasterize_bwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -252,6 +254,18 @@ def gs_tile_bin_sort(cams: CameraArray, N: int, params: GsParams, means2d, depth
                                  _dev(tile_ranges, "i32", "tile_ranges"), _dev(K_out, "i64", "K_out"),
                                  _dev(workspace, "u8", "workspace"), workspace.numel(), _stream(stream))
     _check(st, "gs_tile_bin_sort")
+
+
+def gs_tile_bin_sort_noalloc(cams: CameraArray, N: int, params: GsParams, means2d, depths, radii, K_capacity: int,
+                             keys, values, tile_ranges, K_out, stream=None):
+    """gs_tile_bin_sort without a workspace argument: for callers that cannot allocate device
+    memory, the scratch is the library's built-in array (GS_NOALLOC_SCRATCH_BYTES)."""
+    st = load().gs_tile_bin_sort_noalloc(cams.ptr, cams.C, N, ctypes.byref(params), _dev(means2d, "f32", "means2d"),
+                                         _dev(depths, "f32", "depths"), _dev(radii, "i32", "radii"),
+                                         int(K_capacity), _dev(keys, "u64", "keys", optional=True),
+                                         _dev(values, "i32", "values"), _dev(tile_ranges, "i32", "tile_ranges"),
+                                         _dev(K_out, "i64", "K_out"), _stream(stream))
+    _check(st, "gs_tile_bin_sort_noalloc")
 
 
 def gs_rasterize_fwd(cams: CameraArray, N: int, params: GsParams, channels: int, tile_ranges, values, radii, means2d,

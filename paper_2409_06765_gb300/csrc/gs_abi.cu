@@ -54,6 +54,8 @@ using namespace gs;
 
 static thread_local char g_last_error[512] = "";
 
+void gs::set_last_error(const char *text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
+
 static gs_status fail_cuda(cudaError_t e, const char *where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
     return GS_ERR_CUDA;

@@ -11,6 +11,9 @@ namespace gs {
 // Host-side launch accounting behind gs_kernel_launches() (defined in gs_abi.cu).
 void note_launch();
 
+// Records the text gs_last_error() returns on this thread (defined in gs_abi.cu).
+void set_last_error(const char *text);
+
 constexpr int kMaxCams = GS_MAX_CAMERAS;
 
 // Per-camera constants, passed to kernels by value (a __grid_constant__ CamSet).
