@@ -138,7 +138,7 @@ def build_workload(name: str, rank: int):
 class KernelPath:
     """Preallocated buffers and one fwd+bwd step issued through the C ABI (no host sync)."""
 
-    def __init__(self, scene, cams, tile=16, batch=256):
+    def __init__(self, scene, cams, tile=16, batch=256, ppt=0):
         import torch
         from paper_2409_06765_gb300 import _lib
         self.torch, self.L = torch, _lib
@@ -147,7 +147,7 @@ class KernelPath:
         self.means, self.quats, self.log_scales = t(scene.means), t(scene.quats), t(scene.log_scales)
         self.logits, self.sh, self.deg = t(scene.opacity_logits), t(scene.sh), scene.sh_degree
         self.cams = _lib.CameraArray(cams)
-        self.params = _lib.make_params(tile=tile, batch_depth=batch)
+        self.params = _lib.make_params(tile=tile, batch_depth=batch, pixels_per_thread=ppt)
         C, N = self.cams.C, scene.n
         self.C, self.N = C, N
         f = lambda *s: torch.empty(*s, device=dev)
@@ -181,7 +181,8 @@ class KernelPath:
             self.forward()
             torch.cuda.synchronize()
         self.K = int(self.K_out.item())
-        assert self.K <= self.capacity
+        if not 0 <= self.K <= self.capacity:
+            raise RuntimeError(f"bin/sort returned K = {self.K} for capacity {self.capacity}")
 
     def _alloc_sort(self):
         torch = self.torch
@@ -245,7 +246,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     scene, cams, desc = build_workload(args.workload, rank)
-    kp = KernelPath(scene, cams, tile=args.tile, batch=args.batch)
+    kp = KernelPath(scene, cams, tile=args.tile, batch=args.batch, ppt=args.ppt)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
     target = torch.as_tensor(target_np, device="cuda")
@@ -309,7 +310,7 @@ def run_ours(args):
     if not args.no_e2e:
         leaves = [x.detach().clone().requires_grad_(True) for x in (kp.means, kp.quats, kp.log_scales, kp.logits,
                                                                      kp.sh)]
-        settings = raster.RasterSettings(tile=args.tile, batch_depth=args.batch)
+        settings = raster.RasterSettings(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt)
         state = raster.RasterState()
         host_target = torch.as_tensor(target_np).pin_memory()
         dev_target = torch.empty_like(target)
@@ -375,7 +376,7 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic (seeded clustered Gaussians; no dataset)",
         "config": {"workload": args.workload, "description": desc, "gaussians": scene.n, "sh_degree": scene.sh_degree,
                    "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": args.tile,
-                   "batch_depth": args.batch, "intersections_K": kp.K, "blends_per_view": blends,
+                   "batch_depth": args.batch, "pixels_per_thread": args.ppt, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
         "ms_per_view_fwd_bwd": ms_step_job, "ms_per_view_fwd": ms_fwd,
         "blends_per_s_fwd": blends / (ms_fwd / 1000.0),
@@ -482,6 +483,7 @@ def main():
     ap.add_argument("--workload", default="headline", choices=["headline", "training_step", "tiny"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per compositing thread (0 = library default)")
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")

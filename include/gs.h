@@ -70,7 +70,9 @@ typedef struct gs_params {
     int32_t tile;         /* tile edge in pixels: 8, 16 or 32 */
     int32_t batch_depth;  /* Gaussians staged in shared memory per batch: 32..256, multiple of 32 */
     int32_t antialiased;  /* 0: classic mode; 1: opacity * sqrt(|S'| / |S' + sI|) [App. A] */
-    int32_t reserved;     /* must be 0 */
+    int32_t pixels_per_thread; /* pixels one compositing thread owns, stacked along y: 0 = default
+                                  (1 for 8x8 and 16x16 tiles, 4 for 32x32); also 2 for 16x16, 2 or 4
+                                  for 32x32.  Changes the schedule only, never the result. */
     float eps2d;          /* low-pass s added to the 2D covariance [App. A] */
     float near_plane;     /* a Gaussian is culled when its camera depth t_z < near_plane */
     float alpha_min;      /* a (pixel, Gaussian) pair with alpha < alpha_min is skipped */
@@ -148,7 +150,8 @@ GS_API gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t
 /* out: values [K] int32 (flat index c*N + n), tile_ranges [T,2] int32        */
 /*      ([start, end) into values; (0,0) for an empty tile; T = gs_num_tiles),*/
 /*      keys [K] uint64 (optional, NULL to skip), K_out [1] int64 on the      */
-/*      device = the number of pairs K.  When K > K_capacity only the first   */
+/*      device = the number of pairs K (-1 if an internal bounded wait timed   */
+/*      out, in which case the lists are invalid; not expected to happen).  When K > K_capacity only the first   */
 /*      K_capacity slots are written, the lists are incomplete, and the       */
 /*      caller must reallocate (K_out tells by how much) and call again.      */
 /* workspace: device scratch of at least gs_tile_bin_sort_workspace() bytes,  */

@@ -21,14 +21,15 @@ cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *
 BinSortLayout binsort_layout(long long CN, long long Kcap, int G);
 cudaError_t launch_binsort(const CamSet &, int, const float *, const float *, const int *, long long,
                            unsigned long long *, int *, int *, long long *, void *, cudaStream_t);
-cudaError_t launch_raster_fwd(const CamSet &, const RasterConsts &, int, int, const int *, const int *, const int *,
+cudaError_t launch_raster_fwd(const CamSet &, const RasterConsts &, int, int, int, const int *, const int *, const int *,
                               const float *, const float *, const float *, const float *, const float *, float *,
                               float *, int *, unsigned long long *, cudaStream_t);
-cudaError_t launch_raster_bwd(const CamSet &, const RasterConsts &, int, int, const int *, const int *, const int *,
+cudaError_t launch_raster_bwd(const CamSet &, const RasterConsts &, int, int, int, const int *, const int *, const int *,
                               const float *, const float *, const float *, const float *, const float *,
                               const float *, const int *, const float *, const float *, float *, float *, float *,
                               float *, float *, cudaStream_t);
-int raster_channel_capacity(int tile, int ch, bool restricted);
+int raster_channel_capacity(int tile, int ppt, int ch, bool restricted);
+int raster_pixels_per_thread(int tile, int ppt);
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -106,7 +107,9 @@ static gs_status make_camset(const gs_camera *cams, int C, int tile, CamSet &cs)
 
 static gs_status check_params(const gs_params *p, RasterConsts &rc) {
     if (!p) return fail_arg("params is NULL");
-    if (p->reserved != 0) return fail_arg("params.reserved must be 0");
+    if (p->tile != 8 && p->tile != 16 && p->tile != 32) return fail_arg("tile must be 8, 16 or 32");
+    if (raster_pixels_per_thread(p->tile, p->pixels_per_thread) == 0)
+        return fail_arg("pixels_per_thread: 0, or 1 for 8x8 tiles, 1 or 2 for 16x16, 2 or 4 for 32x32");
     if (p->batch_depth < 32 || p->batch_depth > 256 || (p->batch_depth % 32) != 0)
         return fail_arg("batch_depth must be a multiple of 32 in [32, 256]");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return fail_arg("alpha_max must be in (0, 1)");
@@ -146,7 +149,7 @@ void gs_default_params(gs_params *p) {
     p->tile = 16;
     p->batch_depth = 256;
     p->antialiased = 0;
-    p->reserved = 0;
+    p->pixels_per_thread = 0;
     p->eps2d = 0.3f;
     p->near_plane = 0.01f;
     p->alpha_min = 1.f / 255.f;
@@ -234,6 +237,7 @@ gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs
     GS_TRY(check_cn(C, N));
     cs.N = N;
     if (K_capacity < 0 || K_capacity >= (1ll << 31)) return fail_arg("K_capacity must be in [0, 2^31)");
+    if (cs.total_tiles >= (1 << 28)) return fail_arg("more than 2^28 tiles in one call");
     GS_NONNULL(tile_ranges); GS_NONNULL(K_out); GS_NONNULL(workspace);
     if (N > 0) {
         GS_NONNULL(means2d); GS_NONNULL(depths); GS_NONNULL(radii);
@@ -265,7 +269,8 @@ gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     GS_TRY(check_cn(C, N));
     cs.N = N;
     if (channels < 1 || channels > GS_MAX_CHANNELS) return fail_arg("channels must be in [1, GS_MAX_CHANNELS]");
-    if (raster_channel_capacity(params->tile, channels, blend_count != nullptr) == 0) {
+    const int ppt = raster_pixels_per_thread(params->tile, params->pixels_per_thread);
+    if (raster_channel_capacity(params->tile, ppt, channels, blend_count != nullptr) == 0) {
         snprintf(g_last_error, sizeof(g_last_error), "no kernel for tile %d with %d channels%s", params->tile,
                  channels, blend_count ? " and blend counting" : "");
         return GS_ERR_UNSUPPORTED;
@@ -278,7 +283,7 @@ gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     }
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     if (blend_count && !aligned(blend_count, 8)) return fail_arg("blend_count must be 8-byte aligned");
-    cudaError_t e = launch_raster_fwd(cs, rc, channels, params->batch_depth, tile_ranges, values, radii, means2d,
+    cudaError_t e = launch_raster_fwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, image, final_T, last_contrib,
                                       (unsigned long long *)blend_count, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_rasterize_fwd");
@@ -297,7 +302,8 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     GS_TRY(check_cn(C, N));
     cs.N = N;
     if (channels < 1 || channels > GS_MAX_CHANNELS) return fail_arg("channels must be in [1, GS_MAX_CHANNELS]");
-    if (raster_channel_capacity(params->tile, channels, absgrad != nullptr) == 0) {
+    const int ppt = raster_pixels_per_thread(params->tile, params->pixels_per_thread);
+    if (raster_channel_capacity(params->tile, ppt, channels, absgrad != nullptr) == 0) {
         snprintf(g_last_error, sizeof(g_last_error), "no backward kernel for tile %d with %d channels%s",
                  params->tile, channels, absgrad ? " and absgrad" : "");
         return GS_ERR_UNSUPPORTED;
@@ -309,7 +315,7 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     if (!aligned(means2d, 8) || !aligned(d_means2d, 8)) return fail_arg("means2d/d_means2d must be 8-byte aligned");
     if (absgrad && !aligned(absgrad, 8)) return fail_arg("absgrad must be 8-byte aligned");
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
-    cudaError_t e = launch_raster_bwd(cs, rc, channels, params->batch_depth, tile_ranges, values, radii, means2d,
+    cudaError_t e = launch_raster_bwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, final_T, last_contrib, d_image, d_alpha,
                                       d_means2d, d_conics, d_opacities, d_colors, absgrad, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_rasterize_bwd");

@@ -38,7 +38,7 @@ struct CamSet {
 
 // Byte offsets of the tile_bin_sort workspace regions (see binsort.cu).
 struct BinSortLayout {
-    size_t dk0, dk1, dv0, dv1, counts, partials, misc, hist, tk0, tk1, tvB, total;
+    size_t dk0, dk1, dv0, dv1, counts, rects, offsets, chunk_start, partials, misc, lookback, tk0, tk1, tvB, total;
 };
 
 struct RasterConsts {
@@ -105,6 +105,75 @@ __device__ __forceinline__ float mahalanobis_half(float dx, float dy, float ca, 
 // exp(-sigma) = 2^(-sigma log2 e)
 __device__ __forceinline__ float gauss_weight(float sigma) {
     return ex2_approx(__fmul_rn(-1.4426950408889634f, sigma));
+}
+
+// Launch shape of the compositing kernels: PPT pixels per thread stacked along y, so a
+// tile of TILE x TILE pixels runs TILE*TILE/PPT threads and a warp covers a TILE-wide band
+// of 32*PPT/TILE rows.
+template <int TILE, int PPT>
+struct RasterShape {
+    static constexpr int kPPT = PPT;
+    static constexpr int kThreads = TILE * TILE / PPT;
+    static constexpr int kWarpRows = 32 * PPT / TILE;
+    static_assert(kThreads >= 32 && kThreads <= 1024 && kThreads % 32 == 0, "bad raster shape");
+};
+
+// One Gaussian of a tile's list as both compositing kernels stage it in shared memory:
+//   g   = (mean x, mean y, conic a, conic b)
+//   h   = (conic c, opacity, sigma cut, id as int bits)
+//   box = (x0, x1 - x0, y0, y1 - y0) of the (unclipped) pixel box
+// The sigma cut is ln(opacity / alpha_min): beyond it alpha < alpha_min, so such pairs
+// never blend; it is used only to skip work that would be skipped anyway.
+__device__ __forceinline__ void stage_splat(int id, const float2 *__restrict__ means2d,
+                                            const float *__restrict__ conics, const float *__restrict__ opac,
+                                            const int *__restrict__ radii, float alpha_min, float4 &g, float4 &h,
+                                            int4 &box) {
+    const float2 m = means2d[id];
+    const int r = radii[id];
+    int x0, x1, y0, y1;
+    support_span(m.x, r, x0, x1);
+    support_span(m.y, r, y0, y1);
+    const float o = opac[id];
+    const float cut = !(o >= alpha_min) ? -1.f : (alpha_min > 0.f ? __logf(o / alpha_min) : 3.0e38f);
+    g = make_float4(m.x, m.y, conics[3 * id], conics[3 * id + 1]);
+    h = make_float4(conics[3 * id + 2], o, cut, __int_as_float(id));
+    box = make_int4(x0, x1 - x0, y0, y1 - y0);
+}
+
+// Can the staged Gaussian blend at any pixel of the rectangle of pixel indices
+// [rx0, rx1] x [ry0, ry1]?  False only when the pixel box misses the rectangle or when
+// sigma exceeds the cut (plus a margin far above float32 rounding) on the whole
+// rectangle of pixel centres; so a false answer never removes a pair that blends.
+__device__ __forceinline__ bool box_hits(const int4 &b, int rx0, int rx1, int ry0, int ry1) {
+    return !(b.x > rx1 || b.x + b.y < rx0 || b.z > ry1 || b.z + b.w < ry0);
+}
+
+__device__ __forceinline__ bool may_blend(const float4 &g, const float4 &h, const int4 &b, int rx0, int rx1, int ry0,
+                                          int ry1) {
+    if (!box_hits(b, rx0, rx1, ry0, ry1)) return false;
+    if (!(h.z >= 0.f)) return false;
+    // minimum of sigma(p) = 1/2 (p-m)^T [[a,b],[b,c]] (p-m) over the rectangle of pixel centres
+    const float x0 = (float)rx0 + 0.5f - g.x, x1 = (float)rx1 + 0.5f - g.x;
+    const float y0 = (float)ry0 + 0.5f - g.y, y1 = (float)ry1 + 0.5f - g.y;
+    const float a = g.z, bb = g.w, c = h.x;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    const float ia = 1.f / a, ic = 1.f / c;
+    float best = 3.0e38f;
+    // vertical edges: dx fixed, minimise over dy
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = e ? x1 : x0;
+        const float dy = fminf(fmaxf(-bb * dx * ic, y0), y1);
+        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + bb * dx * dy);
+    }
+    // horizontal edges: dy fixed, minimise over dx
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = e ? y1 : y0;
+        const float dx = fminf(fmaxf(-bb * dy * ia, x0), x1);
+        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + bb * dx * dy);
+    }
+    return best <= h.z * 1.001f + 1e-3f;
 }
 
 }  // namespace gs

@@ -180,37 +180,45 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
     }
 }
 
+// Backward: a CTA of kShBwdThreads threads owns as many consecutive Gaussians.  The
+// coefficient gradients are accumulated over cameras in a second shared-memory row per
+// thread (not in registers, which keeps occupancy up at degree 3) and leave through the
+// same contiguous copy as the coefficients came in.
+constexpr int kShBwdThreads = 128;
+
 template <int DEG>
-__global__ void __launch_bounds__(256) sh_bwd_kernel(int N, const float *__restrict__ sh,
-                                                     const float *__restrict__ means, const int *__restrict__ radii,
-                                                     const __grid_constant__ CamSet cs, ShConsts kc,
-                                                     const float *__restrict__ d_colors, float *__restrict__ d_sh,
-                                                     float *__restrict__ d_means) {
+__global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const float *__restrict__ sh,
+                                                               const float *__restrict__ means,
+                                                               const int *__restrict__ radii,
+                                                               const __grid_constant__ CamSet cs, ShConsts kc,
+                                                               const float *__restrict__ d_colors,
+                                                               float *__restrict__ d_sh, float *__restrict__ d_means) {
     constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
     extern __shared__ float s_coef[];
-    int n0 = blockIdx.x * 256;
-    int cnt = min(256, N - n0);
+    float *s_grad = s_coef + kShBwdThreads * STRIDE;
+    const int n0 = blockIdx.x * kShBwdThreads;
+    const int cnt = min(kShBwdThreads, N - n0);
     const float *src = sh + (size_t)n0 * F;
     stage_rows<F, STRIDE>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
-    __syncthreads();
-    int n = n0 + threadIdx.x;
-    float dc[F];
+    float *gr = s_grad + threadIdx.x * STRIDE;
 #pragma unroll
-    for (int f = 0; f < F; ++f) dc[f] = 0.f;
-    float dm[3] = {0.f, 0.f, 0.f};
+    for (int f = 0; f < F; ++f) gr[f] = 0.f;
+    __syncthreads();
+    const int n = n0 + threadIdx.x;
     if (n < N) {
         const float *cf = s_coef + threadIdx.x * STRIDE;
-        float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
+        const float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
+        float dm[3] = {0.f, 0.f, 0.f};
         for (int c = 0; c < cs.C; ++c) {
-            size_t idx = (size_t)c * N + n;
+            const size_t idx = (size_t)c * N + n;
             if (radii[idx] <= 0) continue;
             const float *R = cs.cam[c].R, *t = cs.cam[c].t;
-            float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
-            float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
-            float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
-            float vx = mx - ox, vy = my - oy, vz = mz - oz;
-            float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-            float x = vx * il, y = vy * il, z = vz * il;
+            const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+            const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+            const float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+            const float vx = mx - ox, vy = my - oy, vz = mz - oz;
+            const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+            const float x = vx * il, y = vy * il, z = vz * il;
             float Y[K];
             sh_eval_basis<DEG>(kc, x, y, z, Y);
             float g[3];
@@ -224,16 +232,16 @@ __global__ void __launch_bounds__(256) sh_bwd_kernel(int N, const float *__restr
             float w[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                dc[3 * k] += Y[k] * g[0];
-                dc[3 * k + 1] += Y[k] * g[1];
-                dc[3 * k + 2] += Y[k] * g[2];
+                gr[3 * k] += Y[k] * g[0];
+                gr[3 * k + 1] += Y[k] * g[1];
+                gr[3 * k + 2] += Y[k] * g[2];
                 w[k] = cf[3 * k] * g[0] + cf[3 * k + 1] * g[1] + cf[3 * k + 2] * g[2];
             }
             if (DEG > 0) {
                 float dd[3] = {0.f, 0.f, 0.f};
                 sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
                 // dir = v / |v|:  d v = (I - dir dir^T) d dir / |v|
-                float p = x * dd[0] + y * dd[1] + z * dd[2];
+                const float p = x * dd[0] + y * dd[1] + z * dd[2];
                 dm[0] += (dd[0] - x * p) * il;
                 dm[1] += (dd[1] - y * p) * il;
                 dm[2] += (dd[2] - z * p) * il;
@@ -243,15 +251,28 @@ __global__ void __launch_bounds__(256) sh_bwd_kernel(int N, const float *__restr
         d_means[3 * n + 1] = dm[1];
         d_means[3 * n + 2] = dm[2];
     }
-    // write d_sh through shared memory so the global stores are contiguous
-    __syncthreads();
-    float *row = s_coef + threadIdx.x * STRIDE;
-#pragma unroll
-    for (int f = 0; f < F; ++f) row[f] = dc[f];
     __syncthreads();
     float *dst = d_sh + (size_t)n0 * F;
-    int total = cnt * F;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = s_coef[(e / F) * STRIDE + e % F];
+    const int total = cnt * F;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        const int nvec = total / 4;
+        float4 *dst4 = reinterpret_cast<float4 *>(dst);
+        for (int v = threadIdx.x; v < nvec; v += kShBwdThreads) {
+            int e = 4 * v;
+            float4 q;
+            q.x = s_grad[(e / F) * STRIDE + e % F];
+            ++e;
+            q.y = s_grad[(e / F) * STRIDE + e % F];
+            ++e;
+            q.z = s_grad[(e / F) * STRIDE + e % F];
+            ++e;
+            q.w = s_grad[(e / F) * STRIDE + e % F];
+            dst4[v] = q;
+        }
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_grad[(e / F) * STRIDE + e % F];
+    } else {
+        for (int e = threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_grad[(e / F) * STRIDE + e % F];
+    }
 }
 
 template <int DEG>
@@ -273,13 +294,13 @@ template <int DEG>
 static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
                                    const float *d_colors, float *d_sh, float *d_means, cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
-    size_t smem = 256 * STRIDE * sizeof(float);
+    size_t smem = 2 * kShBwdThreads * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sh_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sh_bwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
+    sh_bwd_kernel<DEG><<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
                                                             d_sh, d_means);
     note_launch();
     return cudaGetLastError();

@@ -34,10 +34,11 @@ class RasterSettings:
     T_min: float = 1e-4
     background: tuple | None = None
     absgrad: bool = False
+    pixels_per_thread: int = 0
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
-                                self.alpha_min, self.alpha_max, self.T_min)
+                                self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread)
 
 
 @dataclass
@@ -93,6 +94,8 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
         _lib.gs_tile_bin_sort(cams, N, params, means2d, depths, radii, state.capacity, keys, state.values, ranges,
                               K_out, state.workspace)
         K = int(K_out.item())
+        if K < 0:
+            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
         if K <= state.capacity:
             break
         state.ensure(cams, N, params, K, dev)

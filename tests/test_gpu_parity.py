@@ -165,13 +165,22 @@ def test_clustered_forward_matches_oracle(tile, batch):
     assert_image_parity((1 - out["final_T"]).cpu().numpy()[:, None], ref["alpha"].reshape(-1, 1), "alpha")
 
 
-def test_image_is_bit_identical_across_tile_sizes():
-    """The support rule is per pixel, so the tile size changes nothing but the schedule."""
+SCHEDULES = [(8, 1), (16, 1), (16, 2), (32, 2), (32, 4)]
+
+
+def test_image_is_bit_identical_across_schedules():
+    """The support rule is per pixel, so tile size, pixels per thread and batch depth change
+    nothing but the schedule: images, final T and alpha agree bit for bit."""
     sc, cam = _mid_scene(n=10000, seed=3)
-    imgs = [gpu_render(sc, [cam], settings=raster.RasterSettings(tile=t))[0]["image"].cpu().numpy()
-            for t in (8, 16, 32)]
-    np.testing.assert_array_equal(imgs[0], imgs[1])
-    np.testing.assert_array_equal(imgs[0], imgs[2])
+    outs = []
+    for tile, ppt in SCHEDULES:
+        for batch in (64, 256):
+            o = gpu_render(sc, [cam], settings=raster.RasterSettings(tile=tile, pixels_per_thread=ppt,
+                                                                      batch_depth=batch))[0]
+            outs.append((o["image"].cpu().numpy(), o["final_T"].cpu().numpy()))
+    for img, T in outs[1:]:
+        np.testing.assert_array_equal(img, outs[0][0])
+        np.testing.assert_array_equal(T, outs[0][1])
 
 
 def test_multi_camera_uneven_sizes_and_background():
@@ -265,10 +274,12 @@ def _masked_upstream(sc, cams_ref_renders, out_img, out_alpha, rng, P):
     return d_img, d_alpha, int(flips.sum())
 
 
-@pytest.mark.parametrize("deg,aa", [(0, False), (3, False), (3, True)])
-def test_backward_matches_oracle(deg, aa):
+@pytest.mark.parametrize("deg,aa,tile,ppt", [(0, False, 16, 0), (3, False, 16, 0), (3, True, 16, 0),
+                                             (3, False, 8, 1), (3, False, 16, 2), (3, False, 32, 2),
+                                             (3, False, 32, 4)])
+def test_backward_matches_oracle(deg, aa, tile, ppt):
     sc, cam = _mid_scene(n=8000, seed=31 + deg, deg=deg)
-    settings = raster.RasterSettings(antialiased=aa, background=(0.3, 0.2, 0.1))
+    settings = raster.RasterSettings(antialiased=aa, background=(0.3, 0.2, 0.1), tile=tile, pixels_per_thread=ppt)
     bg = np.array([0.3, 0.2, 0.1])
     ref_f = oracle.render(sc, cam, bg=bg, antialiased=aa)
     P = cam.width * cam.height
