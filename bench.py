@@ -195,34 +195,78 @@ class KernelPath:
         torch = self.torch
         self.d_image.copy_(torch.sign(self.image - target) / self.image.numel())
 
-    def forward(self, events=None, count=None):
+    # The step in four parts: the two compositing kernels are launched directly (bracketed by
+    # CUDA events for the roofline); the stages before and after them, some twenty short
+    # launches, can be replayed as CUDA graphs (capture_graphs) to cut launch gaps.
+    def _pre(self):
         L = self.L
         L.gs_project(self.cams, self.means, self.quats, self.log_scales, self.logits, self.params, self.means2d,
                      self.depths, self.conics, self.radii, self.tiles, self.opac)
         L.gs_sh_eval(self.cams, self.deg, self.sh, self.means, self.radii, self.colors)
         L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity,
                            None, self.values, self.ranges, self.K_out, self.workspace)
-        if events:
-            events[0].record()
-        L.gs_rasterize_fwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii, self.means2d,
-                           self.conics, self.opac, self.colors, None, self.image, self.final_T, self.last, count)
-        if events:
-            events[1].record()
 
-    def backward(self, events=None):
+    def _raster_fwd(self, count=None):
+        self.L.gs_rasterize_fwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii,
+                                self.means2d, self.conics, self.opac, self.colors, None, self.image, self.final_T,
+                                self.last, count)
+
+    def _raster_bwd(self):
+        self.L.gs_rasterize_bwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii,
+                                self.means2d, self.conics, self.opac, self.colors, None, self.final_T, self.last,
+                                self.d_image, None, self.d_means2d, self.d_conics, self.d_opac, self.d_colors, None)
+
+    def _post(self):
         L = self.L
-        self.g2d.zero_()
-        if events:
-            events[0].record()
-        L.gs_rasterize_bwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii, self.means2d,
-                           self.conics, self.opac, self.colors, None, self.final_T, self.last, self.d_image, None,
-                           self.d_means2d, self.d_conics, self.d_opac, self.d_colors, None)
-        if events:
-            events[1].record()
         L.gs_sh_eval_bwd(self.cams, self.deg, self.sh, self.means, self.radii, self.d_colors, self.d_sh, self.d_means)
         L.gs_project_bwd(self.cams, self.means, self.quats, self.log_scales, self.logits, self.params, self.radii,
                          self.d_means2d, self.d_conics, self.d_opac, None, self.d_means, self.d_quats,
                          self.d_log_scales, self.d_logits)
+
+    def capture_graphs(self):
+        """Capture the stages around the compositing kernels as CUDA graphs (no host sync inside)."""
+        torch = self.torch
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):  # warm the capture stream once
+            self.g2d.zero_()
+            self._pre()
+            self._post()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        n0 = self.L.gs_kernel_launches()
+        self.g_pre, self.g_post = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_pre):
+            self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
+            self._pre()
+        with torch.cuda.graph(self.g_post):
+            self._post()
+        torch.cuda.synchronize()
+        self.graph_kernels = self.L.gs_kernel_launches() - n0  # kernel nodes of both graphs
+
+    def forward(self, events=None, count=None, graphs=False):
+        if graphs:
+            self.g_pre.replay()
+        else:
+            self._pre()
+        if events:
+            events[0].record()
+        self._raster_fwd(count)
+        if events:
+            events[1].record()
+
+    def backward(self, events=None, graphs=False):
+        if not graphs:
+            self.g2d.zero_()
+        if events:
+            events[0].record()
+        self._raster_bwd()
+        if events:
+            events[1].record()
+        if graphs:
+            self.g_post.replay()
+        else:
+            self._post()
 
     def count_blends(self):
         torch = self.torch
@@ -257,28 +301,36 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    # kernels launched by one step (counted eagerly; graph replays launch the same kernels)
+    n0 = _lib.gs_kernel_launches()
+    kp.forward()
+    kp.backward()
+    torch.cuda.synchronize()
+    launches_per_step = _lib.gs_kernel_launches() - n0
+    graphs = not args.no_graph
+    if graphs:
+        kp.capture_graphs()
     # warm-up
     for _ in range(args.warmup):
-        kp.forward()
-        kp.backward()
+        kp.forward(graphs=graphs)
+        kp.backward(graphs=graphs)
     torch.cuda.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
     fwd_ev = [(ev(), ev()) for _ in range(args.steps)]
     bwd_ev = [(ev(), ev()) for _ in range(args.steps)]
     start, stop = ev(), ev()
-    launches0 = _lib.gs_kernel_launches()
     with ClockSampler(local) as clocks:
         barrier()
         torch.cuda.synchronize()
         start.record()
         for k in range(args.steps):
-            kp.forward(events=fwd_ev[k])
-            kp.backward(events=bwd_ev[k])
+            kp.forward(events=fwd_ev[k], graphs=graphs)
+            kp.backward(events=bwd_ev[k], graphs=graphs)
         stop.record()
         torch.cuda.synchronize()
         barrier()
-    launches = _lib.gs_kernel_launches() - launches0
+    launches = launches_per_step * args.steps
     ms_total = start.elapsed_time(stop)
     ms_step = ms_total / args.steps
     t_fwd_raster = float(np.mean([a.elapsed_time(b) for a, b in fwd_ev]))
@@ -299,7 +351,7 @@ def run_ours(args):
     s2, e2 = ev(), ev()
     s2.record()
     for _ in range(args.steps):
-        kp.forward()
+        kp.forward(graphs=graphs)
     e2.record()
     torch.cuda.synchronize()
     ms_fwd = s2.elapsed_time(e2) / args.steps
@@ -376,7 +428,8 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic (seeded clustered Gaussians; no dataset)",
         "config": {"workload": args.workload, "description": desc, "gaussians": scene.n, "sh_degree": scene.sh_degree,
                    "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": args.tile,
-                   "batch_depth": args.batch, "pixels_per_thread": args.ppt, "intersections_K": kp.K, "blends_per_view": blends,
+                   "batch_depth": args.batch, "pixels_per_thread": args.ppt,
+                   "cuda_graphs": graphs, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
         "ms_per_view_fwd_bwd": ms_step_job, "ms_per_view_fwd": ms_fwd,
         "blends_per_s_fwd": blends / (ms_fwd / 1000.0),
@@ -488,6 +541,7 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch every stage directly instead of graph replays")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -147,7 +147,8 @@ GS_API gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t
 /* rule of gs_project (in float64 from the float32 inputs).                  */
 /*                                                                          */
 /* in : means2d [C,N,2], depths [C,N], radii [C,N]                           */
-/* out: values [K] int32 (flat index c*N + n), tile_ranges [T,2] int32        */
+/* out: values [K] int32 (flat index c*N + n; 16-byte aligned), tile_ranges   */
+/*      [T,2] int32                                                          */
 /*      ([start, end) into values; (0,0) for an empty tile; T = gs_num_tiles),*/
 /*      keys [K] uint64 (optional, NULL to skip), K_out [1] int64 on the      */
 /*      device = the number of pairs K (-1 if an internal bounded wait timed   */

@@ -10,15 +10,16 @@
 //      of at most 7 bits so each digit's run of a sorted block is long).
 // Stability carries the depth order (and the index tie-break) into each tile's list.
 //
-// Each LSD pass is one "onesweep" kernel: the global digit counts of every pass are
-// known up front (a histogram kernel for the depth keys, the emission kernel for the
-// tile keys), a CTA takes the next 4096-item block by ticket, ranks it stably (per-bit
-// ballots inside a warp, warp prefixes across the CTA), publishes its per-digit counts
-// and finds its per-digit offsets by decoupled look-back over the blocks before it, then
-// reorders the block by digit in shared memory so the global stores of each digit's run
-// are contiguous.  A CTA only ever waits on blocks whose tickets came earlier, i.e. on
-// CTAs that are already running, and every wait is bounded: on a timeout the CTA raises
-// an error flag (reported as K_out = -1) instead of waiting forever.
+// Each LSD pass is a reduce-then-scan over blocks of 4096 items: a histogram kernel
+// writes every block's digit counts into a digit-major matrix, two small kernels turn the
+// matrix into each (digit, block) pair's global start, and a persistent scatter kernel
+// ranks each block stably in shared memory (atomic-OR peer masks within a warp, warp
+// prefixes across the CTA), reorders it by digit in place and stores each digit's run
+// contiguously.  The scatter streams its blocks into shared memory with 1-D bulk copies
+// (TMA) double-buffered behind an mbarrier, so the next block is in flight while the
+// current one is ranked.  No CTA waits on another CTA; the only waits are on the CTA's
+// own bulk copies, and they are bounded (a timeout raises an error flag that the call
+// reports as K_out = -1).
 //
 // Emission is balanced by output slot, not by pair: the output is cut into chunks of
 // 1024 slots, a pass over the pairs records which pair starts each chunk, and a CTA
@@ -29,30 +30,26 @@
 //
 // Every kernel reads the data-dependent counts (K) from device memory, so the host never
 // synchronises and the whole call can be captured in a CUDA graph.
+#include <stdlib.h>
+
 #include "gs_internal.cuh"
 
 namespace gs {
 
 constexpr int kRadix = 256;
-constexpr int kMaxPasses = 8;            // 4 depth passes + up to 4 tile passes
-constexpr int kOsThreads = 256;          // onesweep CTA (== kRadix)
-constexpr int kOsIPT = 16;               // items per thread
-constexpr int kOsBlock = kOsThreads * kOsIPT;
+constexpr int kSortThreads = 256;        // histogram CTA (== kRadix)
+constexpr int kSortIPT = 16;             // items per histogram thread
+constexpr int kSortBlock = kSortThreads * kSortIPT;  // items per block of a pass
 constexpr int kChunk = 1024;             // emission chunk (output slots)
 constexpr int kEmitThreads = 256;
 constexpr int kSlotsPerThread = kChunk / kEmitThreads;
-constexpr long long kLookbackSpins = 1ll << 22;
-constexpr unsigned long long kFlagAggregate = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr long long kWaitSpins = 1ll << 22;  // bound on a wait for a bulk copy
 
 // misc region layout (ints)
 constexpr int kMiscNeff = 0;
 constexpr int kMiscErr = 1;
-constexpr int kMiscTickets = 8;                          // [kMaxPasses]
-constexpr int kMiscHist = 64;                            // [kMaxPasses][kRadix] global digit counts
-constexpr int kMiscBase = kMiscHist + kMaxPasses * kRadix;  // [kMaxPasses][kRadix] exclusive digit starts
-constexpr int kMiscInts = kMiscBase + kMaxPasses * kRadix;
+constexpr int kMiscRowsum = 64;                // [kRadix] row sums of the count matrix
+constexpr int kMiscInts = kMiscRowsum + kRadix;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -60,22 +57,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Lanes of the warp (within `valid`) whose digit equals this lane's: one ballot per digit
-// bit, so the cost does not depend on how many distinct digits the warp holds.  Every lane
-// of the warp must call it (lanes outside `valid` pass any digit).
-__device__ __forceinline__ unsigned digit_peers(unsigned d, unsigned valid, int bits) {
-    unsigned p = valid;
-#pragma unroll 1
-    for (int b = 0; b < bits; ++b) {
-        const bool set = (d >> b) & 1u;
-        const unsigned m = __ballot_sync(0xffffffffu, set);
-        p &= set ? m : ~m;
-    }
-    return p;
-}
-
-// Exclusive scan of one int per thread over a CTA of 256 threads; also returns the total.
-__device__ __forceinline__ int block_exclusive_scan(int x, int &total, int *s_tmp /* >= 8 ints */) {
+// Exclusive scan of one int per thread over a CTA of NT threads; also returns the total.
+template <int NT = 256>
+__device__ __forceinline__ int block_exclusive_scan(int x, int &total, int *s_tmp /* >= NT/32 ints */) {
+    constexpr int W = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = x;
 #pragma unroll
@@ -88,21 +73,13 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int &total, int *s_tm
     int wpre = 0;
     total = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < W; ++w) {
         int v = s_tmp[w];
         if (w < warp) wpre += v;
         total += v;
     }
     __syncthreads();
     return wpre + inc - x;
-}
-
-__device__ __forceinline__ unsigned long long load_volatile_u64(const unsigned long long *p) {
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-
-__device__ __forceinline__ void store_volatile_u64(unsigned long long *p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long *>(p) = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -113,27 +90,6 @@ __global__ void zero_ints_kernel(int n, int *__restrict__ p) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) p[t] = 0;
 }
 
-// Zeroes the look-back words of the blocks a pass will use (n from the device when given).
-__global__ void zero_lookback_kernel(const int *__restrict__ n_dev, int n_host, unsigned long long *__restrict__ lb,
-                                     int *__restrict__ ticket) {
-    const int n = n_dev ? *n_dev : n_host;
-    const long long words = (long long)((n + kOsBlock - 1) / kOsBlock) * kRadix;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < words;
-         t += (long long)gridDim.x * blockDim.x)
-        lb[t] = 0ull;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
-}
-
-// Exclusive digit starts of every pass from the global digit counts (one CTA of 256).
-__global__ void digit_base_kernel(const int *__restrict__ hist, int *__restrict__ base, int passes) {
-    __shared__ int s_tmp[8];
-    for (int p = 0; p < passes; ++p) {
-        int tot;
-        const int ex = block_exclusive_scan(hist[p * kRadix + threadIdx.x], tot, s_tmp);
-        base[p * kRadix + threadIdx.x] = ex;
-    }
-}
-
 __global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restrict__ n_eff) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *K_out = 0;
@@ -141,185 +97,321 @@ __global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restri
     }
 }
 
-// Reports a look-back timeout (never expected) through K_out.
+// Reports a timed-out bulk-copy wait (never expected) through K_out.
 __global__ void report_error_kernel(const int *__restrict__ err, long long *__restrict__ K_out) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && *err) *K_out = -1;
 }
 
 // ---------------------------------------------------------------------------
-// stage 1 keys + the digit histograms of all four depth passes
+// stage 1 keys
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) depth_keys_kernel(int CN, const float *__restrict__ depths,
+// Depth key of every (camera, Gaussian) pair.  A pair that touches no pixel (radius 0, or
+// a pixel box that is empty after clipping to the image) gets 0xFFFFFFFF and so sorts
+// after every pair with tiles: in depth order, every pair before the first such key has at
+// least one tile, which the emission relies on.
+__global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __grid_constant__ CamSet cs,
+                                                         const float2 *__restrict__ means2d,
+                                                         const float *__restrict__ depths,
                                                          const int *__restrict__ radii, uint32_t *__restrict__ keys,
-                                                         int *__restrict__ vals, int *__restrict__ hist) {
-    __shared__ int s_h[4][kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    const int n_iter = (CN + stride - 1) / stride;
-    for (int it = 0; it < n_iter; ++it) {
-        const int i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
-        const bool ok = i < CN;
-        uint32_t key = 0xffffffffu;
+                                                         int *__restrict__ vals) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < CN; i += gridDim.x * blockDim.x) {
+        const int r = radii[i];
+        bool ok = r > 0;
         if (ok) {
-            key = radii[i] > 0 ? __float_as_uint(depths[i]) : 0xffffffffu;
-            keys[i] = key;
-            vals[i] = i;
+            const CamDev &cam = cs.cam[i / N];
+            const float2 m = means2d[i];
+            int x0, x1, y0, y1;
+            ok = pixel_box(m.x, m.y, r, cam.W, cam.H, x0, x1, y0, y1);
         }
-        // invisible pairs all carry the same key: count them per warp, not per lane
-        const unsigned inv = __ballot_sync(0xffffffffu, ok && key == 0xffffffffu);
-        if (ok && key != 0xffffffffu) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xffu], 1);
-        }
-        if (lane == 0 && inv) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][0xff], __popc(inv));
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
-        const int v = (&s_h[0][0])[i];
-        if (v) atomicAdd(&hist[i], v);
+        keys[i] = ok ? __float_as_uint(depths[i]) : 0xffffffffu;
+        vals[i] = i;
     }
 }
 
 // ---------------------------------------------------------------------------
-// one stable LSD pass (onesweep)
+// one stable LSD pass as reduce-then-scan: no CTA waits on another
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kOsThreads) onesweep_kernel(
-    const uint32_t *__restrict__ keys_in, const int *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
-    int *__restrict__ vals_out, const int *__restrict__ n_dev, int n_host, int shift, int bits,
-    const int *__restrict__ digit_base, unsigned long long *__restrict__ lookback, int *__restrict__ ticket,
-    int *__restrict__ err) {
-    constexpr int W = kOsThreads / 32;
-    __shared__ int s_block;
-    __shared__ int s_warp[W][kRadix];   // per-warp digit counts, then per-warp offsets inside the block's digit
-    __shared__ int s_local[kRadix];     // start of each digit in the block reordered by digit
-    __shared__ int s_shift[kRadix];     // global position - local position, per digit
-    __shared__ int s_tmp[W];
-    // the reorder buffer; during ranking its first W * kRadix words hold the per-warp lane
-    // masks of each digit (zero between uses)
-    __shared__ uint32_t s_keys[kOsBlock];
-    __shared__ int s_vals[kOsBlock];
-    unsigned(*s_peer)[kRadix] = reinterpret_cast<unsigned(*)[kRadix]>(s_keys);
-    static_assert(W * kRadix <= kOsBlock, "lane masks must fit in the reorder buffer");
+// Digit counts of every kSortBlock-item block: hist[d * cols + b] (digit-major).
+__global__ void __launch_bounds__(kSortThreads) block_hist_kernel(const uint32_t *__restrict__ keys,
+                                                                const int *__restrict__ n_dev, int n_host, int shift,
+                                                                int bits, int cols, int *__restrict__ hist) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ int s_h[W][kRadix];
+    const int warp = threadIdx.x >> 5;
+    const int n = n_dev ? *n_dev : n_host;
+    const int b = blockIdx.x;
+    const int t0 = b * kSortBlock;
+    if (t0 >= n) return;  // uniform
+    for (int i = threadIdx.x; i < W * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned mask = (1u << bits) - 1u;
+    const int end = min(n, t0 + kSortBlock);
+    uint4 q[kSortIPT / 4];  // all loads in flight before the first atomic
+#pragma unroll
+    for (int r = 0; r < kSortIPT / 4; ++r) {
+        const int i0 = t0 + (r * kSortThreads + threadIdx.x) * 4;  // 16-byte aligned: keys are 256-byte aligned
+        if (i0 + 3 < end) {
+            q[r] = *reinterpret_cast<const uint4 *>(keys + i0);
+        } else {
+            q[r].x = i0 + 0 < end ? keys[i0 + 0] : 0u;
+            q[r].y = i0 + 1 < end ? keys[i0 + 1] : 0u;
+            q[r].z = i0 + 2 < end ? keys[i0 + 2] : 0u;
+            q[r].w = i0 + 3 < end ? keys[i0 + 3] : 0u;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kSortIPT / 4; ++r) {
+        const int i0 = t0 + (r * kSortThreads + threadIdx.x) * 4;
+        if (i0 + 0 < end) atomicAdd(&s_h[warp][(q[r].x >> shift) & mask], 1);
+        if (i0 + 1 < end) atomicAdd(&s_h[warp][(q[r].y >> shift) & mask], 1);
+        if (i0 + 2 < end) atomicAdd(&s_h[warp][(q[r].z >> shift) & mask], 1);
+        if (i0 + 3 < end) atomicAdd(&s_h[warp][(q[r].w >> shift) & mask], 1);
+    }
+    __syncthreads();
+    const int d = threadIdx.x;  // kSortThreads == kRadix
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += s_h[w][d];
+    hist[(size_t)d * cols + b] = c;
+}
+
+// Row sums of the digit-major count matrix over its first nb = ceil(n / kSortBlock) columns.
+__global__ void __launch_bounds__(kSortThreads) hist_rowsum_kernel(const int *__restrict__ n_dev, int n_host, int cols,
+                                                                 const int *__restrict__ hist, int *__restrict__ rowsum) {
+    __shared__ int s_tmp[8];
+    const int n = n_dev ? *n_dev : n_host;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int *row = hist + (size_t)blockIdx.x * cols;
+    int s = 0;
+    for (int b = threadIdx.x; b < nb; b += kSortThreads) s += row[b];
+    int tot;
+    block_exclusive_scan(s, tot, s_tmp);
+    if (threadIdx.x == 0) rowsum[blockIdx.x] = tot;
+}
+
+// hist[d * cols + b] <- global start of digit d for block b:
+// sum_{d' < d} rowsum[d'] + sum_{b' < b} hist[d * cols + b'].
+__global__ void __launch_bounds__(kSortThreads) hist_scan_kernel(const int *__restrict__ n_dev, int n_host, int cols,
+                                                               const int *__restrict__ rowsum, int *__restrict__ hist) {
+    __shared__ int s_tmp[8];
+    const int n = n_dev ? *n_dev : n_host;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int d = blockIdx.x;
+    int base;
+    block_exclusive_scan(threadIdx.x < d ? rowsum[threadIdx.x] : 0, base, s_tmp);
+    int *row = hist + (size_t)d * cols;
+    // each thread scans a contiguous segment of the row
+    const int seg = (nb + kSortThreads - 1) / kSortThreads;
+    const int b0 = threadIdx.x * seg, b1 = min(nb, b0 + seg);
+    int s = 0;
+    for (int b = b0; b < b1; ++b) s += row[b];
+    int tot;
+    int run = base + block_exclusive_scan(s, tot, s_tmp);
+    for (int b = b0; b < b1; ++b) {
+        const int v = row[b];
+        row[b] = run;
+        run += v;
+    }
+}
+
+// --- bulk copies (TMA, 1-D) into shared memory with mbarrier completion -------------
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a bulk copy; false (and the error flag raised) when the copy never lands.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, int *err) {
+    for (long long it = 0; it < kWaitSpins; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+constexpr int kTmaThreads = 512;
+constexpr int kTmaWarps = kTmaThreads / 32;
+constexpr int kTmaIPT = kSortBlock / kTmaThreads;  // items per scatter thread
+constexpr size_t kTmaSmem = 2ull * kSortBlock * 8          // double-buffered keys + values (reordered in place)
+                            + 2ull * kTmaWarps * kRadix * 4  // per-warp digit counts, per-warp peer masks
+                            + 2ull * kRadix * 4              // local starts, shifts
+                            + 128;                           // barriers, scratch
+
+// Stable scatter of one pass by persistent CTAs (two per SM): the next block's keys and
+// values are bulk-copied into the other shared-memory buffer while the current block is
+// ranked and stored, so DRAM latency hides behind the ranking instead of stalling it.
+// The ranked block is reordered by digit into its own input buffer (the items are held in
+// registers across the barrier), so each CTA needs no separate reorder buffer.
+__global__ void __launch_bounds__(kTmaThreads, 2) scatter_tma_kernel(const uint32_t *__restrict__ keys_in,
+                                                                     const int *__restrict__ vals_in,
+                                                                     uint32_t *__restrict__ keys_out,
+                                                                     int *__restrict__ vals_out,
+                                                                     const int *__restrict__ n_dev, int n_host,
+                                                                     int shift, int bits, int cols,
+                                                                     const int *__restrict__ hist,
+                                                                     int *__restrict__ err) {
+    constexpr int W = kTmaWarps;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *s_in_k = reinterpret_cast<uint32_t *>(smem);              // [2][kSortBlock]
+    int *s_in_v = reinterpret_cast<int *>(s_in_k + 2 * kSortBlock);      // [2][kSortBlock]
+    int(*s_warp)[kRadix] = reinterpret_cast<int(*)[kRadix]>(s_in_v + 2 * kSortBlock);
+    unsigned(*s_peer)[kRadix] = reinterpret_cast<unsigned(*)[kRadix]>(&s_warp[W][0]);
+    int *s_local = reinterpret_cast<int *>(&s_peer[W][0]);
+    int *s_shift = s_local + kRadix;
+    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(s_shift + kRadix);  // [2]
+    int *s_tmp = reinterpret_cast<int *>(s_bar + 2);                                       // [W]
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = n_dev ? *n_dev : n_host;
-    const int nblocks = (n + kOsBlock - 1) / kOsBlock;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
     const unsigned mask = (1u << bits) - 1u;
-    if (threadIdx.x == 0) s_block = atomicAdd(ticket, 1);
-    for (int i = threadIdx.x; i < W * kRadix; i += kOsThreads) {
-        (&s_warp[0][0])[i] = 0;
-        (&s_peer[0][0])[i] = 0u;
+    if (blockIdx.x >= nb) return;  // uniform
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int blk = s_block;
-    if (blk >= nblocks) return;  // uniform: the grid is sized for the capacity, n may be smaller
-    const int t0 = blk * kOsBlock;
-    const int items = min(kOsBlock, n - t0);
-
-    // load (warp-striped: warp w owns a contiguous run, lanes in order) and rank
-    const int wbase = t0 + warp * 32 * kOsIPT;
-    uint32_t k[kOsIPT];
-    int v[kOsIPT], rank[kOsIPT];
-    unsigned dg[kOsIPT];
-#pragma unroll
-    for (int j = 0; j < kOsIPT; ++j) {
-        const int i = wbase + j * 32 + lane;
-        const bool ok = i < n;
-        k[j] = ok ? keys_in[i] : 0u;
-        v[j] = ok ? vals_in[i] : 0;
-        dg[j] = ok ? ((k[j] >> shift) & mask) : 0xffffffffu;
-    }
-    // stable rank inside the warp: lanes holding the same digit find each other by OR-ing
-    // their lane bit into the warp's word for that digit, the lowest of them advances the
-    // warp's count and clears the word
+    // issue the bulk copies of block `blk` into buffer `buf` (thread 0); the ragged tail of
+    // the last block (fewer than 4 items past a 16-byte boundary) is loaded after the wait
+    auto issue = [&](int blk, int buf) {
+        const int t0 = blk * kSortBlock;
+        const int items = min(kSortBlock, n - t0);
+        const unsigned bytes = (unsigned)(items & ~3) * 4u;
+        mbar_expect_tx(&s_bar[buf], 2u * bytes);
+        if (bytes) {
+            bulk_g2s(s_in_k + buf * kSortBlock, keys_in + t0, bytes, &s_bar[buf]);
+            bulk_g2s(s_in_v + buf * kSortBlock, vals_in + t0, bytes, &s_bar[buf]);
+        }
+    };
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
     const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < kOsIPT; ++j) {
-        const bool ok = dg[j] != 0xffffffffu;
-        const unsigned d = ok ? dg[j] : 0u;
-        if (ok) atomicOr(&s_peer[warp][d], 1u << lane);
-        __syncwarp();
-        const unsigned peers = ok ? s_peer[warp][d] : 0u;
-        const int before = ok ? s_warp[warp][d] : 0;
-        __syncwarp();
-        if (ok && (__ffs(peers) - 1) == lane) {
-            s_warp[warp][d] = before + __popc(peers);
-            s_peer[warp][d] = 0u;
+    int it = 0;
+    for (int blk = blockIdx.x; blk < nb; blk += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int t0 = blk * kSortBlock;
+        const int items = min(kSortBlock, n - t0);
+        // prefetch the next block into the other buffer: the previous iteration ended with a
+        // proxy fence by every thread and a CTA barrier after its last access to that buffer
+        const int next = blk + gridDim.x;
+        if (threadIdx.x == 0 && next < nb) issue(next, buf ^ 1);
+        for (int i = threadIdx.x; i < W * kRadix; i += kTmaThreads) {
+            (&s_warp[0][0])[i] = 0;
+            (&s_peer[0][0])[i] = 0u;
         }
-        rank[j] = before + __popc(peers & lt);
-        __syncwarp();
-    }
-    __syncthreads();
-
-    // per digit: block count, publish, look back, global start
-    {
-        const int d = threadIdx.x;  // kOsThreads == kRadix
-        int run = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const int c = s_warp[w][d];
-            s_warp[w][d] = run;
-            run += c;
+        const bool landed = mbar_wait_bounded(&s_bar[buf], (unsigned)(it >> 1) & 1u, err);
+        uint32_t *ik = s_in_k + buf * kSortBlock;
+        int *iv = s_in_v + buf * kSortBlock;
+        // ragged tail (< 4 items) with plain loads
+        const int body = items & ~3;
+        if (threadIdx.x < items - body) {
+            ik[body + threadIdx.x] = keys_in[t0 + body + threadIdx.x];
+            iv[body + threadIdx.x] = vals_in[t0 + body + threadIdx.x];
         }
-        long long excl = 0;
-        if (d <= (int)mask) {
-            unsigned long long *mine = lookback + (size_t)blk * kRadix + d;
-            if (blk == 0) {
-                store_volatile_u64(mine, kFlagPrefix | (unsigned long long)run);
-            } else {
-                store_volatile_u64(mine, kFlagAggregate | (unsigned long long)run);
-                // sum the counts of the blocks before, back to the nearest one whose inclusive
-                // prefix is known; a block not yet published is waited for (bounded)
-                long long spins = 0;
-                for (int b = blk - 1; b >= 0; --b) {
-                    const unsigned long long *other = lookback + (size_t)b * kRadix + d;
-                    unsigned long long w = load_volatile_u64(other);
-                    while ((w & (kFlagAggregate | kFlagPrefix)) == 0ull) {
-                        if (++spins > kLookbackSpins) {
-                            atomicExch(err, 1);
-                            break;
-                        }
-                        __nanosleep(20);
-                        w = load_volatile_u64(other);
-                    }
-                    excl += (long long)(w & kValueMask);
-                    if ((w & kFlagPrefix) || spins > kLookbackSpins) break;
+        if (!__syncthreads_and(landed)) {
+            // a copy never arrived: give up on this CTA's remaining blocks (the error flag is set);
+            // wait, bounded, for the copy still in flight before shared memory is released
+            if (threadIdx.x == 0 && next < nb) mbar_wait_bounded(&s_bar[buf ^ 1], (unsigned)((it + 1) >> 1) & 1u, err);
+            return;
+        }
+        // stable rank inside each warp (warp w owns items [w*32*kTmaIPT, (w+1)*32*kTmaIPT))
+        uint32_t kk[kTmaIPT];
+        int vv[kTmaIPT], rank[kTmaIPT];
+#pragma unroll
+        for (int j = 0; j < kTmaIPT; ++j) {
+            const int li = warp * 32 * kTmaIPT + j * 32 + lane;
+            const bool ok = li < items;
+            kk[j] = ok ? ik[li] : 0u;
+            vv[j] = ok ? iv[li] : 0;
+            const unsigned d = ok ? ((kk[j] >> shift) & mask) : 0u;
+            if (ok) atomicOr(&s_peer[warp][d], 1u << lane);
+            __syncwarp();
+            const unsigned peers = ok ? s_peer[warp][d] : 0u;
+            const int before = ok ? s_warp[warp][d] : 0;
+            __syncwarp();
+            if (ok && (__ffs(peers) - 1) == lane) {
+                s_warp[warp][d] = before + __popc(peers);
+                s_peer[warp][d] = 0u;
+            }
+            rank[j] = before + __popc(peers & lt);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            int run = 0;
+            if (d < kRadix) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const int c = s_warp[w][d];
+                    s_warp[w][d] = run;
+                    run += c;
                 }
-                store_volatile_u64(mine, kFlagPrefix | (unsigned long long)(excl + run));
+            }
+            int tot;
+            const int local = block_exclusive_scan<kTmaThreads>(run, tot, s_tmp);
+            if (d < kRadix) {
+                s_local[d] = local;
+                s_shift[d] = hist[(size_t)d * cols + blk] - local;
             }
         }
-        int tot;
-        const int local = block_exclusive_scan(run, tot, s_tmp);
-        s_local[d] = local;
-        s_shift[d] = (int)(digit_base[d] + excl) - local;
-    }
-    __syncthreads();
-    // reorder the block by digit in shared memory
+        __syncthreads();
+        // every item of the block is in registers: reorder by digit into the input buffer
 #pragma unroll
-    for (int j = 0; j < kOsIPT; ++j) {
-        if (dg[j] != 0xffffffffu) {
-            const int lp = s_local[dg[j]] + s_warp[warp][dg[j]] + rank[j];
-            if ((unsigned)lp < (unsigned)kOsBlock) {  // holds by construction
-                s_keys[lp] = k[j];
-                s_vals[lp] = v[j];
+        for (int j = 0; j < kTmaIPT; ++j) {
+            const int li = warp * 32 * kTmaIPT + j * 32 + lane;
+            if (li < items) {
+                const unsigned d = (kk[j] >> shift) & mask;
+                const int lp = s_local[d] + s_warp[warp][d] + rank[j];
+                if ((unsigned)lp < (unsigned)kSortBlock) {  // holds by construction
+                    ik[lp] = kk[j];
+                    iv[lp] = vv[j];
+                }
             }
         }
-    }
-    __syncthreads();
-    // contiguous stores of every digit's run
-    for (int i = threadIdx.x; i < items; i += kOsThreads) {
-        const uint32_t kk = s_keys[i];
-        const int pos = i + s_shift[(kk >> shift) & mask];
-        if ((unsigned)pos < (unsigned)n) {  // holds by construction; guards the scatter
-            keys_out[pos] = kk;
-            vals_out[pos] = s_vals[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < items; i += kTmaThreads) {
+            const uint32_t k = ik[i];
+            const int pos = i + s_shift[(k >> shift) & mask];
+            if ((unsigned)pos < (unsigned)n) {  // holds by construction; guards the scatter
+                keys_out[pos] = k;
+                vals_out[pos] = iv[i];
+            }
         }
+        // order this iteration's generic-proxy accesses to the buffer before the bulk copy
+        // that refills it two iterations on
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
     }
 }
 
@@ -442,46 +534,44 @@ __global__ void __launch_bounds__(256) offsets_kernel(int CN, const int *__restr
     }
 }
 
-// Balanced emission of (tile id, pair index) in depth order into [0, n_eff), plus the global
-// digit counts of the tile passes (digit p = bits [digit_bits p, digit_bits (p+1)) of the id).
+// Balanced emission of (tile id, pair index) in depth order into [0, n_eff).
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
     int CN, const __grid_constant__ CamSet cs, const int *__restrict__ order, const int2 *__restrict__ rects,
     const long long *__restrict__ offsets, const int *__restrict__ chunk_start, const int *__restrict__ n_eff,
-    uint32_t *__restrict__ tkeys, int *__restrict__ tvals, int tile_passes, int digit_bits, int *__restrict__ hist) {
-    constexpr int P = kChunk;  // at most one pair per slot: every pair in the chunk has >= 1 tile
+    uint32_t *__restrict__ tkeys, int *__restrict__ tvals) {
+    // at most one pair per slot: every pair before the first tile-less one has >= 1 tile, and
+    // tile-less pairs (offset n_eff or beyond) are never inside a chunk
+    constexpr int P = kChunk;
     __shared__ int s_off[P + 1];  // first slot of each pair, relative to the chunk
     __shared__ int s_xy[P];       // tx0 | ty0 << 16
     __shared__ int s_wc[P];       // rectangle width | camera << 16
     __shared__ int s_id[P];
     __shared__ uint32_t s_key[kChunk + kChunk / 32];
     __shared__ int s_val[kChunk + kChunk / 32];
-    __shared__ int s_h[4][kRadix];
-    __shared__ int s_np;
-    for (int i = threadIdx.x; i < 4 * kRadix; i += kEmitThreads) (&s_h[0][0])[i] = 0;
     const int n = *n_eff;
     const int nchunks = (n + kChunk - 1) / kChunk;
-    const unsigned dmask = (1u << digit_bits) - 1u;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {  // normally one chunk per CTA
         const long long k0 = (long long)ch * kChunk;
         const int len = (int)min((long long)kChunk, n - k0);
         const int j0 = chunk_start[ch];
-        if (threadIdx.x == 0) s_np = 0;
-        __syncthreads();
         // the pairs of this chunk: j0, j0 + 1, ... while their first slot is inside the chunk
-        for (int s = threadIdx.x; s < P; s += kEmitThreads) {
+        // (offsets are non-decreasing, so they form a prefix and a count gives their number)
+        int np = 0;
+#pragma unroll
+        for (int s0 = 0; s0 < P; s0 += kEmitThreads) {
+            const int s = s0 + threadIdx.x;
             const int j = j0 + s;
             const long long off = (j < CN) ? offsets[j] : (1ll << 62);
-            if (off < k0 + len) {
+            const bool in = off < k0 + len;
+            if (in) {
                 const int2 rc = rects[j];
                 s_off[s] = (int)(off - k0);  // negative for the pair that straddles into the chunk
                 s_xy[s] = rc.x;
                 s_wc[s] = rc.y;
                 s_id[s] = order[j];
-                atomicMax(&s_np, s + 1);
             }
+            np += __syncthreads_count(in);
         }
-        __syncthreads();
-        const int np = s_np;
         if (threadIdx.x == 0) s_off[np] = 1 << 30;
         __syncthreads();
         // each thread fills kSlotsPerThread consecutive slots
@@ -507,9 +597,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
                                                  (kk - ky * w));
                 s_key[q + (q >> 5)] = tile;  // padded: one bank shift per 32 slots
                 s_val[q + (q >> 5)] = s_id[p];
-#pragma unroll
-                for (int pass = 0; pass < 4; ++pass)
-                    if (pass < tile_passes) atomicAdd(&s_h[pass][(tile >> (digit_bits * pass)) & dmask], 1);
             }
         }
         __syncthreads();
@@ -518,11 +605,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
             tvals[k0 + q] = s_val[q + (q >> 5)];
         }
         __syncthreads();
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < tile_passes * kRadix; i += kEmitThreads) {
-        const int v = (&s_h[0][0])[i];
-        if (v) atomicAdd(&hist[i], v);
     }
 }
 
@@ -586,7 +668,7 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, int G) {
     };
     const long long cnb = (CN + 255) / 256;
     const long long max_items = CN > Kcap ? CN : Kcap;
-    const long long os_blocks = (max_items + kOsBlock - 1) / kOsBlock;
+    const long long cols = (max_items + kSortBlock - 1) / kSortBlock;
     L.dk0 = take(CN * 4);
     L.dk1 = take(CN * 4);
     L.dv0 = take(CN * 4);
@@ -597,7 +679,7 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, int G) {
     L.chunk_start = take(((Kcap + kChunk - 1) / kChunk + 1) * 4);
     L.partials = take((size_t)(cnb + 1) * 8);
     L.misc = take((size_t)kMiscInts * 4);
-    L.lookback = take((size_t)(os_blocks > 0 ? os_blocks : 1) * kRadix * 8);
+    L.matrix = take((size_t)(cols > 0 ? cols : 1) * kRadix * 4);
     L.tk0 = take(Kcap * 4);
     L.tk1 = take(Kcap * 4);
     L.tvB = take(Kcap * 4);
@@ -605,17 +687,25 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, int G) {
     return L;
 }
 
-static cudaError_t onesweep_pass(const uint32_t *kin, const int *vin, uint32_t *kout, int *vout, const int *n_dev,
-                                 int n_host, long long max_items, int shift, int bits, const int *base,
-                                 unsigned long long *lookback, int *ticket, int *err, int G, cudaStream_t st) {
-    zero_lookback_kernel<<<G, 256, 0, st>>>(n_dev, n_host, lookback, ticket);
+// One stable LSD pass by reduce-then-scan over blocks of kSortBlock items.
+static cudaError_t rts_pass(const uint32_t *kin, const int *vin, uint32_t *kout, int *vout, const int *n_dev,
+                            int n_host, long long max_items, int shift, int bits, int *matrix, int *rowsum, int *err,
+                            cudaStream_t st) {
+    const int cols = (int)((max_items + kSortBlock - 1) / kSortBlock);
+    if (cols <= 0) return cudaSuccess;
+    block_hist_kernel<<<cols, kSortThreads, 0, st>>>(kin, n_dev, n_host, shift, bits, cols, matrix);
     note_launch();
-    const long long blocks = (max_items + kOsBlock - 1) / kOsBlock;
-    if (blocks > 0) {
-        onesweep_kernel<<<(unsigned)blocks, kOsThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, bits,
-                                                                 base, lookback, ticket, err);
-        note_launch();
-    }
+    hist_rowsum_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, matrix, rowsum);
+    note_launch();
+    hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+    note_launch();
+    cudaError_t e =
+        cudaFuncSetAttribute(scatter_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+    if (e != cudaSuccess) return e;
+    const int persistent = 2 * sort_grid_blocks() / 4;  // two CTAs per SM
+    scatter_tma_kernel<<<cols < persistent ? cols : persistent, kTmaThreads, kTmaSmem, st>>>(
+        kin, vin, kout, vout, n_dev, n_host, shift, bits, cols, matrix, err);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -637,10 +727,8 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     int *misc = (int *)(w + L.misc);
     int *n_eff = misc + kMiscNeff;
     int *err = misc + kMiscErr;
-    int *tickets = misc + kMiscTickets;
-    int *hist = misc + kMiscHist;
-    int *base = misc + kMiscBase;
-    unsigned long long *lookback = (unsigned long long *)(w + L.lookback);
+    int *matrix = (int *)(w + L.matrix);
+    int *rowsum = misc + kMiscRowsum;
     uint32_t *tk0 = (uint32_t *)(w + L.tk0), *tk1 = (uint32_t *)(w + L.tk1);
     int *tvB = (int *)(w + L.tvB);
 
@@ -656,21 +744,19 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     const int bits = tile_bits(T);
     const int tpasses = (bits + 6) / 7;                // passes of at most 7 bits
     const int tdigit = (bits + tpasses - 1) / tpasses;  // equal digit widths
-    // counters, histograms, error flag
+    // n_eff, error flag
     zero_ints_kernel<<<(kMiscInts + 255) / 256, 256, 0, st>>>(kMiscInts, misc);
     note_launch();
     // stage 1: depth order of all (camera, Gaussian) pairs
     const int eb = (cn + 255) / 256;
-    depth_keys_kernel<<<G, 256, 0, st>>>(cn, depths, radii, dk0, dv0, hist);
-    note_launch();
-    digit_base_kernel<<<1, kRadix, 0, st>>>(hist, base, 4);
+    depth_keys_kernel<<<G, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < 4; ++pass) {
         const bool even = (pass % 2) == 0;
-        e = onesweep_pass(even ? dk0 : dk1, even ? dv0 : dv1, even ? dk1 : dk0, even ? dv1 : dv0, nullptr, cn, cn,
-                          8 * pass, 8, base + pass * kRadix, lookback, tickets + pass, err, G, st);
+        e = rts_pass(even ? dk0 : dk1, even ? dv0 : dv1, even ? dk1 : dk0, even ? dv1 : dv0, nullptr, cn, cn, 8 * pass,
+                     8, matrix, rowsum, err, st);
         if (e != cudaSuccess) return e;
     }
     const int *order = dv0;  // after 4 passes the sorted pairs are back in (dk0, dv0)
@@ -685,22 +771,17 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     uint32_t *kA = tk0, *kB = tk1;
     int *vA = (tpasses % 2 == 0) ? values : tvB;
     int *vB = (tpasses % 2 == 0) ? tvB : values;
-    int *thist = hist + 4 * kRadix;
-    int *tbase = base + 4 * kRadix;
     if (Kcap > 0) {
         const long long chunks = (Kcap + kChunk - 1) / kChunk;
         const long long emit_blocks = chunks < 2ll * G ? chunks : 2ll * G;  // persistent: 8 CTAs per SM
         emit_kernel<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(cn, cs, order, rects, offsets, chunk_start, n_eff,
-                                                                    kA, vA, tpasses, tdigit, thist);
+                                                                    kA, vA);
         note_launch();
     }
-    digit_base_kernel<<<1, kRadix, 0, st>>>(thist, tbase, tpasses);
-    note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < tpasses; ++pass) {
-        e = onesweep_pass(kA, vA, kB, vB, n_eff, 0, Kcap, tdigit * pass, tdigit, tbase + pass * kRadix, lookback,
-                          tickets + 4 + pass, err, G, st);
+        e = rts_pass(kA, vA, kB, vB, n_eff, 0, Kcap, tdigit * pass, tdigit, matrix, rowsum, err, st);
         if (e != cudaSuccess) return e;
         uint32_t *tk = kA;
         kA = kB;

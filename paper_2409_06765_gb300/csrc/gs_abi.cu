@@ -244,6 +244,7 @@ gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs
     }
     if (K_capacity > 0) GS_NONNULL(values);
     if (!aligned(workspace, 256)) return fail_arg("workspace must be 256-byte aligned");
+    if (values && !aligned(values, 16)) return fail_arg("values must be 16-byte aligned");
     if (N > 0 && !aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     if (keys && !aligned(keys, 8)) return fail_arg("keys must be 8-byte aligned");
