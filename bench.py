@@ -59,8 +59,9 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms; summary() keeps the samples
+    whose timestamps fall inside the timed region (mark() brackets it)."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -68,6 +69,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.window = None
 
     def __enter__(self):
         try:
@@ -75,9 +77,15 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
                                          stderr=subprocess.DEVNULL)
+            t_end = time.time() + 5.0  # wait for the first sample so the timed region is covered
+            while time.time() < t_end and os.path.getsize(self.file.name) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
         return self
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -88,6 +96,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        import datetime
         if self.proc is None or self.file is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.file.flush()
@@ -95,9 +104,20 @@ class ClockSampler:
         with open(self.file.name) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append((ts, parts[1:]))
         os.unlink(self.file.name)
+        inside = rows
+        scope = "whole run"
+        if self.window and any(ts is not None for ts, _ in rows):
+            sel = [(ts, r) for ts, r in rows if ts is not None and self.window[0] - 0.1 <= ts <= self.window[1] + 0.1]
+            if sel:
+                inside, scope = sel, "timed region"
+        rows = [r for _, r in inside]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
 
@@ -111,7 +131,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "power_w_max": max((num(r[3]) or 0) for r in rows)}
+                "reasons": reasons, "samples": len(rows), "scope": scope,
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
 
 
 def build_workload(name: str, rank: int):
@@ -135,151 +156,11 @@ def build_workload(name: str, rank: int):
     return scene, cams, desc
 
 
-class KernelPath:
-    """Preallocated buffers and one fwd+bwd step issued through the C ABI (no host sync)."""
-
-    def __init__(self, scene, cams, tile=16, batch=256, ppt=0):
-        import torch
-        from paper_2409_06765_gb300 import _lib
-        self.torch, self.L = torch, _lib
-        dev = "cuda"
-        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
-        self.means, self.quats, self.log_scales = t(scene.means), t(scene.quats), t(scene.log_scales)
-        self.logits, self.sh, self.deg = t(scene.opacity_logits), t(scene.sh), scene.sh_degree
-        self.cams = _lib.CameraArray(cams)
-        self.params = _lib.make_params(tile=tile, batch_depth=batch, pixels_per_thread=ppt)
-        C, N = self.cams.C, scene.n
-        self.C, self.N = C, N
-        f = lambda *s: torch.empty(*s, device=dev)
-        i = lambda *s: torch.empty(*s, dtype=torch.int32, device=dev)
-        self.means2d, self.depths, self.conics = f(C, N, 2), f(C, N), f(C, N, 3)
-        self.radii, self.tiles, self.opac, self.colors = i(C, N), i(C, N), f(C, N), f(C, N, 3)
-        P = self.cams.num_pixels
-        self.P = P
-        self.image, self.final_T, self.last = f(P, 3), f(P), i(P)
-        self.ranges = i(self.cams.num_tiles(tile), 2)
-        self.K_out = torch.zeros(1, dtype=torch.int64, device=dev)
-        # 2D gradient buffers in one allocation so that one memset clears them
-        self.g2d = torch.zeros(C * N * 9, device=dev)
-        o = 0
-        self.d_means2d = self.g2d[o:o + C * N * 2].view(C, N, 2); o += C * N * 2
-        self.d_conics = self.g2d[o:o + C * N * 3].view(C, N, 3); o += C * N * 3
-        self.d_opac = self.g2d[o:o + C * N].view(C, N); o += C * N
-        self.d_colors = self.g2d[o:o + C * N * 3].view(C, N, 3)
-        self.d_sh, self.d_means = torch.empty_like(self.sh), f(N, 3)
-        self.d_quats, self.d_log_scales, self.d_logits = f(N, 4), f(N, 3), f(N)
-        self.d_image = torch.zeros(P, 3, device=dev)
-        # size the intersection buffers from one real frame (K is data dependent)
-        self.capacity = 1 << 20
-        self._alloc_sort()
-        self.forward()
-        torch.cuda.synchronize()
-        K = int(self.K_out.item())
-        if K > self.capacity:
-            self.capacity = int(K * 1.1) + 1024
-            self._alloc_sort()
-            self.forward()
-            torch.cuda.synchronize()
-        self.K = int(self.K_out.item())
-        if not 0 <= self.K <= self.capacity:
-            raise RuntimeError(f"bin/sort returned K = {self.K} for capacity {self.capacity}")
-
-    def _alloc_sort(self):
-        torch = self.torch
-        self.values = torch.empty(self.capacity, dtype=torch.int32, device="cuda")
-        nbytes = self.L.gs_tile_bin_sort_workspace(self.cams, self.N, self.params, self.capacity)
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-
-    def set_loss_gradient(self, target):
-        """Upstream gradient of the mean L1 loss at the current image (held fixed while timing)."""
-        torch = self.torch
-        self.d_image.copy_(torch.sign(self.image - target) / self.image.numel())
-
-    # The step in four parts: the two compositing kernels are launched directly (bracketed by
-    # CUDA events for the roofline); the stages before and after them, some twenty short
-    # launches, can be replayed as CUDA graphs (capture_graphs) to cut launch gaps.
-    def _pre(self):
-        L = self.L
-        L.gs_project(self.cams, self.means, self.quats, self.log_scales, self.logits, self.params, self.means2d,
-                     self.depths, self.conics, self.radii, self.tiles, self.opac)
-        L.gs_sh_eval(self.cams, self.deg, self.sh, self.means, self.radii, self.colors)
-        L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity,
-                           None, self.values, self.ranges, self.K_out, self.workspace)
-
-    def _raster_fwd(self, count=None):
-        self.L.gs_rasterize_fwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii,
-                                self.means2d, self.conics, self.opac, self.colors, None, self.image, self.final_T,
-                                self.last, count)
-
-    def _raster_bwd(self):
-        self.L.gs_rasterize_bwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii,
-                                self.means2d, self.conics, self.opac, self.colors, None, self.final_T, self.last,
-                                self.d_image, None, self.d_means2d, self.d_conics, self.d_opac, self.d_colors, None)
-
-    def _post(self):
-        L = self.L
-        L.gs_sh_eval_bwd(self.cams, self.deg, self.sh, self.means, self.radii, self.d_colors, self.d_sh, self.d_means)
-        L.gs_project_bwd(self.cams, self.means, self.quats, self.log_scales, self.logits, self.params, self.radii,
-                         self.d_means2d, self.d_conics, self.d_opac, None, self.d_means, self.d_quats,
-                         self.d_log_scales, self.d_logits)
-
-    def capture_graphs(self):
-        """Capture the stages around the compositing kernels as CUDA graphs (no host sync inside)."""
-        torch = self.torch
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):  # warm the capture stream once
-            self.g2d.zero_()
-            self._pre()
-            self._post()
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        n0 = self.L.gs_kernel_launches()
-        self.g_pre, self.g_post = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.g_pre):
-            self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
-            self._pre()
-        with torch.cuda.graph(self.g_post):
-            self._post()
-        torch.cuda.synchronize()
-        self.graph_kernels = self.L.gs_kernel_launches() - n0  # kernel nodes of both graphs
-
-    def forward(self, events=None, count=None, graphs=False):
-        if graphs:
-            self.g_pre.replay()
-        else:
-            self._pre()
-        if events:
-            events[0].record()
-        self._raster_fwd(count)
-        if events:
-            events[1].record()
-
-    def backward(self, events=None, graphs=False):
-        if not graphs:
-            self.g2d.zero_()
-        if events:
-            events[0].record()
-        self._raster_bwd()
-        if events:
-            events[1].record()
-        if graphs:
-            self.g_post.replay()
-        else:
-            self._post()
-
-    def count_blends(self):
-        torch = self.torch
-        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        self.forward(count=cnt)
-        torch.cuda.synchronize()
-        return int(cnt.item())
-
-
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2409_06765_gb300 import _lib, raster
+    from paper_2409_06765_gb300.pipeline import DeviceScene, FramePipeline, Schedule
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,12 +171,15 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     scene, cams, desc = build_workload(args.workload, rank)
-    kp = KernelPath(scene, cams, tile=args.tile, batch=args.batch, ppt=args.ppt)
+    dscene = DeviceScene.from_host(scene)
+    sched = Schedule(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
+                     tile_order=not args.no_tile_order)
+    kp = FramePipeline(dscene, cams, sched)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
     target = torch.as_tensor(target_np, device="cuda")
+    blends = kp.count_blends()  # also renders the first frame
     kp.set_loss_gradient(target)
-    blends = kp.count_blends()
 
     def barrier():
         if world > 1:
@@ -323,12 +207,14 @@ def run_ours(args):
     with ClockSampler(local) as clocks:
         barrier()
         torch.cuda.synchronize()
+        wall0 = time.time()
         start.record()
         for k in range(args.steps):
             kp.forward(events=fwd_ev[k], graphs=graphs)
             kp.backward(events=bwd_ev[k], graphs=graphs)
         stop.record()
         torch.cuda.synchronize()
+        clocks.mark(wall0, time.time())
         barrier()
     launches = launches_per_step * args.steps
     ms_total = start.elapsed_time(stop)
@@ -360,9 +246,10 @@ def run_ours(args):
     # loss D2H every step, Gaussians resident (they are the trainable parameters)
     e2e = None
     if not args.no_e2e:
-        leaves = [x.detach().clone().requires_grad_(True) for x in (kp.means, kp.quats, kp.log_scales, kp.logits,
-                                                                     kp.sh)]
-        settings = raster.RasterSettings(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt)
+        leaves = [x.detach().clone().requires_grad_(True) for x in (dscene.means, dscene.quats, dscene.log_scales,
+                                                                     dscene.opacity_logits, dscene.sh)]
+        settings = raster.RasterSettings(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
+                                         tile_schedule=not args.no_tile_order)
         state = raster.RasterState()
         host_target = torch.as_tensor(target_np).pin_memory()
         dev_target = torch.empty_like(target)
@@ -398,6 +285,9 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     alu_peak = sm_count * 128 * f_max  # FP32 lane operations / s at the maximum SM clock
+    probe = measure_alu_peaks(torch, _lib, sm_count)
+    stages = stage_breakdown(kp, min(args.steps, 10))
+    bounds = stage_bounds(kp, scene, blends, float(peaks["hbm_gbs"]) * 1e9, alu_peak)
     bwd_ach = blends * BWD_OPS_PER_BLEND / (t_bwd_raster / 1000.0)
     fwd_ach = blends * FWD_OPS_PER_BLEND / (t_fwd_raster / 1000.0)
     dominant = "rasterize_bwd" if t_bwd_raster >= t_fwd_raster else "rasterize_fwd"
@@ -417,6 +307,28 @@ def run_ours(args):
                 "bwd": {"ms": t_bwd_raster, "gop_s": bwd_ach / 1e9, "frac": bwd_ach / alu_peak}}
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = ach / (sm_count * 128 * clk["sm_mhz"] * 1e6)
+    roofline["probe"] = {"ffma_gop_s": probe["ffma"] / 1e9, "ex2_gop_s": probe["ex2"] / 1e9,
+                         "frac_of_ffma_probe": ach / probe["ffma"],
+                         "note": "measured by gs_probe_peak (independent FFMA / ex2.approx streams)"}
+    step_bound_ms = sum(b["bound_ms"] for b in bounds.values())
+    stage_table = {k: dict(bounds[k], ms=stages[k], frac=bounds[k]["bound_ms"] / stages[k] if stages[k] > 0 else None)
+                   for k in bounds}
+    step_roofline = {"bound_ms": step_bound_ms, "stages_ms": sum(stages.values()),
+                     "frac": step_bound_ms / sum(stages.values()), "stages": stage_table,
+                     "note": "sum over stages of max(algorithmic bytes / measured HBM GB/s, "
+                             "FP32 ops / (SMs x 128 x f_max)), divided by the eagerly launched stage times"}
+
+    log = lambda msg: print(msg, file=sys.stderr, flush=True)
+    extra = {}
+    if not args.skip_next:
+        for name, fn in (("multiview", lambda: run_multiview(dscene, 5, log)),
+                         ("memory", lambda: run_memory(5, sched, log)),
+                         ("serving", lambda: run_serving(args.serve_seconds, args.serve_rate, log))):
+            try:
+                log(f"{name} ...")
+                extra[name] = fn()
+            except Exception as exc:  # a failed row is reported, not fatal to the headline line
+                extra[name] = {"error": f"{type(exc).__name__}: {str(exc).splitlines()[0][:200]}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -429,18 +341,254 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "gaussians": scene.n, "sh_degree": scene.sh_degree,
                    "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": args.tile,
                    "batch_depth": args.batch, "pixels_per_thread": args.ppt,
-                   "cuda_graphs": graphs, "intersections_K": kp.K, "blends_per_view": blends,
+                   "cuda_graphs": graphs, "tile_order": not args.no_tile_order, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
         "ms_per_view_fwd_bwd": ms_step_job, "ms_per_view_fwd": ms_fwd,
         "blends_per_s_fwd": blends / (ms_fwd / 1000.0),
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
-        "roofline": roofline, "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")},
+        "roofline": roofline, "step_roofline": step_roofline,
+        "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")},
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+        "serving_p99_ms": extra.get("serving", {}).get("p99_ms"),
+        "multiview": extra.get("multiview"), "memory": extra.get("memory"), "serving": extra.get("serving"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_alu_peaks(torch, _lib, sm_count):
+    """FP32 FFMA and ex2.approx lane-op rates of this GPU (best of 5 launches, CUDA events)."""
+    sink = torch.zeros(1, device="cuda")
+    out = {}
+    for kind, name, iters in ((0, "ffma", 20000), (1, "ex2", 2500)):
+        best = 0.0
+        for rep in range(6):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ops = _lib.gs_probe_peak(kind, sm_count * 8, iters, sink)
+            b.record()
+            torch.cuda.synchronize()
+            if rep:
+                best = max(best, ops / (a.elapsed_time(b) / 1000.0))
+        out[name] = best
+    return out
+
+
+STAGES = ("project", "sh", "bin_sort", "rasterize_fwd", "rasterize_bwd", "sh_bwd", "project_bwd")
+
+
+def stage_breakdown(kp, steps):
+    """Device time of each stage: every stage is captured as its own CUDA graph and its replays
+    are bracketed by events, so host launch latency never shows up as stage time."""
+    import torch
+    from paper_2409_06765_gb300 import _lib as L
+    sc = kp.scene
+    fns = {
+        "project": lambda: L.gs_project(kp.cams, sc.means, sc.quats, sc.log_scales, sc.opacity_logits, kp.params,
+                                        kp.means2d, kp.depths, kp.conics, kp.radii, kp.tiles, kp.opac),
+        "sh": lambda: L.gs_sh_eval(kp.cams, sc.sh_degree, sc.sh, sc.means, kp.radii, kp.colors),
+        "bin_sort": lambda: (L.gs_tile_bin_sort(kp.cams, kp.N, kp.params, kp.means2d, kp.depths, kp.radii,
+                                                kp.capacity, None, kp.values, kp.ranges, kp.K_out, kp.workspace),
+                             kp.order is not None and L.gs_tile_order(kp.cams, kp.params, kp.ranges, kp.order)),
+        "rasterize_fwd": kp._raster_fwd,
+        "rasterize_bwd": lambda: (kp.g2d.zero_(), kp._raster_bwd()),
+        "sh_bwd": lambda: L.gs_sh_eval_bwd(kp.cams, sc.sh_degree, sc.sh, sc.means, kp.radii, kp.d_colors, kp.d_sh,
+                                           kp.d_means),
+        "project_bwd": lambda: L.gs_project_bwd(kp.cams, sc.means, sc.quats, sc.log_scales, sc.opacity_logits,
+                                                kp.params, kp.radii, kp.d_means2d, kp.d_conics, kp.d_opac, None,
+                                                kp.d_means, kp.d_quats, kp.d_log_scales, kp.d_logits),
+    }
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for name in STAGES:
+            fns[name]()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graphs = {}
+    for name in STAGES:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fns[name]()
+        graphs[name] = g
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(steps)]
+    for k in range(steps + 2):
+        for i, name in enumerate(STAGES):
+            if k >= 2:
+                ev[k - 2][i].record()
+            graphs[name].replay()
+        if k >= 2:
+            ev[k - 2][len(STAGES)].record()
+    torch.cuda.synchronize()
+    return {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
+            for i, name in enumerate(STAGES)}
+
+
+def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
+    """Algorithmic bytes (HBM-bound stages) or FP32 operations (compositing) of each stage, and the
+    time they take at the peak.  Bytes count what the stage must move as designed: parameters
+    read once, outputs written once, each sort pass reading and writing its keys and values."""
+    import torch
+    C, N, K = kp.C, kp.N, kp.K
+    CN = C * N
+    vis = int(torch.count_nonzero(kp.radii > 0).item())
+    ncoef = 3 * (scene.sh_degree + 1) ** 2
+    tile_bits = max(1, int(np.ceil(np.log2(max(2, kp.ranges.shape[0])))))
+    tpasses = (tile_bits + 6) // 7
+    byt = {
+        # means, quats, log-scales, logit in; means2d, depth, conic, radius, tiles, opacity out
+        "project": N * 44 + CN * 36,
+        # mean + radius of every pair, coefficients of the visible ones; colours out
+        "sh": CN * 16 + vis * ncoef * 4 + CN * 12,
+        # depth keys (read depth, radius, mean2d; write key, value), 4 LSD passes over C*N pairs
+        # (histogram read of keys + read and write of keys and values), tile counting, emission
+        # of K (tile, id) pairs, tpasses LSD passes over K, ranges
+        "bin_sort": CN * 24 + 4 * CN * 20 + CN * 28 + K * 8 + tpasses * K * 20 + K * 4,
+        # d_colors + mean + radius in, visible coefficients in; d_sh and d_means out
+        "sh_bwd": CN * 16 + vis * (12 + ncoef * 4) + N * (ncoef * 4 + 12),
+        # parameters + d_means in, 2D gradients + radius per pair in; d_quats, d_log_scales, d_logits, d_means out
+        "project_bwd": N * (44 + 12) + CN * 28 + N * 44,
+    }
+    out = {k: {"bound": "hbm", "bytes": int(v), "bound_ms": v / hbm_bps * 1000.0} for k, v in byt.items()}
+    out["rasterize_fwd"] = {"bound": "alu", "ops": blends * FWD_OPS_PER_BLEND,
+                            "bound_ms": blends * FWD_OPS_PER_BLEND / alu_ops * 1000.0}
+    out["rasterize_bwd"] = {"bound": "alu", "ops": blends * BWD_OPS_PER_BLEND,
+                            "bound_ms": blends * BWD_OPS_PER_BLEND / alu_ops * 1000.0}
+    return {k: out[k] for k in STAGES}
+
+
+# ------------------------------------------------------------------------------------------
+# the rows beyond the single-view step: batched multi-view, memory, serving
+# ------------------------------------------------------------------------------------------
+
+def _time_graph_steps(pipe, steps, warmup=2):
+    import torch
+    pipe.capture_graphs()
+    for _ in range(warmup):
+        pipe.step(graphs=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        pipe.step(graphs=True)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_multiview(dscene, steps, log):
+    """16 cameras of four resolutions rendered (fwd + bwd) in one call per stage, the launch
+    schedule picked by the autotuner, against the same 16 views rendered one at a time."""
+    import gc
+    import torch
+    from paper_2409_06765_gb300 import autotune, synth
+    from paper_2409_06765_gb300.pipeline import FramePipeline
+    sizes = [(640, 480)] * 4 + [(1280, 720)] * 4 + [(1920, 1080)] * 4 + [(2560, 1440)] * 4
+    cams = synth.sphere_cameras(3 + 3000, sizes)
+    t0 = time.time()
+    tuned = autotune.tune(dscene, cams, backward=True, steps=3, warmup=1, log=log)
+    tune_s = time.time() - t0
+    pipe = FramePipeline(dscene, cams, tuned.best)
+    blends = pipe.count_blends()
+    pipe.d_image.normal_(0.0, 1e-6)
+    ms_batch = _time_graph_steps(pipe, steps)
+    n_launch = pipe.graph_kernels + 2
+    K = pipe.K
+    del pipe
+    gc.collect()
+    torch.cuda.empty_cache()
+    ms_single = 0.0
+    for cam in cams:
+        p1 = FramePipeline(dscene, [cam], tuned.best)
+        p1.forward()
+        p1.d_image.normal_(0.0, 1e-6)
+        ms_single += _time_graph_steps(p1, steps)
+        del p1
+    gc.collect()
+    torch.cuda.empty_cache()
+    px = sum(w * h for w, h in sizes)
+    return {"workload": "3M clustered Gaussians (SH 3), 16 views: 4 each of 640x480, 1280x720, 1920x1080, 2560x1440",
+            "metric": "fwd+bwd of all 16 views", "ms_per_batch": ms_batch, "views_per_s": 16 / (ms_batch / 1000.0),
+            "blends_per_s": blends / (ms_batch / 1000.0), "blends": blends, "intersections_K": K, "pixels": px,
+            "single_view_path_ms": ms_single, "speedup_vs_single_view": ms_single / ms_batch,
+            "schedule": tuned.best.as_dict(), "autotune": tuned.as_dict(), "autotune_seconds": tune_s,
+            "launches_per_batch": n_launch, "cuda_graphs": True}
+
+
+def run_memory(steps, sched, log):
+    """6M Gaussians, four 1080p views, fwd + bwd: device memory of the whole step."""
+    import gc
+    import torch
+    from paper_2409_06765_gb300 import synth
+    from paper_2409_06765_gb300.pipeline import DeviceScene, FramePipeline
+    scene, cams = synth.memory_workload()
+    gc.collect()
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    ds = DeviceScene.from_host(scene)
+    pipe = FramePipeline(ds, cams, sched)
+    blends = pipe.count_blends()
+    pipe.d_image.normal_(0.0, 1e-6)
+    ms = _time_graph_steps(pipe, steps)
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated() - base
+    free1, _ = torch.cuda.mem_get_info()
+    C, N, P, K = pipe.C, pipe.N, pipe.P, pipe.K
+    out = {"workload": "6M Gaussians (log-s N(-4.5,0.8), 20% logits N(3,0.5)), SH 3, 4 x 1920x1080, fwd+bwd",
+           "ms_per_step": ms, "blends": blends, "intersections_K": K, "capacity": pipe.capacity,
+           "peak_allocated_bytes": int(peak), "device_bytes_in_use_delta": int(free0 - free1),
+           "parameters_bytes": ds.nbytes, "parameter_gradient_bytes": ds.nbytes,
+           "per_pair_bytes": C * N * (48 + 36), "per_pixel_bytes": P * 32,
+           "sort_bytes": pipe.values.numel() * 4 + pipe.workspace.numel(),
+           "per_blend_state_would_need_bytes": blends * 8,
+           "note": "backward state is final T + last contributor per pixel; nothing is stored per blend"}
+    del pipe, ds
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(seconds, rate, log, warm_s=2.0):
+    """8 resident scenes (0.5..6M Gaussians), Poisson requests, batched vs single-view serving."""
+    import gc
+    import torch
+    from paper_2409_06765_gb300 import serve, synth
+    sizes_m = [0.5, 1, 2, 3, 4, 5, 5, 6]
+    store = serve.ResidentScenes()
+    t0 = time.time()
+    for sid, m in enumerate(sizes_m):
+        store.add(sid, synth.clustered_scene(int(m * 1_000_000), 50 + sid))
+    setup_s = time.time() - t0
+    trace = serve.poisson_trace(rate, warm_s + seconds, len(sizes_m), seed=58)
+    sat = serve.poisson_trace(10 * rate, 400 / (10 * rate), len(sizes_m), seed=59)  # 400 requests at once
+    out = {"workload": f"8 resident scenes ({', '.join(str(m) for m in sizes_m)} M Gaussians, SH 3); Poisson "
+                       f"{rate:.0f} req/s for {seconds:.0f} s after {warm_s:.0f} s warm-up; sizes 640x480, "
+                       "1280x720, 1920x1080; forward only, image returned to pinned host memory",
+           "scene_setup_s": setup_s, "resident_scene_bytes": sum(s.nbytes for s in store.scenes.values())}
+    for name, kw in (("batched", dict(max_views=8, streams=4)), ("single_view", dict(max_views=1, streams=1))):
+        srv = serve.Server(store, **kw)
+        srv.serve(sat[:16], realtime=False)  # warm the allocator and the kernels
+        res = srv.serve(trace, realtime=True)
+        summ = serve.latency_summary(res, skip_before_s=warm_s)
+        t1 = time.perf_counter()
+        sat_res = srv.serve(sat, realtime=False)
+        sat_s = time.perf_counter() - t1
+        summ["saturated_frames_per_s"] = len(sat_res) / sat_s
+        summ["batches"], summ["overflow_retries"] = srv.batches, srv.overflows
+        out[name] = summ
+        log(f"  serving {name}: p50 {summ['p50_ms']:.2f} ms p99 {summ['p99_ms']:.2f} ms, "
+            f"saturated {summ['saturated_frames_per_s']:.0f} frames/s")
+        del srv
+        gc.collect()
+    out["p99_ms"] = out["batched"]["p99_ms"]
+    del store
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
 
 
 def oracle_setup(scene, cam):
@@ -530,8 +678,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="headline", choices=["headline", "training_step", "tiny"])
     ap.add_argument("--tile", type=int, default=16)
@@ -542,6 +690,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every stage directly instead of graph replays")
+    ap.add_argument("--no-tile-order", action="store_true", help="composite tiles in index order (no gs_tile_order)")
+    ap.add_argument("--skip-next", action="store_true", help="skip the multi-view, memory and serving sections")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

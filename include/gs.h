@@ -98,6 +98,15 @@ GS_API uint64_t gs_kernel_launches(void);
 /* Number of pixels of C cameras (sum of W * H). */
 GS_API int64_t gs_num_pixels(const gs_camera *cams, int32_t C);
 
+/* Throughput probe for the roofline of the compositing kernels (not part of the
+ * method): launches `blocks` CTAs of 256 threads, each thread running 8 independent
+ * chains of iters * 16 operations of one kind -- kind 0: FP32 FFMA, kind 1: the
+ * special-function ex2 approximation.  *ops (host) receives the number of lane
+ * operations launched; time the launch with events on `stream` to get ops/s.  `sink`
+ * is one device float the kernel never actually writes (it keeps the work alive).
+ * GS_ERR_ARG on a bad kind, blocks < 1 or iters outside [1, 2^24]. */
+GS_API gs_status gs_probe_peak(int32_t kind, int32_t blocks, int32_t iters, float *sink, double *ops, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* gs_project -- App. C.1 (projection, EWA splatting), App. E (quaternion,   */
 /* pixel coordinates), App. A (low-pass / anti-aliasing).                    */
@@ -191,6 +200,20 @@ GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int32_t C, int3
                                           int32_t *tile_ranges, int64_t *K_out, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* gs_tile_order -- a launch order for the compositing kernels (not a step   */
+/* of the method; App. C.2 leaves the schedule open): tiles sorted by the    */
+/* length of their list, longest first, in buckets of half an octave (ties   */
+/* in any order).  Handing the heaviest tiles out first shortens the tail    */
+/* of a launch whose per-tile work is uneven (clustered scenes, many views).  */
+/*                                                                          */
+/* in : tile_ranges [T,2] from gs_tile_bin_sort                              */
+/* out: tile_order [T] int32, a permutation of 0..T-1 (T = gs_num_tiles)     */
+/* One CTA, no scratch; never synchronises.                                  */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_tile_order(const gs_camera *cams, int32_t C, const gs_params *params,
+                               const int32_t *tile_ranges, int32_t *tile_order, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* gs_rasterize_fwd -- App. C.2: for each pixel p (centre i+0.5, j+0.5) walk */
 /* its tile's sorted list front to back; a Gaussian counts at p only if p is */
 /* inside its pixel box; sigma = 1/2 D^T conic D with D = p - mu';           */
@@ -208,12 +231,15 @@ GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int32_t C, int3
 /*      blend_count (optional device int64, NULL to skip): += the number of   */
 /*      (pixel, Gaussian) pairs whose alpha was evaluated.                    */
 /* channels: 1..GS_MAX_CHANNELS; 1,2,3,4,8,16,32,64 use specialised kernels.  */
+/* tile_order (optional device int32 [T], NULL for 0..T-1): the order in      */
+/*      which tiles are handed to the GPU (gs_tile_order: heaviest first);    */
+/*      it must be a permutation of 0..T-1.  Results do not depend on it.     */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                            int32_t channels, const int32_t *tile_ranges, const int32_t *values,
                            const int32_t *radii, const float *means2d, const float *conics, const float *opacities,
                            const float *colors, const float *background, float *image, float *final_T,
-                           int32_t *last_contrib, int64_t *blend_count, void *stream);
+                           int32_t *last_contrib, int64_t *blend_count, const int32_t *tile_order, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* gs_rasterize_bwd -- App. D.1: replay each pixel back to front from its    */
@@ -232,6 +258,7 @@ GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, c
 /*      [pixels, channels], d_alpha [pixels] or NULL                         */
 /* out (accumulated, caller zeroes): d_means2d [C,N,2], d_conics [C,N,3],     */
 /*      d_opacities [C,N], d_colors [C,N,channels], absgrad [C,N,2] or NULL   */
+/* tile_order: as for gs_rasterize_fwd.                                      */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                            int32_t channels, const int32_t *tile_ranges, const int32_t *values,
@@ -239,7 +266,8 @@ GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, c
                            const float *colors, const float *background, const float *final_T,
                            const int32_t *last_contrib, const float *d_image, const float *d_alpha,
                            float *d_means2d, float *d_conics, float *d_opacities, float *d_colors,
-                           float *absgrad, void *stream);
+                           float *absgrad, const int32_t *tile_order,
+                           void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* gs_sh_eval_bwd -- backward of gs_sh_eval: d_sh[n] = sum_c Y(dir_c) *      */

@@ -27,7 +27,8 @@ GS_MAX_CHANNELS = 64
 EXPORTED = (
     "gs_default_params", "gs_status_string", "gs_last_error", "gs_num_tiles", "gs_num_pixels", "gs_project",
     "gs_sh_eval", "gs_tile_bin_sort_workspace", "gs_tile_bin_sort", "gs_rasterize_fwd", "gs_rasterize_bwd",
-    "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc",
+    "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc", "gs_probe_peak",
+    "gs_tile_order",
 )
 GS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -81,6 +82,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_num_tiles": (_I64, [_CAM, _I32, _I32]),
             "gs_kernel_launches": (ctypes.c_uint64, []),
             "gs_num_pixels": (_I64, [_CAM, _I32]),
+            "gs_probe_peak": (_I32, [_I32, _I32, _I32, _P, ctypes.POINTER(ctypes.c_double), _P]),
             "gs_project": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P]),
             "gs_sh_eval": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P]),
             "gs_tile_bin_sort_workspace": (_I64, [_CAM, _I32, _I32, _PAR, _I64]),
@@ -88,9 +90,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         _P]),
             "gs_tile_bin_sort_noalloc": (_I32, [_CAM, _I32, _I32, _PAR, _P, _P, _P, _I64, _P, _P, _P, _P, _P]),
             "gs_rasterize_fwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                        _P]),
+                                        _P, _P]),
             "gs_rasterize_bwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                        _P, _P, _P, _P, _P, _P]),
+                                        _P, _P, _P, _P, _P, _P, _P]),
+            "gs_tile_order": (_I32, [_CAM, _I32, _PAR, _P, _P, _P]),
             "gs_sh_eval_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
             "gs_project_bwd": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                       _P]),
@@ -213,6 +216,14 @@ def gs_kernel_launches() -> int:
     return int(load().gs_kernel_launches())
 
 
+def gs_probe_peak(kind: int, blocks: int, iters: int, sink, stream=None) -> float:
+    """Launch the FFMA (kind 0) or EX2 (kind 1) throughput probe; returns the lane operations launched."""
+    ops = ctypes.c_double(0.0)
+    _check(load().gs_probe_peak(int(kind), int(blocks), int(iters), _dev(sink, "f32", "sink"), ctypes.byref(ops),
+                                _stream(stream)), "gs_probe_peak")
+    return float(ops.value)
+
+
 def gs_num_tiles(cams: CameraArray, tile: int) -> int:
     return int(load().gs_num_tiles(cams.ptr, cams.C, tile))
 
@@ -271,7 +282,7 @@ def gs_tile_bin_sort_noalloc(cams: CameraArray, N: int, params: GsParams, means2
 
 def gs_rasterize_fwd(cams: CameraArray, N: int, params: GsParams, channels: int, tile_ranges, values, radii, means2d,
                      conics, opacities, colors, background, image, final_T, last_contrib, blend_count=None,
-                     stream=None):
+                     stream=None, tile_order=None):
     keep, bgp = _bg(background, channels)
     st = load().gs_rasterize_fwd(cams.ptr, cams.C, N, ctypes.byref(params), channels,
                                  _dev(tile_ranges, "i32", "tile_ranges"), _dev(values, "i32", "values"),
@@ -279,14 +290,15 @@ def gs_rasterize_fwd(cams: CameraArray, N: int, params: GsParams, channels: int,
                                  _dev(conics, "f32", "conics"), _dev(opacities, "f32", "opacities"),
                                  _dev(colors, "f32", "colors"), bgp, _dev(image, "f32", "image"),
                                  _dev(final_T, "f32", "final_T"), _dev(last_contrib, "i32", "last_contrib"),
-                                 _dev(blend_count, "i64", "blend_count", optional=True), _stream(stream))
+                                 _dev(blend_count, "i64", "blend_count", optional=True),
+                                 _dev(tile_order, "i32", "tile_order", optional=True), _stream(stream))
     del keep
     _check(st, "gs_rasterize_fwd")
 
 
 def gs_rasterize_bwd(cams: CameraArray, N: int, params: GsParams, channels: int, tile_ranges, values, radii, means2d,
                      conics, opacities, colors, background, final_T, last_contrib, d_image, d_alpha, d_means2d,
-                     d_conics, d_opacities, d_colors, absgrad=None, stream=None):
+                     d_conics, d_opacities, d_colors, absgrad=None, stream=None, tile_order=None):
     keep, bgp = _bg(background, channels)
     st = load().gs_rasterize_bwd(cams.ptr, cams.C, N, ctypes.byref(params), channels,
                                  _dev(tile_ranges, "i32", "tile_ranges"), _dev(values, "i32", "values"),
@@ -297,9 +309,16 @@ def gs_rasterize_bwd(cams: CameraArray, N: int, params: GsParams, channels: int,
                                  _dev(d_alpha, "f32", "d_alpha", optional=True), _dev(d_means2d, "f32", "d_means2d"),
                                  _dev(d_conics, "f32", "d_conics"), _dev(d_opacities, "f32", "d_opacities"),
                                  _dev(d_colors, "f32", "d_colors"), _dev(absgrad, "f32", "absgrad", optional=True),
-                                 _stream(stream))
+                                 _dev(tile_order, "i32", "tile_order", optional=True), _stream(stream))
     del keep
     _check(st, "gs_rasterize_bwd")
+
+
+def gs_tile_order(cams: CameraArray, params: GsParams, tile_ranges, tile_order, stream=None):
+    """Tiles ordered longest list first (a launch order for the compositing kernels)."""
+    st = load().gs_tile_order(cams.ptr, cams.C, ctypes.byref(params), _dev(tile_ranges, "i32", "tile_ranges"),
+                              _dev(tile_order, "i32", "tile_order"), _stream(stream))
+    _check(st, "gs_tile_order")
 
 
 def gs_sh_eval_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors, d_sh, d_means, stream=None):

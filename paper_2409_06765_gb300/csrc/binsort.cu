@@ -644,6 +644,53 @@ __global__ void ranges_kernel(const int *__restrict__ n_dev, int T, int CN, cons
 }
 
 // ---------------------------------------------------------------------------
+// launch order of the compositing kernels: longest tile lists first
+// ---------------------------------------------------------------------------
+
+// Bucket of a list length: 0 for an empty list, else 1 + 2 floor(log2 len) + the bit below
+// the leading one (half-octave buckets, at most 63).
+__device__ __forceinline__ int length_bucket(int len) {
+    if (len <= 0) return 0;
+    const int l = 31 - __clz(len);
+    const int half = l > 0 ? (len >> (l - 1)) & 1 : 0;
+    return 1 + 2 * l + half;
+}
+
+// One CTA: counting sort of the tiles by bucket, buckets in descending order.
+__global__ void __launch_bounds__(1024) tile_order_kernel(int T, const int2 *__restrict__ ranges,
+                                                          int *__restrict__ order) {
+    __shared__ int s_cnt[64];
+    __shared__ int s_cur[64];
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const int2 r = ranges[t];
+        atomicAdd(&s_cnt[length_bucket(r.y - r.x)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 63; b >= 0; --b) {
+            s_cur[b] = run;
+            run += s_cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const int2 r = ranges[t];
+        const int pos = atomicAdd(&s_cur[length_bucket(r.y - r.x)], 1);
+        if ((unsigned)pos < (unsigned)T) order[pos] = t;  // holds by construction
+    }
+}
+
+cudaError_t launch_tile_order(int T, const int *tile_ranges, int *order, cudaStream_t st) {
+    if (T <= 0) return cudaSuccess;
+    tile_order_kernel<<<1, 1024, 0, st>>>(T, (const int2 *)tile_ranges, order);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
@@ -700,7 +747,7 @@ static cudaError_t rts_pass(const uint32_t *kin, const int *vin, uint32_t *kout,
     hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
     note_launch();
     cudaError_t e =
-        cudaFuncSetAttribute(scatter_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+        ensure_smem((const void *)scatter_tma_kernel, (int)kTmaSmem);
     if (e != cudaSuccess) return e;
     const int persistent = 2 * sort_grid_blocks() / 4;  // two CTAs per SM
     scatter_tma_kernel<<<cols < persistent ? cols : persistent, kTmaThreads, kTmaSmem, st>>>(

@@ -28,11 +28,39 @@ cudaError_t launch_raster_bwd(const CamSet &, const RasterConsts &, int, int, in
                               const float *, const float *, const float *, const float *, const float *,
                               const float *, const int *, const float *, const float *, float *, float *, float *,
                               float *, float *, cudaStream_t);
+cudaError_t launch_probe(int, int, int, float *, double *, cudaStream_t);
+cudaError_t launch_tile_order(int, const int *, int *, cudaStream_t);
 int raster_channel_capacity(int tile, int ppt, int ch, bool restricted);
 int raster_pixels_per_thread(int tile, int ppt);
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t ensure_smem(const void *kernel, int bytes) {
+    struct Entry {
+        int dev;
+        const void *kernel;
+        int bytes;
+    };
+    static std::mutex mu;
+    static Entry table[256];
+    static int used = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+        if (table[i].dev == dev && table[i].kernel == kernel && table[i].bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < used; ++i)
+        if (table[i].dev == dev && table[i].kernel == kernel) {
+            table[i].bytes = bytes;
+            return cudaSuccess;
+        }
+    if (used < 256) table[used++] = Entry{dev, kernel, bytes};
+    return cudaSuccess;
+}
 
 // CTAs of the sort kernels: 4 per SM of the current device (cached per device).
 int sort_grid_blocks() {
@@ -123,6 +151,7 @@ static gs_status check_params(const gs_params *p, RasterConsts &rc) {
     rc.alpha_max = p->alpha_max;
     rc.T_min = p->T_min;
     rc.antialiased = p->antialiased ? 1 : 0;
+    rc.tile_order = nullptr;
     return GS_OK;
 }
 
@@ -176,6 +205,14 @@ int64_t gs_num_tiles(const gs_camera *cams, int32_t C, int32_t tile) {
     CamSet cs;
     if (make_camset(cams, C, tile, cs) != GS_OK) return -1;
     return cs.total_tiles;
+}
+
+gs_status gs_probe_peak(int32_t kind, int32_t blocks, int32_t iters, float *sink, double *ops, void *stream) {
+    if (kind != 0 && kind != 1) return fail_arg("probe kind must be 0 (FFMA) or 1 (EX2)");
+    if (blocks < 1 || iters < 1 || iters > (1 << 24)) return fail_arg("probe blocks >= 1, iters in [1, 2^24]");
+    if (!sink || !ops) return fail_arg("probe sink and ops must be non-null");
+    cudaError_t e = launch_probe(kind, blocks, iters, sink, ops, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_probe_peak");
 }
 
 int64_t gs_num_pixels(const gs_camera *cams, int32_t C) {
@@ -258,11 +295,23 @@ gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_tile_bin_sort");
 }
 
+gs_status gs_tile_order(const gs_camera *cams, int32_t C, const gs_params *params, const int32_t *tile_ranges,
+                        int32_t *tile_order, void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_NONNULL(tile_ranges); GS_NONNULL(tile_order);
+    if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
+    cudaError_t e = launch_tile_order(cs.total_tiles, tile_ranges, tile_order, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_tile_order");
+}
+
 gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params, int32_t channels,
                            const int32_t *tile_ranges, const int32_t *values, const int32_t *radii,
                            const float *means2d, const float *conics, const float *opacities, const float *colors,
                            const float *background, float *image, float *final_T, int32_t *last_contrib,
-                           int64_t *blend_count, void *stream) {
+                           int64_t *blend_count, const int32_t *tile_order, void *stream) {
     RasterConsts rc;
     CamSet cs;
     GS_TRY(check_params(params, rc));
@@ -284,6 +333,7 @@ gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     }
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     if (blend_count && !aligned(blend_count, 8)) return fail_arg("blend_count must be 8-byte aligned");
+    rc.tile_order = tile_order;
     cudaError_t e = launch_raster_fwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, image, final_T, last_contrib,
                                       (unsigned long long *)blend_count, (cudaStream_t)stream);
@@ -295,7 +345,8 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
                            const float *means2d, const float *conics, const float *opacities, const float *colors,
                            const float *background, const float *final_T, const int32_t *last_contrib,
                            const float *d_image, const float *d_alpha, float *d_means2d, float *d_conics,
-                           float *d_opacities, float *d_colors, float *absgrad, void *stream) {
+                           float *d_opacities, float *d_colors, float *absgrad, const int32_t *tile_order,
+                           void *stream) {
     RasterConsts rc;
     CamSet cs;
     GS_TRY(check_params(params, rc));
@@ -316,6 +367,7 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     if (!aligned(means2d, 8) || !aligned(d_means2d, 8)) return fail_arg("means2d/d_means2d must be 8-byte aligned");
     if (absgrad && !aligned(absgrad, 8)) return fail_arg("absgrad must be 8-byte aligned");
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
+    rc.tile_order = tile_order;
     cudaError_t e = launch_raster_bwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, final_T, last_contrib, d_image, d_alpha,
                                       d_means2d, d_conics, d_opacities, d_colors, absgrad, (cudaStream_t)stream);

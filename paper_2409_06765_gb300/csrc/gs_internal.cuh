@@ -14,6 +14,11 @@ void note_launch();
 // Records the text gs_last_error() returns on this thread (defined in gs_abi.cu).
 void set_last_error(const char *text);
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// The attribute is set once per (device, kernel, size): setting it again on every call
+// can stall the host until the device is idle, which would serialise eager launches.
+cudaError_t ensure_smem(const void *kernel, int bytes);
+
 constexpr int kMaxCams = GS_MAX_CAMERAS;
 
 // Per-camera constants, passed to kernels by value (a __grid_constant__ CamSet).
@@ -44,7 +49,15 @@ struct BinSortLayout {
 struct RasterConsts {
     float eps2d, near_plane, alpha_min, alpha_max, T_min;
     int antialiased;
+    const int *tile_order;  // compositing: CTA b renders tile tile_order[b] (NULL: tile b)
 };
+
+// Global tile rendered by this CTA of a compositing launch; -1 for an out-of-range entry of
+// a caller-supplied order (the CTA then renders nothing).
+__device__ __forceinline__ int tile_of_block(const RasterConsts &rc, int total_tiles) {
+    const int t = rc.tile_order ? rc.tile_order[blockIdx.x] : (int)blockIdx.x;
+    return (unsigned)t < (unsigned)total_tiles ? t : -1;
+}
 
 // Camera of a global tile: the last camera whose tile_offset <= gtile.
 __device__ __forceinline__ int camera_of_tile(const CamSet &cs, int gtile) {

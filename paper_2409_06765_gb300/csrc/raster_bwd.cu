@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
     __shared__ int s_max;
 
-    const int gt = blockIdx.x;
+    const int gt = tile_of_block(rc, cs.total_tiles);
+    if (gt < 0) return;  // uniform over the CTA
     const int c = camera_of_tile(cs, gt);
     const CamDev &cam = cs.cam[c];
     const int local = gt - cam.tile_offset;
@@ -256,7 +257,7 @@ static cudaError_t launch_bwd_t(const CamSet &cs, const RasterConsts &rc, int ch
     const size_t smem = raster_bwd_smem(batch, CHC);
     auto kern = raster_bwd_kernel<TILE, PPT, CHC, ABSG>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (cs.total_tiles == 0) return cudaSuccess;

@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
     int4 *s_b = reinterpret_cast<int4 *>(s_h + batch);
     float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
 
-    const int gt = blockIdx.x;
+    const int gt = tile_of_block(rc, cs.total_tiles);
+    if (gt < 0) return;  // uniform over the CTA
     const int c = camera_of_tile(cs, gt);
     const CamDev &cam = cs.cam[c];
     const int local = gt - cam.tile_offset;
@@ -173,7 +174,7 @@ static cudaError_t launch_fwd_t(const CamSet &cs, const RasterConsts &rc, int ch
     const size_t smem = raster_fwd_smem(batch, CHC);
     auto kern = raster_fwd_kernel<TILE, PPT, CHC, COUNT>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (cs.total_tiles == 0) return cudaSuccess;

@@ -281,8 +281,7 @@ static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, con
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 256 * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sh_fwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = ensure_smem((const void *)sh_fwd_kernel<DEG>, (int)smem);
         if (e != cudaSuccess) return e;
     }
     sh_fwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), colors);
@@ -296,8 +295,7 @@ static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, con
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 2 * kShBwdThreads * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sh_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = ensure_smem((const void *)sh_bwd_kernel<DEG>, (int)smem);
         if (e != cudaSuccess) return e;
     }
     sh_bwd_kernel<DEG><<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,

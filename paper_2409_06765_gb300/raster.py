@@ -18,7 +18,8 @@ import torch
 
 from . import _lib
 
-__all__ = ["RasterSettings", "RasterState", "project", "sh_eval", "bin_sort", "rasterize_fwd", "forward_pass",
+__all__ = ["RasterSettings", "RasterState", "project", "sh_eval", "bin_sort", "tile_order", "rasterize_fwd",
+           "forward_pass",
            "rasterization", "RasterizeGaussians"]
 
 
@@ -35,6 +36,7 @@ class RasterSettings:
     background: tuple | None = None
     absgrad: bool = False
     pixels_per_thread: int = 0
+    tile_schedule: bool = True  # hand the longest tile lists to the GPU first (gs_tile_order)
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
@@ -47,6 +49,7 @@ class RasterState:
     capacity: int = 0
     values: torch.Tensor | None = None
     workspace: torch.Tensor | None = None
+    tile_order: torch.Tensor | None = None
     ws_key: tuple = field(default_factory=tuple)
 
     def ensure(self, cams, N, params, K, device):
@@ -103,8 +106,15 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
     return dict(values=values, ranges=ranges, K=K, keys=None if keys is None else keys[:K])
 
 
+def tile_order(cams, params, ranges):
+    """Launch order of the compositing kernels: longest tile lists first."""
+    order = torch.empty(ranges.shape[0], dtype=torch.int32, device=ranges.device)
+    _lib.gs_tile_order(cams, params, ranges, order)
+    return order
+
+
 def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, conics, opacities, colors, background,
-                  count_blends=False):
+                  count_blends=False, order=None):
     dev = means2d.device
     P = cams.num_pixels
     image = torch.empty(P, channels, device=dev)
@@ -114,7 +124,7 @@ def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, con
     if values.numel() == 0:
         values = torch.empty(1, dtype=torch.int32, device=dev)
     _lib.gs_rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, conics, opacities, colors,
-                          background, image, final_T, last, blends)
+                          background, image, final_T, last, blends, tile_order=order)
     return image, final_T, last, blends
 
 
@@ -131,11 +141,12 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
         colors = features
     ch = colors.shape[-1]
     bs = bin_sort(cams, N, params, sp["means2d"], sp["depths"], sp["radii"], state)
+    order = tile_order(cams, params, bs["ranges"]) if settings.tile_schedule else None
     image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
                                                  sp["means2d"], sp["conics"], sp["opacities"], colors,
-                                                 settings.background, count_blends)
+                                                 settings.background, count_blends, order)
     return dict(sp, colors=colors, values=bs["values"], ranges=bs["ranges"], K=bs["K"], image=image,
-                final_T=final_T, last_contrib=last, blends=blends, params=params)
+                final_T=final_T, last_contrib=last, blends=blends, params=params, tile_order=order)
 
 
 class RasterizeGaussians(torch.autograd.Function):
@@ -152,6 +163,7 @@ class RasterizeGaussians(torch.autograd.Function):
                            sh_degree=sh_degree if use_sh else 0, features=feats, settings=settings, state=state)
         ctx.cams, ctx.settings, ctx.sh_degree, ctx.use_sh = cams, settings, sh_degree, use_sh
         ctx.feat_dim = None if use_sh else sh_or_features.dim()
+        ctx.tile_order = out["tile_order"]
         ctx.save_for_backward(means, quats, log_scales, opacity_logits, sh_or_features, out["radii"], out["means2d"],
                               out["conics"], out["opacities"], out["colors"], out["values"], out["ranges"],
                               out["final_T"], out["last_contrib"])
@@ -178,7 +190,7 @@ class RasterizeGaussians(torch.autograd.Function):
         vals = values if values.numel() else torch.empty(1, dtype=torch.int32, device=dev)
         _lib.gs_rasterize_bwd(cams, N, params, ch, ranges, vals, radii, means2d, conics, opac, colors,
                               settings.background, final_T, last, d_image, d_alpha, d_means2d, d_conics, d_opac,
-                              d_colors, absgrad)
+                              d_colors, absgrad, tile_order=ctx.tile_order)
         if absgrad is not None:
             RasterizeGaussians.last_absgrad = absgrad
         d_means = torch.empty(N, 3, device=dev)

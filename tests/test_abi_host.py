@@ -70,7 +70,7 @@ def test_host_validation_rejects_bad_arguments_before_any_launch():
     bad = _lib.make_params(batch_depth=100)
     assert lib.gs_project(cams.ptr, 1, 10, *[fake] * 4, ctypes.byref(bad), *[fake] * 6, null) == _lib.GS_ERR_ARG
     # channels
-    args = [fake] * 12
+    args = [fake] * 12 + [null]  # ... blend_count, tile_order (NULL)
     assert lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(p), 0, *args, null) == _lib.GS_ERR_ARG
     p8 = _lib.make_params(tile=8)
     assert lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(p8), 7, *args, null) == _lib.GS_ERR_UNSUPPORTED
@@ -83,6 +83,8 @@ def test_host_validation_rejects_bad_arguments_before_any_launch():
                               ctypes.c_void_p(768), 1000, null, ctypes.c_void_p(1024), ctypes.c_void_p(2048),
                               ctypes.c_void_p(4096), ctypes.c_void_p(8192), ws - 1, null)
     assert st == _lib.GS_ERR_CAPACITY
+    # tile order: NULL output
+    assert lib.gs_tile_order(cams.ptr, 1, ctypes.byref(p), fake, null, null) == _lib.GS_ERR_ARG
 
 
 def _support_span_f32(m, r):

@@ -183,6 +183,43 @@ def test_image_is_bit_identical_across_schedules():
         np.testing.assert_array_equal(T, outs[0][1])
 
 
+def _bucket(n):
+    """Half-octave bucket of a list length (0 for an empty list), as gs_tile_order defines it."""
+    if n <= 0:
+        return 0
+    l = int(n).bit_length() - 1
+    return 1 + 2 * l + ((int(n) >> (l - 1)) & 1 if l > 0 else 0)
+
+
+def test_tile_order_is_a_permutation_longest_first_and_changes_nothing():
+    sc = synth.clustered_scene(20000, 12, sh_degree=1, log_scale_mu=-3.3)
+    cams = synth.sphere_cameras(12, [(200, 120), (96, 64), (333, 201)])
+    plain = gpu_render(sc, cams, settings=raster.RasterSettings(tile_schedule=False))[0]
+    ordered = gpu_render(sc, cams, settings=raster.RasterSettings(tile_schedule=True))[0]
+    order = ordered["tile_order"].cpu().numpy()
+    rg = ordered["ranges"].cpu().numpy()
+    T = rg.shape[0]
+    assert np.array_equal(np.sort(order), np.arange(T))
+    lengths = rg[order, 1] - rg[order, 0]
+    buckets = np.array([_bucket(n) for n in lengths])
+    assert np.all(np.diff(buckets) <= 0), "tiles are not in descending length buckets"
+    assert buckets[0] == _bucket((rg[:, 1] - rg[:, 0]).max())  # ties inside a bucket come in any order
+    for k in ("image", "final_T", "last_contrib"):
+        np.testing.assert_array_equal(plain[k].cpu().numpy(), ordered[k].cpu().numpy())
+
+
+def test_tile_order_backward_matches_index_order():
+    sc = synth.clustered_scene(8000, 13, sh_degree=2, log_scale_mu=-3.3)
+    cams = synth.sphere_cameras(13, [(128, 96)])
+    rng = np.random.default_rng(13)
+    g = rng.normal(size=(128 * 96, 3)).astype(np.float32)
+    a = gpu_grads(sc, cams, g, settings=raster.RasterSettings(tile_schedule=False))[0]
+    b = gpu_grads(sc, cams, g, settings=raster.RasterSettings(tile_schedule=True))[0]
+    for k in a:
+        # the atomics add in another order: equal up to float32 rounding
+        assert rel_l2(b[k], a[k]) <= 1e-5, k
+
+
 def test_multi_camera_uneven_sizes_and_background():
     sc = synth.clustered_scene(15000, 9, sh_degree=2, log_scale_mu=-3.3)
     cams = synth.sphere_cameras(9, [(64, 48), (131, 77), (40, 90)])
