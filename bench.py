@@ -41,7 +41,7 @@ METRIC = "fwd+bwd ms/view and Gaussian-pixel blends/s, 3M Gaussians @1080p; serv
 UNIT = "blends/s"
 
 # Algorithmic work per evaluated blend (FP32 lane operations), read off the arithmetic of
-# App. C.2 / App. D.1 as implemented (an FMA counts as one operation, MUFU ops separate):
+# App. C.2 / App. D.2 as implemented (an FMA counts as one operation, MUFU ops separate):
 #   forward : box test 4, delta 2, sigma 6, exp scale 1, alpha 2 (mul, min), skip test 1,
 #             T(1-alpha) 2, stop test 1, weight 1, colour 3 FMA, bookkeeping 2     -> 25 ops + 1 MUFU
 #   backward: forward part up to alpha 16, 1/(1-alpha) 1 MUFU + 1, T 1, weight 1, gc 3,
@@ -156,6 +156,21 @@ def build_workload(name: str, rank: int):
     return scene, cams, desc
 
 
+def job_totals(ms_step, blends, world, device):
+    """Whole-job step time (max over ranks) and work (sum over ranks): replicas render their
+    own views, so the job takes as long as its slowest rank and does the work of all."""
+    if world <= 1:
+        return float(ms_step), float(blends)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_step, float(blends)], device=device, dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -172,8 +187,15 @@ def run_ours(args):
         torch.cuda.set_device(0)
     scene, cams, desc = build_workload(args.workload, rank)
     dscene = DeviceScene.from_host(scene)
-    sched = Schedule(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
-                     tile_order=not args.no_tile_order)
+    tuned = None
+    if args.tune:
+        from paper_2409_06765_gb300 import autotune
+        tuned = autotune.tune(dscene, cams, backward=True, steps=5, warmup=2,
+                              schedules=autotune.candidates(tile_order=not args.no_tile_order))
+        sched = tuned.best
+    else:
+        sched = Schedule(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
+                         tile_order=not args.no_tile_order)
     kp = FramePipeline(dscene, cams, sched)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
@@ -221,15 +243,7 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     t_fwd_raster = float(np.mean([a.elapsed_time(b) for a, b in fwd_ev]))
     t_bwd_raster = float(np.mean([a.elapsed_time(b) for a, b in bwd_ev]))
-    if world > 1:
-        t = torch.tensor([ms_step, float(blends)], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_step_job, blends_job = float(mx[0]), float(sm[1])
-    else:
-        ms_step_job, blends_job = ms_step, float(blends)
+    ms_step_job, blends_job = job_totals(ms_step, blends, world, "cuda")
     value = blends_job / (ms_step_job / 1000.0)
 
     # forward-only timing (separate loop, same buffers)
@@ -248,8 +262,8 @@ def run_ours(args):
     if not args.no_e2e:
         leaves = [x.detach().clone().requires_grad_(True) for x in (dscene.means, dscene.quats, dscene.log_scales,
                                                                      dscene.opacity_logits, dscene.sh)]
-        settings = raster.RasterSettings(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
-                                         tile_schedule=not args.no_tile_order)
+        settings = raster.RasterSettings(tile=sched.tile, batch_depth=sched.batch_depth,
+                                         pixels_per_thread=sched.pixels_per_thread, tile_schedule=sched.tile_order)
         state = raster.RasterState()
         host_target = torch.as_tensor(target_np).pin_memory()
         dev_target = torch.empty_like(target)
@@ -339,13 +353,15 @@ def run_ours(args):
         "ms_per_step": ms_step_job, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded clustered Gaussians; no dataset)",
         "config": {"workload": args.workload, "description": desc, "gaussians": scene.n, "sh_degree": scene.sh_degree,
-                   "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": args.tile,
-                   "batch_depth": args.batch, "pixels_per_thread": args.ppt,
-                   "cuda_graphs": graphs, "tile_order": not args.no_tile_order, "intersections_K": kp.K, "blends_per_view": blends,
+                   "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": sched.tile,
+                   "batch_depth": sched.batch_depth, "pixels_per_thread": sched.pixels_per_thread,
+                   "schedule_from": "autotuner" if tuned else "command line",
+                   "cuda_graphs": graphs, "tile_order": sched.tile_order, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
         "ms_per_view_fwd_bwd": ms_step_job, "ms_per_view_fwd": ms_fwd,
         "blends_per_s_fwd": blends / (ms_fwd / 1000.0),
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+        "autotune": tuned.as_dict() if tuned else None,
         "roofline": roofline, "step_roofline": step_roofline,
         "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")},
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
@@ -682,9 +698,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="headline", choices=["headline", "training_step", "tiny"])
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="use --tile/--batch/--ppt instead of the autotuner's pick")
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--ppt", type=int, default=0, help="pixels per compositing thread (0 = library default)")
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--ppt", type=int, default=2, help="pixels per compositing thread (0 = library default)")
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")

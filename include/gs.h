@@ -242,7 +242,7 @@ GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, c
                            int32_t *last_contrib, int64_t *blend_count, const int32_t *tile_order, void *stream);
 
 /* ------------------------------------------------------------------------ */
-/* gs_rasterize_bwd -- App. D.1: replay each pixel back to front from its    */
+/* gs_rasterize_bwd -- App. D.2: replay each pixel back to front from its    */
 /* last contributor, recovering T_n = T_{n+1} / (1 - alpha_n) from final_T,  */
 /* and accumulate per (camera, Gaussian):                                    */
 /*   dL/dc_n     += alpha_n T_n dL/dC                                         */
@@ -281,7 +281,7 @@ GS_API gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int
                          float *d_means, void *stream);
 
 /* ------------------------------------------------------------------------ */
-/* gs_project_bwd -- App. D.2 / D.3 and the gradient-flow figure: from        */
+/* gs_project_bwd -- App. D.3 / D.4 and the gradient-flow figure: from        */
 /* d_means2d, d_conics, d_opacities (and optional d_depths, for depth         */
 /* rendering) of every camera to the leaves: dSigma' = -Y dY Y,              */
 /* dSigma = T^T dSigma' T and dT = dSigma' T Sigma^T + dSigma'^T T Sigma      */

@@ -115,7 +115,7 @@ def rotation(q) -> np.ndarray:
 
 
 def drot_dquat(q) -> np.ndarray:
-    """[dR/dw, dR/dx, dR/dy, dR/dz] at a unit quaternion, App. D.3."""
+    """[dR/dw, dR/dx, dR/dy, dR/dz] at a unit quaternion, App. D.4."""
     q = _d64(q)
     D = np.zeros(36)
     _load().orc_drot(_p(q), _p(D))
@@ -250,7 +250,7 @@ def render_trace(splats, colors, px, py, bg=None, alpha_min=ALPHA_MIN, alpha_max
 
 def render_splats_bwd(splats, colors, width, height, d_color, d_alpha=None, pixels=None, bg=None,
                       alpha_min=ALPHA_MIN, alpha_max=ALPHA_MAX, T_min=T_MIN, want_absgrad=False):
-    """App. D.1: gradients of sum_p <d_color[p], C_p> + d_alpha[p] (1 - T_p) w.r.t. 2D splat data."""
+    """App. D.2: gradients of sum_p <d_color[p], C_p> + d_alpha[p] (1 - T_p) w.r.t. 2D splat data."""
     colors = _d64(colors)
     ch = colors.shape[1]
     N = colors.shape[0]
@@ -274,7 +274,7 @@ def render_splats_bwd(splats, colors, width, height, d_color, d_alpha=None, pixe
 
 
 # --------------------------------------------------------------------------- #
-# App. D.2 / D.3: projection backward                                          #
+# App. D.3 / D.4: projection backward                                          #
 # --------------------------------------------------------------------------- #
 
 def project_bwd(scene, cam, d_means2d, d_conics, d_opacities, d_depths=None, eps2d=EPS2D, near=NEAR,

@@ -12,7 +12,7 @@
  *     [gradient-flow figure];
  *   - world->camera t = R_cw mu + t_cw, pinhole mean mu' = (fx tx/tz + cx,
  *     fy ty/tz + cy) [App. E, pixel coordinates], EWA Jacobian J with the
- *     focal lengths [App. D.2, dJ/dt], Sigma' = J R_cw Sigma R_cw^T J^T
+ *     focal lengths [App. D.3, dJ/dt], Sigma' = J R_cw Sigma R_cw^T J^T
  *     [App. C.1], low-pass Sigma' + s I and the anti-aliased opacity
  *     compensation [App. A, anti-aliasing];
  *   - conic = (Sigma' + sI)^-1, radius ceil(3 sqrt(lambda_max)) and its
@@ -21,7 +21,7 @@
  *     direction [App. C.1];
  *   - per-pixel front-to-back compositing over ALL visible Gaussians sorted
  *     by (depth, index), no tiles [App. C.2, discrete rendering sum];
- *   - the analytic backward [App. D.1-D.3];
+ *   - the analytic backward [App. D.2-D.4];
  *   - the tile binning / sorting result by direct enumeration [App. C.2].
  *
  * Readings where the paper is silent (also listed in the design notes):
@@ -514,7 +514,7 @@ static void atomic_add(double *p, double v) {
     *p += v;
 }
 
-/* Backward of the compositing sum [App. D.1]: per pixel, back to front with
+/* Backward of the compositing sum [App. D.2]: per pixel, back to front with
  * T_{n-1} = T_n / (1 - alpha_{n-1}) and the suffix S_n = sum_{m>n} c_m alpha_m T_m
  * (here S starts at T_final * bg so the background term is included).  Gradients
  * accumulate (+=) into per-Gaussian 2D buffers. */
@@ -585,10 +585,10 @@ ORC_EXPORT void orc_render_bwd(int N, const double *means2d, const double *conic
 }
 
 /* ------------------------------------------------------------------ */
-/* projection backward [App. D.2, D.3, gradient-flow figure]           */
+/* projection backward [App. D.3, D.4, gradient-flow figure]           */
 /* ------------------------------------------------------------------ */
 
-/* dR/dw, dR/dx, dR/dy, dR/dz at the unit quaternion (w,x,y,z) [App. D.3]. */
+/* dR/dw, dR/dx, dR/dy, dR/dz at the unit quaternion (w,x,y,z) [App. D.4]. */
 static void drot_dquat(const double q[4], double D[4][9]) {
     double w = q[0], x = q[1], y = q[2], z = q[3];
     double Dw[9] = {0, -z, y, z, 0, -x, -y, x, 0};
@@ -622,7 +622,7 @@ ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats,
         double dYm[4] = {d_conics[3 * n], 0.5 * d_conics[3 * n + 1], 0.5 * d_conics[3 * n + 1],
                          d_conics[3 * n + 2]};
         double Ym[4] = {Y[0], Y[1], Y[1], Y[2]};
-        /* d Sigma' = -Y dY Y   (dY/dx = -Y dSigma'/dx Y)  [App. D.1] */
+        /* d Sigma' = -Y dY Y   (dY/dx = -Y dSigma'/dx Y)  [App. D.2] */
         double t1[4], G2[4];
         matmul(Ym, dYm, t1, 2, 2, 2);
         matmul(t1, Ym, G2, 2, 2, 2);
@@ -642,7 +642,7 @@ ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats,
             double gb = k * (-2.0 * b * det1 + 2.0 * b * det0);
             G2[0] += ga; G2[3] += gc; G2[1] += 0.5 * gb; G2[2] += 0.5 * gb;
         }
-        /* Sigma' = T Sigma T^T:  dSigma = T^T G T,  dT = G T Sigma^T + G^T T Sigma [App. D.2] */
+        /* Sigma' = T Sigma T^T:  dSigma = T^T G T,  dT = G T Sigma^T + G^T T Sigma [App. D.3] */
         double Tt[6], GT[6], dSig[9], TS[6], dT[6], G2t[4], tmp[6];
         transpose(sp.T, Tt, 2, 3);
         matmul(G2, sp.T, GT, 2, 2, 3);
@@ -666,7 +666,7 @@ ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats,
         dt[0] += gmx * fx / tz;
         dt[1] += gmy * fy / tz;
         dt[2] += -gmx * fx * tx / tz2 - gmy * fy * ty / tz2;
-        /* through J: dJ/dtx, dJ/dty, dJ/dtz [App. D.2] */
+        /* through J: dJ/dtx, dJ/dty, dJ/dtz [App. D.3] */
         dt[0] += dJ[2] * (-fx / tz2);
         dt[1] += dJ[5] * (-fy / tz2);
         dt[2] += dJ[0] * (-fx / tz2) + dJ[2] * (2.0 * fx * tx / tz3) + dJ[4] * (-fy / tz2) +
@@ -675,7 +675,7 @@ ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats,
         /* t = R_cw mu + t_cw:  dmu = R_cw^T dt */
         for (int i = 0; i < 3; i++)
             d_means[3 * n + i] += Wr[0 + i] * dt[0] + Wr[3 + i] * dt[1] + Wr[6 + i] * dt[2];
-        /* Sigma = M M^T:  dM = dSigma M + dSigma^T M [App. D.3] */
+        /* Sigma = M M^T:  dM = dSigma M + dSigma^T M [App. D.4] */
         double dSigt[9], dM[9], t2[9];
         transpose(dSig, dSigt, 3, 3);
         matmul(dSig, g.M, dM, 3, 3, 3);
@@ -807,7 +807,7 @@ ORC_EXPORT void orc_rotation(const double *q, double *R) {
     quat_to_rot(qh, R);
 }
 
-/* dR/dw, dR/dx, dR/dy, dR/dz at a unit quaternion, 4 x 9 [App. D.3]. */
+/* dR/dw, dR/dx, dR/dy, dR/dz at a unit quaternion, 4 x 9 [App. D.4]. */
 ORC_EXPORT void orc_drot(const double *q, double *D) {
     double M[4][9];
     drot_dquat(q, M);

@@ -1,4 +1,4 @@
-// Projection of 3D Gaussians to 2D splats and its backward (App. C.1, App. D.2-D.3,
+// Projection of 3D Gaussians to 2D splats and its backward (App. C.1, App. D.3-D.4,
 // App. E, App. A anti-aliasing).  One thread per Gaussian; each thread loops over
 // the cameras of the call so the Gaussian's 44 bytes of parameters are read once.
 #include "gs_internal.cuh"
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     }
 }
 
-// dR/dq_k at the unit quaternion (w, x, y, z), App. D.3 (the factor 2 included).
+// dR/dq_k at the unit quaternion (w, x, y, z), App. D.4 (the factor 2 included).
 __device__ __forceinline__ void drot(const float q[4], const float dR[9], float dq[4]) {
     float w = q[0], x = q[1], y = q[2], z = q[3];
     // <dR, dR/dw>
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         float ga = d_conics[3 * idx], gb = d_conics[3 * idx + 1], gc = d_conics[3 * idx + 2];
         float gop = d_opac[idx];
         // conic scalars (a, b, c) -> matrix gradient dY = [[ga, gb/2], [gb/2, gc]];
-        // dSigma' = -Y dY Y  (App. D.1)
+        // dSigma' = -Y dY Y  (App. D.2)
         float Ya = sp.conic[0], Yb = sp.conic[1], Yc = sp.conic[2];
         float hb = 0.5f * gb;
         float m00 = Ya * ga + Yb * hb, m01 = Ya * hb + Yb * gc;

@@ -1,4 +1,4 @@
-// Backward of the compositing sum (App. D.1), one CTA per tile.
+// Backward of the compositing sum (App. D.2), one CTA per tile.
 //
 // Each pixel replays its list back to front from its last contributor: alpha is
 // recomputed with the forward's exact arithmetic (same staging, same formulas, so the same

@@ -7,7 +7,7 @@ N-dimensional features).  Every stage runs in libgs kernels; PyTorch only provid
 the device buffers, the stream and autograd.
 
 Memory: the forward keeps, per pixel, only the final transmittance and the index of
-the last contributor (App. D.1 replays the compositing from them), so the saved
+the last contributor (App. D.2 replays the compositing from them), so the saved
 state is O(pixels + Gaussians + intersections).
 """
 from __future__ import annotations

@@ -103,7 +103,7 @@ class ResidentScenes:
         self.scenes: dict[int, DeviceScene] = {}
         self.k_rate: dict[int, float] = {}
 
-    def add(self, sid: int, host_scene, calib_camera=None, schedule: Schedule = Schedule()):
+    def add(self, sid: int, host_scene, calib_camera=None, schedule: Schedule = Schedule(), calib_poses: int = 4):
         need = host_scene.means.nbytes + host_scene.quats.nbytes + host_scene.log_scales.nbytes + \
             host_scene.opacity_logits.nbytes + host_scene.sh.nbytes
         free, _ = torch.cuda.mem_get_info(self.device)
@@ -111,10 +111,15 @@ class ResidentScenes:
             raise MemoryError(f"scene {sid} needs {need} bytes, {free - self.reserve} free")
         ds = DeviceScene.from_host(host_scene, device=self.device)
         self.scenes[sid] = ds
-        cam = calib_camera or synth.sphere_cameras(1234 + sid, [(1280, 720)])[0]
-        pipe = FramePipeline(ds, [cam], schedule, backward=False)
-        self.k_rate[sid] = max(pipe.K, 1) / float(cam.width * cam.height)
-        del pipe
+        # intersections per pixel: the largest over a few poses (the server raises it further
+        # whenever a batch overflows its estimate)
+        cams = [calib_camera] if calib_camera else synth.sphere_cameras(1234 + sid, [(1280, 720)] * calib_poses)
+        rate = 0.0
+        for cam in cams:
+            pipe = FramePipeline(ds, [cam], schedule, backward=False)
+            rate = max(rate, max(pipe.K, 1) / float(cam.width * cam.height))
+            del pipe
+        self.k_rate[sid] = rate
         return ds
 
 
@@ -220,6 +225,9 @@ class Server:
                 reserved -= b.nbytes
                 done = clock()
                 K = int(b.host_k.item())
+                px = sum(r.camera.width * r.camera.height for r in b.reqs)
+                if K > 0:  # learn the scene's intersections per pixel from every batch
+                    self.store.k_rate[b.sid] = max(self.store.k_rate[b.sid], K / px)
                 if K < 0 or K > b.capacity:
                     self.overflows += 1
                     retry.append((b.sid, b.reqs, int(max(K, b.capacity) * 1.1) + 1024))
@@ -295,7 +303,11 @@ def latency_summary(results, skip_before_s=0.0):
         return {"requests": 0}
     kept = [r for r in results if r.arrival >= skip_before_s]
     span = max(r.done for r in kept) - min(r.arrival for r in kept)
+    wait = np.array([r.launched - r.arrival for r in kept]) * 1000.0
+    service = np.array([r.done - r.launched for r in kept]) * 1000.0
     return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)), "p90_ms": float(np.percentile(lat, 90)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "queue_wait_p50_ms": float(np.percentile(wait, 50)), "queue_wait_p99_ms": float(np.percentile(wait, 99)),
+            "batch_time_p50_ms": float(np.percentile(service, 50)), "batch_time_p99_ms": float(np.percentile(service, 99)),
             "frames_per_s": float(lat.size / span) if span > 0 else None,
             "mean_views_per_batch": float(np.mean([r.batch_views for r in kept]))}

@@ -172,7 +172,7 @@ def test_sh_gradients_wrt_coefficients_and_mean():
 
 
 def test_jacobian_of_J_matches_printed_derivatives():
-    """App. D.2 prints dJ/dt for J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]]."""
+    """App. D.3 prints dJ/dt for J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]]."""
     fx, fy = 300.0, 250.0
     t = np.array([0.3, -0.2, 2.5])
 
@@ -190,7 +190,7 @@ def test_jacobian_of_J_matches_printed_derivatives():
 
 
 def test_suffix_recurrence_equals_direct_sum():
-    """App. D.1: dC/dalpha_n = c_n T_n - S_n/(1 - alpha_n) equals the derivative of the sum."""
+    """App. D.2: dC/dalpha_n = c_n T_n - S_n/(1 - alpha_n) equals the derivative of the sum."""
     rng = np.random.default_rng(9)
     n = 7
     a = rng.uniform(0.05, 0.8, n)

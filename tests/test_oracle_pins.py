@@ -33,7 +33,7 @@ def _identity_cam(W, H, f, cx, cy):
 
 
 # --------------------------------------------------------------------------- #
-# rotation (App. E) and its derivative (App. D.3)                              #
+# rotation (App. E) and its derivative (App. D.4)                              #
 # --------------------------------------------------------------------------- #
 
 def _rodrigues(axis, angle):
