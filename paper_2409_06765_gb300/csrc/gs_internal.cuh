@@ -127,9 +127,29 @@ template <int TILE, int PPT>
 struct RasterShape {
     static constexpr int kPPT = PPT;
     static constexpr int kThreads = TILE * TILE / PPT;
-    static constexpr int kWarpRows = 32 * PPT / TILE;
+    // Each warp owns a band of kBandW x kBandH pixels: 8 columns x 4 lane rows, every lane
+    // PPT consecutive pixels of its column.  Narrow, tall bands keep most lanes of a warp
+    // inside the footprint of a small Gaussian (a 32 x 4 band would leave most of them idle).
+    static constexpr int kBandW = 8;
+    static constexpr int kBandH = 4 * PPT;
+    static constexpr int kBandsX = TILE / kBandW;
     static_assert(kThreads >= 32 && kThreads <= 1024 && kThreads % 32 == 0, "bad raster shape");
+    static_assert(TILE % kBandW == 0 && TILE % kBandH == 0 && kBandsX * (TILE / kBandH) == kThreads / 32,
+                  "bands must tile the tile");
 };
+
+// Pixel band of warp `warp` of a tile whose corner is (tx0, ty0), and this lane's column and
+// first row inside it.
+template <class S>
+__device__ __forceinline__ void warp_band(int tx0, int ty0, int warp, int lane, int &wx0, int &wx1, int &wy0,
+                                          int &wy1, int &px, int &py0) {
+    wx0 = tx0 + (warp % S::kBandsX) * S::kBandW;
+    wy0 = ty0 + (warp / S::kBandsX) * S::kBandH;
+    wx1 = wx0 + S::kBandW - 1;
+    wy1 = wy0 + S::kBandH - 1;
+    px = wx0 + (lane % S::kBandW);
+    py0 = wy0 + (lane / S::kBandW) * S::kPPT;
+}
 
 // One Gaussian of a tile's list as both compositing kernels stage it in shared memory:
 //   g   = (mean x, mean y, conic a, conic b)

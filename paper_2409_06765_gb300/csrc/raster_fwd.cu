@@ -39,12 +39,9 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
     const int local = gt - cam.tile_offset;
     const int tx0 = (local % cam.tiles_x) * TILE, ty0 = (local / cam.tiles_x) * TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this warp's band of pixels
-    const int wx0 = tx0, wx1 = tx0 + TILE - 1;
-    const int wy0 = ty0 + warp * S::kWarpRows, wy1 = wy0 + S::kWarpRows - 1;
-
-    const int px = tx0 + threadIdx.x % TILE;
-    const int py0 = ty0 + (threadIdx.x / TILE) * PPT;
+    // this warp's band of pixels and this thread's column / first row in it
+    int wx0, wx1, wy0, wy1, px, py0;
+    warp_band<S>(tx0, ty0, warp, lane, wx0, wx1, wy0, wy1, px, py0);
     const float fx = (float)px + 0.5f;
     int last[PPT];
     bool done[PPT];
