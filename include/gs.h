@@ -147,6 +147,35 @@ GS_API gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t
                      const float *means, const int32_t *radii, float *colors, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* gs_sh_eval_depth -- depth rendering (App. A): gs_sh_eval plus a fourth     */
+/* feature channel holding each Gaussian's camera-space depth z, so that the  */
+/* compositing of the 4 channels yields the accumulated depth                */
+/* sum_n z_n alpha_n T_n beside the colour.                                   */
+/*                                                                          */
+/* in : as gs_sh_eval, plus depths [C,N] from gs_project                      */
+/* out: colors_rgbd [C,N,4] = (r, g, b, z); zeros for invisible pairs         */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_sh_eval_depth(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                                  const float *means, const int32_t *radii, const float *depths,
+                                  float *colors_rgbd, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* gs_expected_depth -- App. A: expected depth = accumulated depth divided   */
+/* by the accumulated opacity sum_n alpha_n T_n = 1 - final_T; 0 where that   */
+/* is 0.  One value per pixel.                                               */
+/*                                                                          */
+/* in : image [P, channels] (accumulated depth in channel depth_channel),     */
+/*      final_T [P];  out: expected_depth [P]                                */
+/* gs_expected_depth_bwd: ADDS the chain into d_image[:, depth_channel]      */
+/*      (dE/dA = 1/a) and d_alpha (dE/da = -E/a), for gs_rasterize_bwd.       */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_expected_depth(int64_t P, const float *image, int32_t channels, int32_t depth_channel,
+                                   const float *final_T, float *expected_depth, void *stream);
+GS_API gs_status gs_expected_depth_bwd(int64_t P, const float *image, int32_t channels, int32_t depth_channel,
+                                       const float *final_T, const float *d_expected_depth, float *d_image,
+                                       float *d_alpha, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* gs_tile_bin_sort -- App. C.2: bin every visible Gaussian into the tiles   */
 /* its pixel box touches and sort each tile's list by depth.                 */
 /*                                                                          */
@@ -279,6 +308,14 @@ GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, c
 GS_API gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
                          const float *means, const int32_t *radii, const float *d_colors, float *d_sh,
                          float *d_means, void *stream);
+
+/* gs_sh_eval_depth_bwd: gs_sh_eval_bwd for (r, g, b, z) rows: the colour   */
+/* part as gs_sh_eval_bwd, and d_depths [C,N] = the z channel's gradient      */
+/* (OVERWRITTEN; 0 for invisible pairs), to be passed to gs_project_bwd.      */
+GS_API gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree,
+                                      const float *sh, const float *means, const int32_t *radii,
+                                      const float *d_colors_rgbd, float *d_sh, float *d_means, float *d_depths,
+                                      void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* gs_project_bwd -- App. D.3 / D.4 and the gradient-flow figure: from        */

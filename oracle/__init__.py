@@ -351,3 +351,59 @@ def render_grads(scene, cam, d_image, d_alpha=None, pixels=None, bg=None, antial
     return dict(d_means=g3["d_means"] + d_means_sh, d_quats=g3["d_quats"], d_log_scales=g3["d_log_scales"],
                 d_opacity_logits=g3["d_opacity_logits"], d_sh=d_sh, splat_grads=g2, splats=sp,
                 colors=colors)
+
+
+# --------------------------------------------------------------------------- #
+# App. A: depth rendering                                                      #
+#   accumulated depth  A = sum_n z_n alpha_n T_n   (z_n = camera-space depth)  #
+#   expected depth     E = A / sum_n alpha_n T_n = A / (1 - T_final), 0 if 0   #
+# --------------------------------------------------------------------------- #
+
+def render_depth(scene, cam, pixels=None, bg=None, antialiased=False, eps2d=EPS2D, near=NEAR,
+                 alpha_min=ALPHA_MIN, alpha_max=ALPHA_MAX, T_min=T_MIN):
+    """Colour, accumulated depth and expected depth: the depth is a fourth feature channel
+    composited with the same weights alpha_n T_n as the colour (background 0 for it)."""
+    sp = project(scene, cam, eps2d=eps2d, near=near, antialiased=antialiased)
+    colors, _ = sh_colors(scene, cam)
+    rgbd = np.concatenate([colors, sp["depths"][:, None]], axis=1)
+    bg4 = None if bg is None else np.concatenate([_d64(bg), [0.0]])
+    r = render_splats(sp, rgbd, cam.width, cam.height, pixels=pixels, bg=bg4, alpha_min=alpha_min,
+                      alpha_max=alpha_max, T_min=T_min)
+    acc = r["color"][:, 3]
+    a = 1.0 - r["T"]
+    expected = np.where(a > 0.0, acc / np.where(a > 0.0, a, 1.0), 0.0)
+    return dict(color=r["color"][:, :3], acc_depth=acc, expected_depth=expected, alpha=a, T=r["T"],
+                ncontrib=r["ncontrib"], blends=r["blends"], splats=sp, colors=rgbd)
+
+
+def render_depth_grads(scene, cam, d_color, d_acc_depth=None, d_expected_depth=None, d_alpha=None, pixels=None,
+                       bg=None, antialiased=False, eps2d=EPS2D, near=NEAR, alpha_min=ALPHA_MIN,
+                       alpha_max=ALPHA_MAX, T_min=T_MIN):
+    """Gradients of <d_color, C> + <d_acc, A> + <d_exp, E> + <d_alpha, alpha> w.r.t. the leaves.
+
+    E = A / a with a = 1 - T_final: dE/dA = 1/a and dE/da = -E/a, so the expected-depth term
+    becomes an accumulated-depth term and an alpha term; the depth channel's per-Gaussian
+    gradient is the gradient w.r.t. z_n = t_z, passed to the projection backward."""
+    f = render_depth(scene, cam, pixels=pixels, bg=bg, antialiased=antialiased, eps2d=eps2d, near=near,
+                     alpha_min=alpha_min, alpha_max=alpha_max, T_min=T_min)
+    P = f["T"].shape[0]
+    g4 = np.zeros((P, 4))
+    g4[:, :3] = _d64(d_color).reshape(P, 3)
+    gA = np.zeros(P) if d_alpha is None else _d64(d_alpha).reshape(P).copy()
+    if d_acc_depth is not None:
+        g4[:, 3] += _d64(d_acc_depth).reshape(P)
+    if d_expected_depth is not None:
+        dE = _d64(d_expected_depth).reshape(P)
+        a = f["alpha"]
+        ok = a > 0.0
+        inv = np.where(ok, 1.0 / np.where(ok, a, 1.0), 0.0)
+        g4[:, 3] += dE * inv
+        gA += -dE * f["expected_depth"] * inv
+    bg4 = None if bg is None else np.concatenate([_d64(bg), [0.0]])
+    g2 = render_splats_bwd(f["splats"], f["colors"], cam.width, cam.height, g4, d_alpha=gA, pixels=pixels, bg=bg4,
+                           alpha_min=alpha_min, alpha_max=alpha_max, T_min=T_min)
+    d_sh, d_means_sh = sh_bwd(scene, cam, g2["d_colors"][:, :3])
+    g3 = project_bwd(scene, cam, g2["d_means2d"], g2["d_conics"], g2["d_opacities"], d_depths=g2["d_colors"][:, 3],
+                     eps2d=eps2d, near=near, antialiased=antialiased)
+    return dict(d_means=g3["d_means"] + d_means_sh, d_quats=g3["d_quats"], d_log_scales=g3["d_log_scales"],
+                d_opacity_logits=g3["d_opacity_logits"], d_sh=d_sh, forward=f)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgs.so")
-SOURCES = ["gs_abi.cu", "project.cu", "sh.cu", "binsort.cu", "raster_fwd.cu", "raster_bwd.cu", "gs_noalloc.cu", "probe.cu"]
+SOURCES = ["gs_abi.cu", "project.cu", "sh.cu", "binsort.cu", "raster_fwd.cu", "raster_bwd.cu", "gs_noalloc.cu", "probe.cu", "depth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -28,7 +28,7 @@ EXPORTED = (
     "gs_default_params", "gs_status_string", "gs_last_error", "gs_num_tiles", "gs_num_pixels", "gs_project",
     "gs_sh_eval", "gs_tile_bin_sort_workspace", "gs_tile_bin_sort", "gs_rasterize_fwd", "gs_rasterize_bwd",
     "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc", "gs_probe_peak",
-    "gs_tile_order",
+    "gs_tile_order", "gs_sh_eval_depth", "gs_sh_eval_depth_bwd", "gs_expected_depth", "gs_expected_depth_bwd",
 )
 GS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -94,6 +94,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_rasterize_bwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                         _P, _P, _P, _P, _P, _P, _P]),
             "gs_tile_order": (_I32, [_CAM, _I32, _PAR, _P, _P, _P]),
+            "gs_sh_eval_depth": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P]),
+            "gs_sh_eval_depth_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+            "gs_expected_depth": (_I32, [_I64, _P, _I32, _I32, _P, _P, _P]),
+            "gs_expected_depth_bwd": (_I32, [_I64, _P, _I32, _I32, _P, _P, _P, _P, _P]),
             "gs_sh_eval_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
             "gs_project_bwd": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                       _P]),
@@ -312,6 +316,37 @@ def gs_rasterize_bwd(cams: CameraArray, N: int, params: GsParams, channels: int,
                                  _dev(tile_order, "i32", "tile_order", optional=True), _stream(stream))
     del keep
     _check(st, "gs_rasterize_bwd")
+
+
+def gs_sh_eval_depth(cams: CameraArray, sh_degree: int, sh, means, radii, depths, colors_rgbd, stream=None):
+    N = means.shape[0]
+    _check(load().gs_sh_eval_depth(cams.ptr, cams.C, N, sh_degree, _dev(sh, "f32", "sh"), _dev(means, "f32", "means"),
+                                   _dev(radii, "i32", "radii"), _dev(depths, "f32", "depths"),
+                                   _dev(colors_rgbd, "f32", "colors_rgbd"), _stream(stream)), "gs_sh_eval_depth")
+
+
+def gs_sh_eval_depth_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors_rgbd, d_sh, d_means, d_depths,
+                         stream=None):
+    N = means.shape[0]
+    _check(load().gs_sh_eval_depth_bwd(cams.ptr, cams.C, N, sh_degree, _dev(sh, "f32", "sh"),
+                                       _dev(means, "f32", "means"), _dev(radii, "i32", "radii"),
+                                       _dev(d_colors_rgbd, "f32", "d_colors_rgbd"), _dev(d_sh, "f32", "d_sh"),
+                                       _dev(d_means, "f32", "d_means"), _dev(d_depths, "f32", "d_depths"),
+                                       _stream(stream)), "gs_sh_eval_depth_bwd")
+
+
+def gs_expected_depth(image, depth_channel: int, final_T, expected, stream=None):
+    P, ch = image.shape
+    _check(load().gs_expected_depth(P, _dev(image, "f32", "image"), ch, depth_channel, _dev(final_T, "f32", "final_T"),
+                                    _dev(expected, "f32", "expected_depth"), _stream(stream)), "gs_expected_depth")
+
+
+def gs_expected_depth_bwd(image, depth_channel: int, final_T, d_expected, d_image, d_alpha, stream=None):
+    P, ch = image.shape
+    _check(load().gs_expected_depth_bwd(P, _dev(image, "f32", "image"), ch, depth_channel,
+                                        _dev(final_T, "f32", "final_T"), _dev(d_expected, "f32", "d_expected"),
+                                        _dev(d_image, "f32", "d_image"), _dev(d_alpha, "f32", "d_alpha"),
+                                        _stream(stream)), "gs_expected_depth_bwd")
 
 
 def gs_tile_order(cams: CameraArray, params: GsParams, tile_ranges, tile_order, stream=None):

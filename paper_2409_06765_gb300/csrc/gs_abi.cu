@@ -15,9 +15,13 @@ cudaError_t launch_project_fwd(const CamSet &, const RasterConsts &, int, const 
 cudaError_t launch_project_bwd(const CamSet &, const RasterConsts &, int, const float *, const float *, const float *,
                                const float *, const int *, const float *, const float *, const float *, const float *,
                                float *, float *, float *, float *, cudaStream_t);
-cudaError_t launch_sh_fwd(const CamSet &, int, int, const float *, const float *, const int *, float *, cudaStream_t);
+cudaError_t launch_sh_fwd(const CamSet &, int, int, const float *, const float *, const int *, float *, const float *,
+                          cudaStream_t);
 cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *, const int *, const float *, float *,
-                          float *, cudaStream_t);
+                          float *, float *, cudaStream_t);
+cudaError_t launch_expected_depth(long long, const float *, int, int, const float *, float *, cudaStream_t);
+cudaError_t launch_expected_depth_bwd(long long, const float *, int, int, const float *, const float *, float *,
+                                      float *, cudaStream_t);
 BinSortLayout binsort_layout(long long CN, long long Kcap, int G);
 cudaError_t launch_binsort(const CamSet &, int, const float *, const float *, const int *, long long,
                            unsigned long long *, int *, int *, long long *, void *, cudaStream_t);
@@ -251,8 +255,47 @@ gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_deg
     if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
     if (N == 0) return GS_OK;
     GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(colors);
-    cudaError_t e = launch_sh_fwd(cs, sh_degree, N, sh, means, radii, colors, (cudaStream_t)stream);
+    cudaError_t e = launch_sh_fwd(cs, sh_degree, N, sh, means, radii, colors, nullptr, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval");
+}
+
+gs_status gs_sh_eval_depth(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                           const float *means, const int32_t *radii, const float *depths, float *colors_rgbd,
+                           void *stream) {
+    CamSet cs;
+    GS_TRY(make_camset(cams, C, 16, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(depths); GS_NONNULL(colors_rgbd);
+    cudaError_t e = launch_sh_fwd(cs, sh_degree, N, sh, means, radii, colors_rgbd, depths, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_depth");
+}
+
+gs_status gs_expected_depth(int64_t P, const float *image, int32_t channels, int32_t depth_channel,
+                            const float *final_T, float *expected_depth, void *stream) {
+    if (P < 0) return fail_arg("P must be >= 0");
+    if (channels < 1 || depth_channel < 0 || depth_channel >= channels)
+        return fail_arg("depth_channel must be in [0, channels)");
+    if (P == 0) return GS_OK;
+    GS_NONNULL(image); GS_NONNULL(final_T); GS_NONNULL(expected_depth);
+    cudaError_t e = launch_expected_depth(P, image, channels, depth_channel, final_T, expected_depth,
+                                          (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_expected_depth");
+}
+
+gs_status gs_expected_depth_bwd(int64_t P, const float *image, int32_t channels, int32_t depth_channel,
+                                const float *final_T, const float *d_expected_depth, float *d_image, float *d_alpha,
+                                void *stream) {
+    if (P < 0) return fail_arg("P must be >= 0");
+    if (channels < 1 || depth_channel < 0 || depth_channel >= channels)
+        return fail_arg("depth_channel must be in [0, channels)");
+    if (P == 0) return GS_OK;
+    GS_NONNULL(image); GS_NONNULL(final_T); GS_NONNULL(d_expected_depth); GS_NONNULL(d_image); GS_NONNULL(d_alpha);
+    cudaError_t e = launch_expected_depth_bwd(P, image, channels, depth_channel, final_T, d_expected_depth, d_image,
+                                              d_alpha, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_expected_depth_bwd");
 }
 
 int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
@@ -385,8 +428,25 @@ gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh
     if (N == 0) return GS_OK;
     GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(d_colors); GS_NONNULL(d_sh);
     GS_NONNULL(d_means);
-    cudaError_t e = launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors, d_sh, d_means, (cudaStream_t)stream);
+    cudaError_t e =
+        launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors, d_sh, d_means, nullptr, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_bwd");
+}
+
+gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
+                               const float *means, const int32_t *radii, const float *d_colors_rgbd, float *d_sh,
+                               float *d_means, float *d_depths, void *stream) {
+    CamSet cs;
+    GS_TRY(make_camset(cams, C, 16, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(d_colors_rgbd); GS_NONNULL(d_sh);
+    GS_NONNULL(d_means); GS_NONNULL(d_depths);
+    cudaError_t e = launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors_rgbd, d_sh, d_means, d_depths,
+                                  (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_depth_bwd");
 }
 
 gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const float *means, const float *quats,

@@ -137,8 +137,9 @@ template <int DEG>
 __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restrict__ sh,
                                                      const float *__restrict__ means, const int *__restrict__ radii,
                                                      const __grid_constant__ CamSet cs, ShConsts kc,
-                                                     float *__restrict__ colors) {
+                                                     float *__restrict__ colors, const float *__restrict__ depths) {
     constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    const int OS = depths ? 4 : 3;  // (r, g, b) or (r, g, b, depth) per (camera, Gaussian)
     extern __shared__ float s_coef[];
     int n0 = blockIdx.x * 256;
     int cnt = min(256, N - n0);
@@ -151,13 +152,15 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
     float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
     for (int c = 0; c < cs.C; ++c) {
         size_t idx = (size_t)c * N + n;
-        float *out = colors + 3 * idx;
+        float *out = colors + OS * idx;
         if (radii[idx] <= 0) {
             out[0] = 0.f;
             out[1] = 0.f;
             out[2] = 0.f;
+            if (depths) out[3] = 0.f;
             continue;
         }
+        if (depths) out[3] = depths[idx];
         const float *R = cs.cam[c].R, *t = cs.cam[c].t;
         // camera centre = -R^T t
         float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
@@ -192,8 +195,10 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
                                                                const int *__restrict__ radii,
                                                                const __grid_constant__ CamSet cs, ShConsts kc,
                                                                const float *__restrict__ d_colors,
-                                                               float *__restrict__ d_sh, float *__restrict__ d_means) {
+                                                               float *__restrict__ d_sh, float *__restrict__ d_means,
+                                                               float *__restrict__ d_depths) {
     constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    const int IS = d_depths ? 4 : 3;  // d_colors rows: (r, g, b) or (r, g, b, depth)
     extern __shared__ float s_coef[];
     float *s_grad = s_coef + kShBwdThreads * STRIDE;
     const int n0 = blockIdx.x * kShBwdThreads;
@@ -211,6 +216,7 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
         float dm[3] = {0.f, 0.f, 0.f};
         for (int c = 0; c < cs.C; ++c) {
             const size_t idx = (size_t)c * N + n;
+            if (d_depths) d_depths[idx] = radii[idx] > 0 ? d_colors[IS * idx + 3] : 0.f;
             if (radii[idx] <= 0) continue;
             const float *R = cs.cam[c].R, *t = cs.cam[c].t;
             const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
                 float raw = 0.5f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) raw += Y[k] * cf[3 * k + ch];
-                g[ch] = raw > 0.f ? d_colors[3 * idx + ch] : 0.f;  // the clamp at 0 passes no gradient
+                g[ch] = raw > 0.f ? d_colors[IS * idx + ch] : 0.f;  // the clamp at 0 passes no gradient
             }
             float w[K];
 #pragma unroll
@@ -277,21 +283,22 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
 
 template <int DEG>
 static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
-                                   float *colors, cudaStream_t st) {
+                                   float *colors, const float *depths, cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 256 * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = ensure_smem((const void *)sh_fwd_kernel<DEG>, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sh_fwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), colors);
+    sh_fwd_kernel<DEG><<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), colors, depths);
     note_launch();
     return cudaGetLastError();
 }
 
 template <int DEG>
 static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
-                                   const float *d_colors, float *d_sh, float *d_means, cudaStream_t st) {
+                                   const float *d_colors, float *d_sh, float *d_means, float *d_depths,
+                                   cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 2 * kShBwdThreads * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
@@ -299,28 +306,28 @@ static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, con
         if (e != cudaSuccess) return e;
     }
     sh_bwd_kernel<DEG><<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
-                                                            d_sh, d_means);
+                                                            d_sh, d_means, d_depths);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_sh_fwd(const CamSet &cs, int deg, int N, const float *sh, const float *means, const int *radii,
-                          float *colors, cudaStream_t st) {
+                          float *colors, const float *depths, cudaStream_t st) {
     switch (deg) {
-        case 0: return launch_sh_fwd_t<0>(cs, N, sh, means, radii, colors, st);
-        case 1: return launch_sh_fwd_t<1>(cs, N, sh, means, radii, colors, st);
-        case 2: return launch_sh_fwd_t<2>(cs, N, sh, means, radii, colors, st);
-        default: return launch_sh_fwd_t<3>(cs, N, sh, means, radii, colors, st);
+        case 0: return launch_sh_fwd_t<0>(cs, N, sh, means, radii, colors, depths, st);
+        case 1: return launch_sh_fwd_t<1>(cs, N, sh, means, radii, colors, depths, st);
+        case 2: return launch_sh_fwd_t<2>(cs, N, sh, means, radii, colors, depths, st);
+        default: return launch_sh_fwd_t<3>(cs, N, sh, means, radii, colors, depths, st);
     }
 }
 
 cudaError_t launch_sh_bwd(const CamSet &cs, int deg, int N, const float *sh, const float *means, const int *radii,
-                          const float *d_colors, float *d_sh, float *d_means, cudaStream_t st) {
+                          const float *d_colors, float *d_sh, float *d_means, float *d_depths, cudaStream_t st) {
     switch (deg) {
-        case 0: return launch_sh_bwd_t<0>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
-        case 1: return launch_sh_bwd_t<1>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
-        case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
-        default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, st);
+        case 0: return launch_sh_bwd_t<0>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
+        case 1: return launch_sh_bwd_t<1>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
+        case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
+        default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
     }
 }
 

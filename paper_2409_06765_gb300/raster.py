@@ -75,9 +75,14 @@ def project(cams, means, quats, log_scales, opacity_logits, params):
     return out
 
 
-def sh_eval(cams, sh_degree, sh, means, radii):
-    colors = torch.empty(cams.C, means.shape[0], 3, device=means.device)
-    _lib.gs_sh_eval(cams, sh_degree, sh, means, radii, colors)
+def sh_eval(cams, sh_degree, sh, means, radii, depths=None):
+    """SH colours [C,N,3]; with ``depths``, (r, g, b, z) rows [C,N,4] for depth rendering (App. A)."""
+    ch = 3 if depths is None else 4
+    colors = torch.empty(cams.C, means.shape[0], ch, device=means.device)
+    if depths is None:
+        _lib.gs_sh_eval(cams, sh_degree, sh, means, radii, colors)
+    else:
+        _lib.gs_sh_eval_depth(cams, sh_degree, sh, means, radii, depths, colors)
     return colors
 
 
@@ -129,14 +134,16 @@ def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, con
 
 
 def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_degree=0, features=None,
-                 settings: RasterSettings | None = None, state: RasterState | None = None, count_blends=False):
-    """Project, colour, bin/sort and composite.  Returns a dict of every intermediate."""
+                 settings: RasterSettings | None = None, state: RasterState | None = None, count_blends=False,
+                 depth=False):
+    """Project, colour, bin/sort and composite.  Returns a dict of every intermediate.  With
+    ``depth`` (SH colours only) the image gains a fourth channel, the accumulated depth."""
     settings = settings or RasterSettings()
     params = settings.params()
     N = means.shape[0]
     sp = project(cams, means, quats, log_scales, opacity_logits, params)
     if features is None:
-        colors = sh_eval(cams, sh_degree, sh, means, sp["radii"])
+        colors = sh_eval(cams, sh_degree, sh, means, sp["radii"], sp["depths"] if depth else None)
     else:
         colors = features
     ch = colors.shape[-1]
@@ -150,31 +157,45 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
 
 
 class RasterizeGaussians(torch.autograd.Function):
-    """image [P, ch], alpha [P] = f(means, quats, log_scales, opacity_logits, sh | features)."""
+    """image [P, ch], alpha [P], radii, expected depth [P] (empty unless asked)
+    = f(means, quats, log_scales, opacity_logits, sh | features).
+
+    depth: 0 = colour only; 1 = a fourth channel with the accumulated depth (App. A);
+    2 = as 1 and the expected depth (accumulated depth / alpha) as a fourth output."""
 
     @staticmethod
-    def forward(ctx, means, quats, log_scales, opacity_logits, sh_or_features, cams, sh_degree, settings, state):
+    def forward(ctx, means, quats, log_scales, opacity_logits, sh_or_features, cams, sh_degree, settings, state,
+                depth=0):
         use_sh = sh_degree is not None
+        if depth and not use_sh:
+            raise ValueError("depth rendering needs SH colours")
         feats = None
         if not use_sh:
             f = sh_or_features
             feats = (f.unsqueeze(0).expand(cams.C, *f.shape) if f.dim() == 2 else f).contiguous()
+        if depth and settings.background is not None:
+            settings = RasterSettings(**{**settings.__dict__, "background": tuple(settings.background)[:3] + (0.0,)})
         out = forward_pass(cams, means, quats, log_scales, opacity_logits, sh=sh_or_features if use_sh else None,
-                           sh_degree=sh_degree if use_sh else 0, features=feats, settings=settings, state=state)
-        ctx.cams, ctx.settings, ctx.sh_degree, ctx.use_sh = cams, settings, sh_degree, use_sh
+                           sh_degree=sh_degree if use_sh else 0, features=feats, settings=settings, state=state,
+                           depth=bool(depth))
+        edepth = torch.empty(0, device=means.device)
+        if depth == 2:
+            edepth = torch.empty(cams.num_pixels, device=means.device)
+            _lib.gs_expected_depth(out["image"], 3, out["final_T"], edepth)
+        ctx.cams, ctx.settings, ctx.sh_degree, ctx.use_sh, ctx.depth = cams, settings, sh_degree, use_sh, depth
         ctx.feat_dim = None if use_sh else sh_or_features.dim()
         ctx.tile_order = out["tile_order"]
         ctx.save_for_backward(means, quats, log_scales, opacity_logits, sh_or_features, out["radii"], out["means2d"],
                               out["conics"], out["opacities"], out["colors"], out["values"], out["ranges"],
-                              out["final_T"], out["last_contrib"])
+                              out["final_T"], out["last_contrib"], out["image"] if depth == 2 else None)
         ctx.mark_non_differentiable(out["radii"])
         alpha = 1.0 - out["final_T"]
-        return out["image"], alpha, out["radii"]
+        return out["image"], alpha, out["radii"], edepth
 
     @staticmethod
-    def backward(ctx, d_image, d_alpha, _d_radii):
+    def backward(ctx, d_image, d_alpha, _d_radii, d_edepth):
         (means, quats, log_scales, logits, shf, radii, means2d, conics, opac, colors, values, ranges, final_T,
-         last) = ctx.saved_tensors
+         last, image) = ctx.saved_tensors
         cams, settings = ctx.cams, ctx.settings
         params = settings.params()
         C, N = cams.C, means.shape[0]
@@ -187,6 +208,10 @@ class RasterizeGaussians(torch.autograd.Function):
         absgrad = torch.zeros(C, N, 2, device=dev) if settings.absgrad else None
         d_image = d_image.contiguous() if d_image is not None else torch.zeros(cams.num_pixels, ch, device=dev)
         d_alpha = d_alpha.contiguous() if d_alpha is not None else None
+        if ctx.depth == 2 and d_edepth is not None and d_edepth.numel():
+            d_image = d_image.clone()
+            d_alpha = d_alpha.clone() if d_alpha is not None else torch.zeros(cams.num_pixels, device=dev)
+            _lib.gs_expected_depth_bwd(image, 3, final_T, d_edepth.contiguous(), d_image, d_alpha)
         vals = values if values.numel() else torch.empty(1, dtype=torch.int32, device=dev)
         _lib.gs_rasterize_bwd(cams, N, params, ch, ranges, vals, radii, means2d, conics, opac, colors,
                               settings.background, final_T, last, d_image, d_alpha, d_means2d, d_conics, d_opac,
@@ -194,9 +219,14 @@ class RasterizeGaussians(torch.autograd.Function):
         if absgrad is not None:
             RasterizeGaussians.last_absgrad = absgrad
         d_means = torch.empty(N, 3, device=dev)
+        d_depths = None
         if ctx.use_sh:
             d_sh = torch.empty_like(shf)
-            _lib.gs_sh_eval_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means)
+            if ctx.depth:
+                d_depths = torch.empty(C, N, device=dev)
+                _lib.gs_sh_eval_depth_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means, d_depths)
+            else:
+                _lib.gs_sh_eval_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means)
             d_feat = d_sh
         else:
             d_means.zero_()
@@ -204,21 +234,30 @@ class RasterizeGaussians(torch.autograd.Function):
         d_quats = torch.empty(N, 4, device=dev)
         d_log_scales = torch.empty(N, 3, device=dev)
         d_logits = torch.empty(N, device=dev)
-        _lib.gs_project_bwd(cams, means, quats, log_scales, logits, params, radii, d_means2d, d_conics, d_opac, None,
-                            d_means, d_quats, d_log_scales, d_logits)
-        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None
+        _lib.gs_project_bwd(cams, means, quats, log_scales, logits, params, radii, d_means2d, d_conics, d_opac,
+                            d_depths, d_means, d_quats, d_log_scales, d_logits)
+        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None, None
+
+
+RENDER_MODES = {"RGB": 0, "D": 1, "ED": 2, "RGB+D": 1, "RGB+ED": 2}
 
 
 def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=None, *, features=None,
-                  sh_degree=None, settings: RasterSettings | None = None, state: RasterState | None = None):
+                  sh_degree=None, settings: RasterSettings | None = None, state: RasterState | None = None,
+                  render_mode: str = "RGB"):
     """Render C cameras.  Returns (images, alphas, meta) with one [H, W, ch] / [H, W] tensor per camera.
 
     Pass SH coefficients ``sh`` [N, K, 3] (degree inferred from K) or N-dimensional
     ``features`` [N, D] / [C, N, D].  Parameters are the leaves of the paper's
-    gradient-flow figure: log-scales and opacity logits.
+    gradient-flow figure: log-scales and opacity logits.  ``render_mode`` (SH colours):
+    "RGB"; "D" / "RGB+D" with the accumulated depth sum z alpha T; "ED" / "RGB+ED" with the
+    expected depth, the accumulated depth over alpha (App. A).
     """
     if cameras is None:
         raise ValueError("cameras are required")
+    if render_mode not in RENDER_MODES:
+        raise ValueError(f"render_mode must be one of {sorted(RENDER_MODES)}")
+    depth = RENDER_MODES[render_mode]
     cams = cameras if isinstance(cameras, _lib.CameraArray) else _lib.CameraArray(cameras)
     settings = settings or RasterSettings()
     if features is None:
@@ -226,11 +265,17 @@ def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=Non
             raise ValueError("give sh or features")
         K = sh.shape[1]
         sh_degree = {1: 0, 4: 1, 9: 2, 16: 3}[K] if sh_degree is None else sh_degree
-        img, alpha, radii = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, sh, cams, sh_degree,
-                                                     settings, state)
+        img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, sh, cams,
+                                                             sh_degree, settings, state, depth)
     else:
-        img, alpha, radii = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, features, cams, None,
-                                                     settings, state)
+        if depth:
+            raise ValueError("depth render modes need SH colours")
+        img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, features,
+                                                             cams, None, settings, state, 0)
+    if depth == 2:
+        img = torch.cat([img[:, :3], edepth[:, None]], dim=1)
+    if render_mode in ("D", "ED"):
+        img = img[:, 3:4]
     images, alphas = [], []
     for (w, h), off in zip(cams.sizes, cams.pixel_offsets()):
         images.append(img[off:off + w * h].view(h, w, -1))

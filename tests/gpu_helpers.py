@@ -55,7 +55,7 @@ def gpu_grads(scene, cams, d_image, d_alpha=None, settings=None):
     for x in leaves:
         x.requires_grad_(True)
     ca = _lib.CameraArray(cams)
-    img, alpha, _ = raster.RasterizeGaussians.apply(*leaves, ca, d["sh_degree"], settings or raster.RasterSettings(),
+    img, alpha, _, _ = raster.RasterizeGaussians.apply(*leaves, ca, d["sh_degree"], settings or raster.RasterSettings(),
                                                     None)
     outs, grads_in = [img], [torch.as_tensor(np.asarray(d_image, np.float32), device="cuda").reshape(img.shape)]
     if d_alpha is not None:
