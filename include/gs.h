@@ -307,7 +307,7 @@ GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, c
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
                          const float *means, const int32_t *radii, const float *d_colors, float *d_sh,
-                         float *d_means, void *stream);
+                         float *d_means, float *d_viewmats, void *stream);
 
 /* gs_sh_eval_depth_bwd: gs_sh_eval_bwd for (r, g, b, z) rows: the colour   */
 /* part as gs_sh_eval_bwd, and d_depths [C,N] = the z channel's gradient      */
@@ -315,7 +315,7 @@ GS_API gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int
 GS_API gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree,
                                       const float *sh, const float *means, const int32_t *radii,
                                       const float *d_colors_rgbd, float *d_sh, float *d_means, float *d_depths,
-                                      void *stream);
+                                      float *d_viewmats, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* gs_project_bwd -- App. D.3 / D.4 and the gradient-flow figure: from        */
@@ -325,6 +325,11 @@ GS_API gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t 
 /* (T = J R_cw), dJ -> dt, d mu = R_cw^T dt, dM = dSigma M + dSigma^T M,      */
 /* dR = dM S, dS = diag(R^T dM), dq through dR/dq and the normalisation,     */
 /* d log_scale = dS s, d logit = d o * o (1 - o).  Sums over the C cameras.   */
+/* d_viewmats (optional, NULL to skip): pose gradient (App. A), ACCUMULATED  */
+/* (+=) into [C,4,4] laid out like gs_camera.viewmat: rows 0-2 get           */
+/* dR_cw = sum_n (J^T dT + dt mu^T) and dt_cw = sum_n dt (t = R_cw mu + t_cw, */
+/* T = J R_cw); row 3 is left untouched.  gs_sh_eval_bwd / _depth_bwd add    */
+/* the view-direction term (centre = -R_cw^T t_cw) into the same array.       */
 /* d_means is ACCUMULATED (+=, so the SH term from gs_sh_eval_bwd adds up);   */
 /* d_quats, d_log_scales and d_opacity_logits are OVERWRITTEN.               */
 /* ------------------------------------------------------------------------ */
@@ -332,7 +337,8 @@ GS_API gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, con
                          const float *log_scales, const float *opacity_logits, const gs_params *params,
                          const int32_t *radii, const float *d_means2d, const float *d_conics,
                          const float *d_opacities, const float *d_depths, float *d_means, float *d_quats,
-                         float *d_log_scales, float *d_opacity_logits, void *stream);
+                         float *d_log_scales, float *d_opacity_logits, float *d_viewmats,
+                                void *stream);
 
 #ifdef __cplusplus
 }

@@ -66,7 +66,7 @@ def _load():
         lib.orc_sh_basis.argtypes = [_i, _i, _D, _D]
         lib.orc_sh_basis_grad.argtypes = [_i, _i, _D, _D]
         lib.orc_sh_colors.argtypes = [_i, _i, _D, _D, _D, _D, _D]
-        lib.orc_sh_bwd.argtypes = [_i, _i, _D, _D, _D, _D, _D, _D]
+        lib.orc_sh_bwd.argtypes = [_i, _i, _D, _D, _D, _D, _D, _D, _D]
         lib.orc_render.argtypes = [_i, _D, _D, _D, _D, _i, _D, _I, _I, _i, _i, _D, _d, _d, _d, _i, _I,
                                    _D, _D, _I, ctypes.POINTER(ctypes.c_longlong)]
         lib.orc_render_trace.argtypes = [_i, _D, _D, _D, _D, _i, _D, _I, _I, _i, _i, _D, _d, _d, _d, _i,
@@ -75,7 +75,7 @@ def _load():
         lib.orc_render_bwd.argtypes = [_i, _D, _D, _D, _D, _i, _D, _I, _I, _i, _i, _D, _d, _d, _d, _i, _I,
                                        _D, _D, _D, _D, _D, _D, _D]
         lib.orc_project_bwd.argtypes = [_i, _D, _D, _D, _D, _D, _D, _i, _i, _d, _d, _i, _D, _D, _D, _D,
-                                        _D, _D, _D, _D]
+                                        _D, _D, _D, _D, _D]
         lib.orc_bin_sort.argtypes = [_i, _i, _F, _F, _I, _I, _I, _i, _ll, _U64, _I, _I]
         lib.orc_bin_sort.restype = _ll
         lib.orc_num_threads.restype = _i
@@ -199,13 +199,15 @@ def sh_colors(scene, cam, means=None, sh=None):
     return colors, raw
 
 
-def sh_bwd(scene, cam, d_colors):
+def sh_bwd(scene, cam, d_colors, d_viewmat=None):
+    """SH backward; with ``d_viewmat`` (float64 [16]) also accumulates the pose gradient of the
+    view direction into it."""
     c = camera(cam)
     N = scene.n
     K = (scene.sh_degree + 1) ** 2
     d_sh, d_means = np.zeros((N, K, 3)), np.zeros((N, 3))
     _load().orc_sh_bwd(N, scene.sh_degree, _p(_d64(scene.sh)), _p(_d64(scene.means)), _p(c.viewmat),
-                       _p(_d64(d_colors)), _p(d_sh), _p(d_means))
+                       _p(_d64(d_colors)), _p(d_sh), _p(d_means), _p(d_viewmat))
     return d_sh, d_means
 
 
@@ -278,7 +280,8 @@ def render_splats_bwd(splats, colors, width, height, d_color, d_alpha=None, pixe
 # --------------------------------------------------------------------------- #
 
 def project_bwd(scene, cam, d_means2d, d_conics, d_opacities, d_depths=None, eps2d=EPS2D, near=NEAR,
-                antialiased=False):
+                antialiased=False, d_viewmat=None):
+    """Projection backward; with ``d_viewmat`` (float64 [16]) also accumulates the pose gradient."""
     lib = _load()
     c = camera(cam)
     N = scene.n
@@ -289,7 +292,7 @@ def project_bwd(scene, cam, d_means2d, d_conics, d_opacities, d_depths=None, eps
                         _p(_d64(scene.opacity_logits)), _p(c.viewmat), _p(c.intr), c.width, c.height,
                         float(eps2d), float(near), int(bool(antialiased)), _p(_d64(d_means2d)),
                         _p(_d64(d_conics)), _p(_d64(d_opacities)), _p(dd), _p(out["d_means"]),
-                        _p(out["d_quats"]), _p(out["d_log_scales"]), _p(out["d_opacity_logits"]))
+                        _p(out["d_quats"]), _p(out["d_log_scales"]), _p(out["d_opacity_logits"]), _p(d_viewmat))
     return out
 
 
@@ -345,12 +348,13 @@ def render_grads(scene, cam, d_image, d_alpha=None, pixels=None, bg=None, antial
     colors, _ = sh_colors(scene, cam)
     g2 = render_splats_bwd(sp, colors, cam.width, cam.height, d_image, d_alpha=d_alpha, pixels=pixels, bg=bg,
                            alpha_min=alpha_min, alpha_max=alpha_max, T_min=T_min, want_absgrad=True)
-    d_sh, d_means_sh = sh_bwd(scene, cam, g2["d_colors"])
+    d_view = np.zeros(16)
+    d_sh, d_means_sh = sh_bwd(scene, cam, g2["d_colors"], d_viewmat=d_view)
     g3 = project_bwd(scene, cam, g2["d_means2d"], g2["d_conics"], g2["d_opacities"], eps2d=eps2d, near=near,
-                     antialiased=antialiased)
+                     antialiased=antialiased, d_viewmat=d_view)
     return dict(d_means=g3["d_means"] + d_means_sh, d_quats=g3["d_quats"], d_log_scales=g3["d_log_scales"],
-                d_opacity_logits=g3["d_opacity_logits"], d_sh=d_sh, splat_grads=g2, splats=sp,
-                colors=colors)
+                d_opacity_logits=g3["d_opacity_logits"], d_sh=d_sh, d_viewmat=d_view.reshape(4, 4),
+                splat_grads=g2, splats=sp, colors=colors)
 
 
 # --------------------------------------------------------------------------- #

@@ -345,8 +345,11 @@ ORC_EXPORT void orc_sh_colors(int N, int deg, const double *sh, const double *me
     }
 }
 
+/* d_viewmat (16, may be NULL) accumulates the pose gradient of the view direction [App. A,
+   pose optimization]: the centre c = -R^T t, v = mu - c, so dL/dc = -dL/dv and
+   dL/dR_ij += t_i dL/dv_j, dL/dt_i += sum_j R_ij dL/dv_j. */
 ORC_EXPORT void orc_sh_bwd(int N, int deg, const double *sh, const double *means, const double *viewmat,
-                           const double *d_colors, double *d_sh, double *d_means) {
+                           const double *d_colors, double *d_sh, double *d_means, double *d_viewmat) {
     int K = (deg + 1) * (deg + 1);
     double cc[3];
     camera_centre(viewmat, cc);
@@ -374,7 +377,22 @@ ORC_EXPORT void orc_sh_bwd(int N, int deg, const double *sh, const double *means
         }
         /* d dir / d v = (I - dir dir^T) / |v| */
         double dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
-        for (int i = 0; i < 3; i++) d_means[3 * n + i] += (ddir[i] - dir[i] * dd) / len;
+        double dv[3];
+        for (int i = 0; i < 3; i++) {
+            dv[i] = (ddir[i] - dir[i] * dd) / len;
+            d_means[3 * n + i] += dv[i];
+        }
+        if (d_viewmat) {
+            for (int i = 0; i < 3; i++) {
+                for (int j = 0; j < 3; j++) {
+#pragma omp atomic
+                    d_viewmat[4 * i + j] += viewmat[4 * i + 3] * dv[j];
+                }
+                double r = viewmat[4 * i] * dv[0] + viewmat[4 * i + 1] * dv[1] + viewmat[4 * i + 2] * dv[2];
+#pragma omp atomic
+                d_viewmat[4 * i + 3] += r;
+            }
+        }
     }
 }
 
@@ -600,13 +618,16 @@ static void drot_dquat(const double q[4], double D[4][9]) {
     }
 }
 
-/* Accumulates (+=) gradients of one camera into the 3D leaves.  d_depths may be NULL. */
+/* Accumulates (+=) gradients of one camera into the 3D leaves.  d_depths may be NULL.
+   d_viewmat (16, may be NULL) accumulates the pose gradient [App. A, pose optimization]:
+   through t = R mu + t_w (dR += dt mu^T, dt_w += dt) and through T = J R in
+   Sigma' = T Sigma T^T (dR += J^T dT). */
 ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats, const double *log_scales,
                                 const double *logits, const double *viewmat, const double *intr, int W,
                                 int H, double eps2d, double near_plane, int antialiased,
                                 const double *d_means2d, const double *d_conics, const double *d_opac,
                                 const double *d_depths, double *d_means, double *d_quats,
-                                double *d_log_scales, double *d_logits) {
+                                double *d_log_scales, double *d_logits, double *d_viewmat) {
     const double *vm = viewmat;
     const double Wr[9] = {vm[0], vm[1], vm[2], vm[4], vm[5], vm[6], vm[8], vm[9], vm[10]};
     const double fx = intr[0], fy = intr[1];
@@ -675,6 +696,22 @@ ORC_EXPORT void orc_project_bwd(int N, const double *means, const double *quats,
         /* t = R_cw mu + t_cw:  dmu = R_cw^T dt */
         for (int i = 0; i < 3; i++)
             d_means[3 * n + i] += Wr[0 + i] * dt[0] + Wr[3 + i] * dt[1] + Wr[6 + i] * dt[2];
+        if (d_viewmat) {
+            /* J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]];  dR = J^T dT + dt mu^T */
+            double J[6] = {fx / tz, 0.0, -fx * tx / tz2, 0.0, fy / tz, -fy * ty / tz2};
+            double Jt[6], dRw[9];
+            transpose(J, Jt, 2, 3);
+            matmul(Jt, dT, dRw, 3, 2, 3);
+            for (int i = 0; i < 3; i++) {
+                for (int j = 0; j < 3; j++) {
+                    double v = dRw[3 * i + j] + dt[i] * means[3 * n + j];
+#pragma omp atomic
+                    d_viewmat[4 * i + j] += v;
+                }
+#pragma omp atomic
+                d_viewmat[4 * i + 3] += dt[i];
+            }
+        }
         /* Sigma = M M^T:  dM = dSigma M + dSigma^T M [App. D.4] */
         double dSigt[9], dM[9], t2[9];
         transpose(dSig, dSigt, 3, 3);

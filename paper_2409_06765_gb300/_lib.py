@@ -95,12 +95,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         _P, _P, _P, _P, _P, _P, _P]),
             "gs_tile_order": (_I32, [_CAM, _I32, _PAR, _P, _P, _P]),
             "gs_sh_eval_depth": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P]),
-            "gs_sh_eval_depth_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+            "gs_sh_eval_depth_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
             "gs_expected_depth": (_I32, [_I64, _P, _I32, _I32, _P, _P, _P]),
             "gs_expected_depth_bwd": (_I32, [_I64, _P, _I32, _I32, _P, _P, _P, _P, _P]),
-            "gs_sh_eval_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
+            "gs_sh_eval_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
             "gs_project_bwd": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                      _P]),
+                                      _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -119,6 +119,7 @@ class CameraArray:
 
     def __init__(self, cams):
         cams = list(cams)
+        self.cams = cams  # the tuples or camera objects it was built from
         if not 1 <= len(cams) <= GS_MAX_CAMERAS:
             raise ValueError(f"1..{GS_MAX_CAMERAS} cameras per call, got {len(cams)}")
         self.arr = (GsCamera * len(cams))()
@@ -326,13 +327,14 @@ def gs_sh_eval_depth(cams: CameraArray, sh_degree: int, sh, means, radii, depths
 
 
 def gs_sh_eval_depth_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors_rgbd, d_sh, d_means, d_depths,
-                         stream=None):
+                         stream=None, d_viewmats=None):
     N = means.shape[0]
     _check(load().gs_sh_eval_depth_bwd(cams.ptr, cams.C, N, sh_degree, _dev(sh, "f32", "sh"),
                                        _dev(means, "f32", "means"), _dev(radii, "i32", "radii"),
                                        _dev(d_colors_rgbd, "f32", "d_colors_rgbd"), _dev(d_sh, "f32", "d_sh"),
                                        _dev(d_means, "f32", "d_means"), _dev(d_depths, "f32", "d_depths"),
-                                       _stream(stream)), "gs_sh_eval_depth_bwd")
+                                       _dev(d_viewmats, "f32", "d_viewmats", optional=True), _stream(stream)),
+           "gs_sh_eval_depth_bwd")
 
 
 def gs_expected_depth(image, depth_channel: int, final_T, expected, stream=None):
@@ -356,16 +358,19 @@ def gs_tile_order(cams: CameraArray, params: GsParams, tile_ranges, tile_order, 
     _check(st, "gs_tile_order")
 
 
-def gs_sh_eval_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors, d_sh, d_means, stream=None):
+def gs_sh_eval_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors, d_sh, d_means, stream=None,
+                   d_viewmats=None):
     N = means.shape[0]
     st = load().gs_sh_eval_bwd(cams.ptr, cams.C, N, sh_degree, _dev(sh, "f32", "sh"), _dev(means, "f32", "means"),
                                _dev(radii, "i32", "radii"), _dev(d_colors, "f32", "d_colors"),
-                               _dev(d_sh, "f32", "d_sh"), _dev(d_means, "f32", "d_means"), _stream(stream))
+                               _dev(d_sh, "f32", "d_sh"), _dev(d_means, "f32", "d_means"),
+                               _dev(d_viewmats, "f32", "d_viewmats", optional=True), _stream(stream))
     _check(st, "gs_sh_eval_bwd")
 
 
 def gs_project_bwd(cams: CameraArray, means, quats, log_scales, opacity_logits, params: GsParams, radii, d_means2d,
-                   d_conics, d_opacities, d_depths, d_means, d_quats, d_log_scales, d_opacity_logits, stream=None):
+                   d_conics, d_opacities, d_depths, d_means, d_quats, d_log_scales, d_opacity_logits, stream=None,
+                   d_viewmats=None):
     N = means.shape[0]
     st = load().gs_project_bwd(cams.ptr, cams.C, N, _dev(means, "f32", "means"), _dev(quats, "f32", "quats"),
                                _dev(log_scales, "f32", "log_scales"), _dev(opacity_logits, "f32", "opacity_logits"),
@@ -374,5 +379,6 @@ def gs_project_bwd(cams: CameraArray, means, quats, log_scales, opacity_logits, 
                                _dev(d_opacities, "f32", "d_opacities"),
                                _dev(d_depths, "f32", "d_depths", optional=True), _dev(d_means, "f32", "d_means"),
                                _dev(d_quats, "f32", "d_quats"), _dev(d_log_scales, "f32", "d_log_scales"),
-                               _dev(d_opacity_logits, "f32", "d_opacity_logits"), _stream(stream))
+                               _dev(d_opacity_logits, "f32", "d_opacity_logits"),
+                               _dev(d_viewmats, "f32", "d_viewmats", optional=True), _stream(stream))
     _check(st, "gs_project_bwd")

@@ -14,11 +14,11 @@ cudaError_t launch_project_fwd(const CamSet &, const RasterConsts &, int, const 
                                const float *, float *, float *, float *, int *, int *, float *, cudaStream_t);
 cudaError_t launch_project_bwd(const CamSet &, const RasterConsts &, int, const float *, const float *, const float *,
                                const float *, const int *, const float *, const float *, const float *, const float *,
-                               float *, float *, float *, float *, cudaStream_t);
+                               float *, float *, float *, float *, float *, cudaStream_t);
 cudaError_t launch_sh_fwd(const CamSet &, int, int, const float *, const float *, const int *, float *, const float *,
                           cudaStream_t);
 cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *, const int *, const float *, float *,
-                          float *, float *, cudaStream_t);
+                          float *, float *, float *, cudaStream_t);
 cudaError_t launch_expected_depth(long long, const float *, int, int, const float *, float *, cudaStream_t);
 cudaError_t launch_expected_depth_bwd(long long, const float *, int, int, const float *, const float *, float *,
                                       float *, cudaStream_t);
@@ -419,7 +419,7 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
 
 gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
                          const float *means, const int32_t *radii, const float *d_colors, float *d_sh,
-                         float *d_means, void *stream) {
+                         float *d_means, float *d_viewmats, void *stream) {
     CamSet cs;
     GS_TRY(make_camset(cams, C, 16, cs));
     GS_TRY(check_cn(C, N));
@@ -429,13 +429,14 @@ gs_status gs_sh_eval_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh
     GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(d_colors); GS_NONNULL(d_sh);
     GS_NONNULL(d_means);
     cudaError_t e =
-        launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors, d_sh, d_means, nullptr, (cudaStream_t)stream);
+        launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors, d_sh, d_means, nullptr, d_viewmats,
+                      (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_bwd");
 }
 
 gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,
                                const float *means, const int32_t *radii, const float *d_colors_rgbd, float *d_sh,
-                               float *d_means, float *d_depths, void *stream) {
+                               float *d_means, float *d_depths, float *d_viewmats, void *stream) {
     CamSet cs;
     GS_TRY(make_camset(cams, C, 16, cs));
     GS_TRY(check_cn(C, N));
@@ -445,7 +446,7 @@ gs_status gs_sh_eval_depth_bwd(const gs_camera *cams, int32_t C, int32_t N, int3
     GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(radii); GS_NONNULL(d_colors_rgbd); GS_NONNULL(d_sh);
     GS_NONNULL(d_means); GS_NONNULL(d_depths);
     cudaError_t e = launch_sh_bwd(cs, sh_degree, N, sh, means, radii, d_colors_rgbd, d_sh, d_means, d_depths,
-                                  (cudaStream_t)stream);
+                                  d_viewmats, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_eval_depth_bwd");
 }
 
@@ -453,7 +454,8 @@ gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const floa
                          const float *log_scales, const float *opacity_logits, const gs_params *params,
                          const int32_t *radii, const float *d_means2d, const float *d_conics, const float *d_opacities,
                          const float *d_depths, float *d_means, float *d_quats, float *d_log_scales,
-                         float *d_opacity_logits, void *stream) {
+                         float *d_opacity_logits, float *d_viewmats,
+                         void *stream) {
     RasterConsts rc;
     CamSet cs;
     GS_TRY(check_params(params, rc));
@@ -468,7 +470,7 @@ gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const floa
     if (!aligned(d_means2d, 8)) return fail_arg("d_means2d must be 8-byte aligned");
     cudaError_t e = launch_project_bwd(cs, rc, N, means, quats, log_scales, opacity_logits, radii, d_means2d, d_conics,
                                        d_opacities, d_depths, d_means, d_quats, d_log_scales, d_opacity_logits,
-                                       (cudaStream_t)stream);
+                                       d_viewmats, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project_bwd");
 }
 

@@ -52,6 +52,27 @@ struct RasterConsts {
     const int *tile_order;  // compositing: CTA b renders tile tile_order[b] (NULL: tile b)
 };
 
+// Sums v[0..V) over the CTA and adds the totals to dst[0..V) with one atomic each (thread
+// k adds value k).  Every thread of the CTA must call it; s_red holds V * (warps) floats.
+template <int V>
+__device__ __forceinline__ void block_sum_atomic(float (&v)[V], float *dst, float *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        float x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_red[warp * V + k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        float t = 0.f;
+        for (int w = 0; w < warps; ++w) t += s_red[w * V + threadIdx.x];
+        if (t != 0.f) atomicAdd(dst + threadIdx.x, t);
+    }
+    __syncthreads();
+}
+
 // Global tile rendered by this CTA of a compositing launch; -1 for an out-of-range entry of
 // a caller-supplied order (the CTA then renders nothing).
 __device__ __forceinline__ int tile_of_block(const RasterConsts &rc, int total_tiles) {

@@ -178,98 +178,125 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     const float *__restrict__ logits, const __grid_constant__ CamSet cs, RasterConsts rc,
     const int *__restrict__ radii, const float2 *__restrict__ d_means2d, const float *__restrict__ d_conics,
     const float *__restrict__ d_opac, const float *__restrict__ d_depths, float *__restrict__ d_means,
-    float4 *__restrict__ d_quats, float *__restrict__ d_log_scales, float *__restrict__ d_logits) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    float4 *__restrict__ d_quats, float *__restrict__ d_log_scales, float *__restrict__ d_logits,
+    float *__restrict__ d_viewmats) {
+    __shared__ float s_red[8 * 12];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = n < N;
     bool any = false;
-    for (int c = 0; c < cs.C; ++c) any |= radii[(size_t)c * N + n] > 0;
-    if (!any) {
+    if (valid)
+        for (int c = 0; c < cs.C; ++c) any |= radii[(size_t)c * N + n] > 0;
+    if (valid && !any) {
         d_quats[n] = make_float4(0.f, 0.f, 0.f, 0.f);
         d_log_scales[3 * n] = 0.f;
         d_log_scales[3 * n + 1] = 0.f;
         d_log_scales[3 * n + 2] = 0.f;
         d_logits[n] = 0.f;
-        return;
     }
+    const bool work = valid && any;
+    if (!work && !d_viewmats) return;  // with a pose gradient every thread joins the CTA sums
     Gauss3 g;
-    load_gauss(n, log_scales, quats, logits, g);
-    float mean[3] = {means[3 * n], means[3 * n + 1], means[3 * n + 2]};
+    float mean[3] = {0.f, 0.f, 0.f};
+    if (work) {
+        load_gauss(n, log_scales, quats, logits, g);
+        mean[0] = means[3 * n];
+        mean[1] = means[3 * n + 1];
+        mean[2] = means[3 * n + 2];
+    }
     float dmu[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // symmetric matrix gradient: xx, xy, xz, yy, yz, zz
     float d_o = 0.f;
     for (int c = 0; c < cs.C; ++c) {
-        size_t idx = (size_t)c * N + n;
-        if (radii[idx] <= 0) continue;
+        const size_t idx = (size_t)c * N + n;
         const CamDev &cam = cs.cam[c];
+        float pose[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // rows of [dR | dt]
         Splat2 sp;
-        if (!splat_of(g, mean, cam, rc, sp)) continue;
-        float2 gm = d_means2d[idx];
-        float ga = d_conics[3 * idx], gb = d_conics[3 * idx + 1], gc = d_conics[3 * idx + 2];
-        float gop = d_opac[idx];
-        // conic scalars (a, b, c) -> matrix gradient dY = [[ga, gb/2], [gb/2, gc]];
-        // dSigma' = -Y dY Y  (App. D.2)
-        float Ya = sp.conic[0], Yb = sp.conic[1], Yc = sp.conic[2];
-        float hb = 0.5f * gb;
-        float m00 = Ya * ga + Yb * hb, m01 = Ya * hb + Yb * gc;
-        float m10 = Yb * ga + Yc * hb, m11 = Yb * hb + Yc * gc;
-        float G00 = -(m00 * Ya + m01 * Yb);
-        float G01 = -(m00 * Yb + m01 * Yc);
-        float G11 = -(m10 * Yb + m11 * Yc);
-        d_o += gop * sp.comp;
-        if (rc.antialiased && sp.comp > 0.f) {
-            // comp = sqrt(det0/det1): gradient w.r.t. the entries (a, b, c) of Sigma'
-            float a = sp.cov0[0], b = sp.cov0[1], cc = sp.cov0[2];
-            float det0 = a * cc - b * b;
-            float det1 = sp.cov[0] * sp.cov[2] - sp.cov[1] * sp.cov[1];
-            float k = gop * g.o / (2.f * sp.comp) / (det1 * det1);
-            G00 += k * (cc * det1 - det0 * sp.cov[2]);
-            G11 += k * (a * det1 - det0 * sp.cov[0]);
-            G01 += 0.5f * k * (2.f * b * det0 - 2.f * b * det1);
-        }
-        // Sigma' = T Sigma T^T:  dSigma = T^T G T;  dT = 2 G T Sigma (G, Sigma symmetric)
-        const float *T = sp.T;
-        float GT0[3], GT1[3];  // rows of G T
+        if (work && radii[idx] > 0 && splat_of(g, mean, cam, rc, sp)) {
+            float2 gm = d_means2d[idx];
+            float ga = d_conics[3 * idx], gb = d_conics[3 * idx + 1], gc = d_conics[3 * idx + 2];
+            float gop = d_opac[idx];
+            // conic scalars (a, b, c) -> matrix gradient dY = [[ga, gb/2], [gb/2, gc]];
+            // dSigma' = -Y dY Y  (App. D.2)
+            float Ya = sp.conic[0], Yb = sp.conic[1], Yc = sp.conic[2];
+            float hb = 0.5f * gb;
+            float m00 = Ya * ga + Yb * hb, m01 = Ya * hb + Yb * gc;
+            float m10 = Yb * ga + Yc * hb, m11 = Yb * hb + Yc * gc;
+            float G00 = -(m00 * Ya + m01 * Yb);
+            float G01 = -(m00 * Yb + m01 * Yc);
+            float G11 = -(m10 * Yb + m11 * Yc);
+            d_o += gop * sp.comp;
+            if (rc.antialiased && sp.comp > 0.f) {
+                // comp = sqrt(det0/det1): gradient w.r.t. the entries (a, b, c) of Sigma'
+                float a = sp.cov0[0], b = sp.cov0[1], cc = sp.cov0[2];
+                float det0 = a * cc - b * b;
+                float det1 = sp.cov[0] * sp.cov[2] - sp.cov[1] * sp.cov[1];
+                float k = gop * g.o / (2.f * sp.comp) / (det1 * det1);
+                G00 += k * (cc * det1 - det0 * sp.cov[2]);
+                G11 += k * (a * det1 - det0 * sp.cov[0]);
+                G01 += 0.5f * k * (2.f * b * det0 - 2.f * b * det1);
+            }
+            // Sigma' = T Sigma T^T:  dSigma = T^T G T;  dT = 2 G T Sigma (G, Sigma symmetric)
+            const float *T = sp.T;
+            float GT0[3], GT1[3];  // rows of G T
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            GT0[k] = G00 * T[k] + G01 * T[3 + k];
-            GT1[k] = G01 * T[k] + G11 * T[3 + k];
-        }
-        // dSigma_ij += T0i GT0j + T1i GT1j
-        dSig[0] += T[0] * GT0[0] + T[3] * GT1[0];
-        dSig[1] += T[0] * GT0[1] + T[3] * GT1[1];
-        dSig[2] += T[0] * GT0[2] + T[3] * GT1[2];
-        dSig[3] += T[1] * GT0[1] + T[4] * GT1[1];
-        dSig[4] += T[1] * GT0[2] + T[4] * GT1[2];
-        dSig[5] += T[2] * GT0[2] + T[5] * GT1[2];
-        const float *S = g.Sig;
-        float dT[6];
+            for (int k = 0; k < 3; ++k) {
+                GT0[k] = G00 * T[k] + G01 * T[3 + k];
+                GT1[k] = G01 * T[k] + G11 * T[3 + k];
+            }
+            // dSigma_ij += T0i GT0j + T1i GT1j
+            dSig[0] += T[0] * GT0[0] + T[3] * GT1[0];
+            dSig[1] += T[0] * GT0[1] + T[3] * GT1[1];
+            dSig[2] += T[0] * GT0[2] + T[3] * GT1[2];
+            dSig[3] += T[1] * GT0[1] + T[4] * GT1[1];
+            dSig[4] += T[1] * GT0[2] + T[4] * GT1[2];
+            dSig[5] += T[2] * GT0[2] + T[5] * GT1[2];
+            const float *S = g.Sig;
+            float dT[6];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float s0 = k == 0 ? S[0] : (k == 1 ? S[1] : S[2]);
-            float s1 = k == 0 ? S[1] : (k == 1 ? S[3] : S[4]);
-            float s2 = k == 0 ? S[2] : (k == 1 ? S[4] : S[5]);
-            dT[k] = 2.f * (GT0[0] * s0 + GT0[1] * s1 + GT0[2] * s2);
-            dT[3 + k] = 2.f * (GT1[0] * s0 + GT1[1] * s1 + GT1[2] * s2);
+            for (int k = 0; k < 3; ++k) {
+                float s0 = k == 0 ? S[0] : (k == 1 ? S[1] : S[2]);
+                float s1 = k == 0 ? S[1] : (k == 1 ? S[3] : S[4]);
+                float s2 = k == 0 ? S[2] : (k == 1 ? S[4] : S[5]);
+                dT[k] = 2.f * (GT0[0] * s0 + GT0[1] * s1 + GT0[2] * s2);
+                dT[3 + k] = 2.f * (GT1[0] * s0 + GT1[1] * s1 + GT1[2] * s2);
+            }
+            // T = J R_cw:  dJ = dT R_cw^T (only the non-constant entries of J are needed)
+            const float *W = cam.R;
+            float dJ00 = dT[0] * W[0] + dT[1] * W[1] + dT[2] * W[2];
+            float dJ02 = dT[0] * W[6] + dT[1] * W[7] + dT[2] * W[8];
+            float dJ11 = dT[3] * W[3] + dT[4] * W[4] + dT[5] * W[5];
+            float dJ12 = dT[3] * W[6] + dT[4] * W[7] + dT[5] * W[8];
+            float tx = sp.t[0], ty = sp.t[1], tz = sp.t[2];
+            float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+            float fx = cam.fx, fy = cam.fy;
+            float dtx = gm.x * fx * iz - dJ02 * fx * iz2;
+            float dty = gm.y * fy * iz - dJ12 * fy * iz2;
+            float dtz = -gm.x * fx * tx * iz2 - gm.y * fy * ty * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * tx * iz3 -
+                        dJ11 * fy * iz2 + dJ12 * 2.f * fy * ty * iz3;
+            if (d_depths) dtz += d_depths[idx];
+            // t = R_cw mu + t_cw:  dmu = R_cw^T dt
+            dmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+            dmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+            dmu[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+            if (d_viewmats) {
+                // pose (App. A): dR_cw = J^T dT + dt mu^T,  dt_cw = dt, with
+                // J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]]
+                const float dt3[3] = {dtx, dty, dtz};
+                const float j02 = -fx * tx * iz2, j12 = -fy * ty * iz2;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    pose[j] = fx * iz * dT[j] + dt3[0] * mean[j];
+                    pose[4 + j] = fy * iz * dT[3 + j] + dt3[1] * mean[j];
+                    pose[8 + j] = j02 * dT[j] + j12 * dT[3 + j] + dt3[2] * mean[j];
+                }
+                pose[3] = dtx;
+                pose[7] = dty;
+                pose[11] = dtz;
+            }
         }
-        // T = J R_cw:  dJ = dT R_cw^T (only the non-constant entries of J are needed)
-        const float *W = cam.R;
-        float dJ00 = dT[0] * W[0] + dT[1] * W[1] + dT[2] * W[2];
-        float dJ02 = dT[0] * W[6] + dT[1] * W[7] + dT[2] * W[8];
-        float dJ11 = dT[3] * W[3] + dT[4] * W[4] + dT[5] * W[5];
-        float dJ12 = dT[3] * W[6] + dT[4] * W[7] + dT[5] * W[8];
-        float tx = sp.t[0], ty = sp.t[1], tz = sp.t[2];
-        float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
-        float fx = cam.fx, fy = cam.fy;
-        float dtx = gm.x * fx * iz - dJ02 * fx * iz2;
-        float dty = gm.y * fy * iz - dJ12 * fy * iz2;
-        float dtz = -gm.x * fx * tx * iz2 - gm.y * fy * ty * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * tx * iz3 -
-                    dJ11 * fy * iz2 + dJ12 * 2.f * fy * ty * iz3;
-        if (d_depths) dtz += d_depths[idx];
-        // t = R_cw mu + t_cw:  dmu = R_cw^T dt
-        dmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
-        dmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
-        dmu[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+        if (d_viewmats) block_sum_atomic<12>(pose, d_viewmats + 16 * c, s_red);
     }
+    if (!work) return;
     d_means[3 * n] += dmu[0];
     d_means[3 * n + 1] += dmu[1];
     d_means[3 * n + 2] += dmu[2];
@@ -311,11 +338,11 @@ cudaError_t launch_project_bwd(const CamSet &cs, const RasterConsts &rc, int N, 
                                const float *quats, const float *log_scales, const float *logits, const int *radii,
                                const float *d_means2d, const float *d_conics, const float *d_opac,
                                const float *d_depths, float *d_means, float *d_quats, float *d_log_scales,
-                               float *d_logits, cudaStream_t st) {
+                               float *d_logits, float *d_viewmats, cudaStream_t st) {
     int blocks = (N + 255) / 256;
     project_bwd_kernel<<<blocks, 256, 0, st>>>(N, means, (const float4 *)quats, log_scales, logits, cs, rc, radii,
                                                 (const float2 *)d_means2d, d_conics, d_opac, d_depths, d_means,
-                                                (float4 *)d_quats, d_log_scales, d_logits);
+                                                (float4 *)d_quats, d_log_scales, d_logits, d_viewmats);
     note_launch();
     return cudaGetLastError();
 }

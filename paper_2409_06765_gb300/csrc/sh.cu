@@ -196,10 +196,12 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
                                                                const __grid_constant__ CamSet cs, ShConsts kc,
                                                                const float *__restrict__ d_colors,
                                                                float *__restrict__ d_sh, float *__restrict__ d_means,
-                                                               float *__restrict__ d_depths) {
+                                                               float *__restrict__ d_depths,
+                                                               float *__restrict__ d_viewmats) {
     constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
     const int IS = d_depths ? 4 : 3;  // d_colors rows: (r, g, b) or (r, g, b, depth)
     extern __shared__ float s_coef[];
+    __shared__ float s_red[(kShBwdThreads / 32) * 12];
     float *s_grad = s_coef + kShBwdThreads * STRIDE;
     const int n0 = blockIdx.x * kShBwdThreads;
     const int cnt = min(kShBwdThreads, N - n0);
@@ -210,15 +212,19 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
     for (int f = 0; f < F; ++f) gr[f] = 0.f;
     __syncthreads();
     const int n = n0 + threadIdx.x;
-    if (n < N) {
-        const float *cf = s_coef + threadIdx.x * STRIDE;
-        const float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
-        float dm[3] = {0.f, 0.f, 0.f};
-        for (int c = 0; c < cs.C; ++c) {
-            const size_t idx = (size_t)c * N + n;
+    const bool valid = n < N;
+    const float *cf = s_coef + threadIdx.x * STRIDE;
+    const float mx = valid ? means[3 * n] : 0.f, my = valid ? means[3 * n + 1] : 0.f,
+                mz = valid ? means[3 * n + 2] : 0.f;
+    float dm[3] = {0.f, 0.f, 0.f};
+    for (int c = 0; c < cs.C; ++c) {  // every thread runs every camera (the pose sums are CTA-wide)
+        const size_t idx = (size_t)c * N + n;
+        float dv[3] = {0.f, 0.f, 0.f};  // gradient w.r.t. v = mu - centre for this camera
+        const float *R = cs.cam[c].R, *t = cs.cam[c].t;
+        if (valid) {
             if (d_depths) d_depths[idx] = radii[idx] > 0 ? d_colors[IS * idx + 3] : 0.f;
-            if (radii[idx] <= 0) continue;
-            const float *R = cs.cam[c].R, *t = cs.cam[c].t;
+        }
+        if (valid && radii[idx] > 0) {
             const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
             const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
             const float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
@@ -248,11 +254,27 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
                 sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
                 // dir = v / |v|:  d v = (I - dir dir^T) d dir / |v|
                 const float p = x * dd[0] + y * dd[1] + z * dd[2];
-                dm[0] += (dd[0] - x * p) * il;
-                dm[1] += (dd[1] - y * p) * il;
-                dm[2] += (dd[2] - z * p) * il;
+                dv[0] = (dd[0] - x * p) * il;
+                dv[1] = (dd[1] - y * p) * il;
+                dv[2] = (dd[2] - z * p) * il;
             }
         }
+        dm[0] += dv[0];
+        dm[1] += dv[1];
+        dm[2] += dv[2];
+        if (d_viewmats && DEG > 0) {
+            // pose (App. A): centre = -R^T t, so dR_ij += t_i dv_j and dt_i += sum_j R_ij dv_j
+            float pose[12];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) pose[4 * i + j] = t[i] * dv[j];
+                pose[4 * i + 3] = R[3 * i] * dv[0] + R[3 * i + 1] * dv[1] + R[3 * i + 2] * dv[2];
+            }
+            block_sum_atomic<12>(pose, d_viewmats + 16 * c, s_red);
+        }
+    }
+    if (valid) {
         d_means[3 * n] = dm[0];
         d_means[3 * n + 1] = dm[1];
         d_means[3 * n + 2] = dm[2];
@@ -298,7 +320,7 @@ static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, con
 template <int DEG>
 static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
                                    const float *d_colors, float *d_sh, float *d_means, float *d_depths,
-                                   cudaStream_t st) {
+                                   float *d_viewmats, cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 2 * kShBwdThreads * STRIDE * sizeof(float);
     if (smem > 48 * 1024) {
@@ -306,7 +328,7 @@ static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, con
         if (e != cudaSuccess) return e;
     }
     sh_bwd_kernel<DEG><<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
-                                                            d_sh, d_means, d_depths);
+                                                            d_sh, d_means, d_depths, d_viewmats);
     note_launch();
     return cudaGetLastError();
 }
@@ -322,12 +344,13 @@ cudaError_t launch_sh_fwd(const CamSet &cs, int deg, int N, const float *sh, con
 }
 
 cudaError_t launch_sh_bwd(const CamSet &cs, int deg, int N, const float *sh, const float *means, const int *radii,
-                          const float *d_colors, float *d_sh, float *d_means, float *d_depths, cudaStream_t st) {
+                          const float *d_colors, float *d_sh, float *d_means, float *d_depths, float *d_viewmats,
+                          cudaStream_t st) {
     switch (deg) {
-        case 0: return launch_sh_bwd_t<0>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
-        case 1: return launch_sh_bwd_t<1>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
-        case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
-        default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, st);
+        case 0: return launch_sh_bwd_t<0>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
+        case 1: return launch_sh_bwd_t<1>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
+        case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
+        default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
     }
 }
 

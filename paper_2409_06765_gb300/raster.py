@@ -165,7 +165,7 @@ class RasterizeGaussians(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, means, quats, log_scales, opacity_logits, sh_or_features, cams, sh_degree, settings, state,
-                depth=0):
+                depth=0, viewmats=None):
         use_sh = sh_degree is not None
         if depth and not use_sh:
             raise ValueError("depth rendering needs SH colours")
@@ -189,6 +189,7 @@ class RasterizeGaussians(torch.autograd.Function):
                               out["conics"], out["opacities"], out["colors"], out["values"], out["ranges"],
                               out["final_T"], out["last_contrib"], out["image"] if depth == 2 else None)
         ctx.mark_non_differentiable(out["radii"])
+        ctx.viewmats_like = viewmats  # the pose leaf, if any (its values are in cams)
         alpha = 1.0 - out["final_T"]
         return out["image"], alpha, out["radii"], edepth
 
@@ -220,13 +221,17 @@ class RasterizeGaussians(torch.autograd.Function):
             RasterizeGaussians.last_absgrad = absgrad
         d_means = torch.empty(N, 3, device=dev)
         d_depths = None
+        want_pose = ctx.viewmats_like is not None and ctx.needs_input_grad[10]
+        d_view = torch.zeros(C, 4, 4, device=dev) if want_pose else None
         if ctx.use_sh:
             d_sh = torch.empty_like(shf)
             if ctx.depth:
                 d_depths = torch.empty(C, N, device=dev)
-                _lib.gs_sh_eval_depth_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means, d_depths)
+                _lib.gs_sh_eval_depth_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means, d_depths,
+                                          d_viewmats=d_view)
             else:
-                _lib.gs_sh_eval_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means)
+                _lib.gs_sh_eval_bwd(cams, ctx.sh_degree, shf, means, radii, d_colors, d_sh, d_means,
+                                    d_viewmats=d_view)
             d_feat = d_sh
         else:
             d_means.zero_()
@@ -235,8 +240,10 @@ class RasterizeGaussians(torch.autograd.Function):
         d_log_scales = torch.empty(N, 3, device=dev)
         d_logits = torch.empty(N, device=dev)
         _lib.gs_project_bwd(cams, means, quats, log_scales, logits, params, radii, d_means2d, d_conics, d_opac,
-                            d_depths, d_means, d_quats, d_log_scales, d_logits)
-        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None, None
+                            d_depths, d_means, d_quats, d_log_scales, d_logits, d_viewmats=d_view)
+        if d_view is not None:
+            d_view = d_view.to(ctx.viewmats_like.device).reshape(ctx.viewmats_like.shape)
+        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None, None, d_view
 
 
 RENDER_MODES = {"RGB": 0, "D": 1, "ED": 2, "RGB+D": 1, "RGB+ED": 2}
@@ -244,20 +251,29 @@ RENDER_MODES = {"RGB": 0, "D": 1, "ED": 2, "RGB+D": 1, "RGB+ED": 2}
 
 def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=None, *, features=None,
                   sh_degree=None, settings: RasterSettings | None = None, state: RasterState | None = None,
-                  render_mode: str = "RGB"):
+                  render_mode: str = "RGB", viewmats=None):
     """Render C cameras.  Returns (images, alphas, meta) with one [H, W, ch] / [H, W] tensor per camera.
 
     Pass SH coefficients ``sh`` [N, K, 3] (degree inferred from K) or N-dimensional
     ``features`` [N, D] / [C, N, D].  Parameters are the leaves of the paper's
     gradient-flow figure: log-scales and opacity logits.  ``render_mode`` (SH colours):
     "RGB"; "D" / "RGB+D" with the accumulated depth sum z alpha T; "ED" / "RGB+ED" with the
-    expected depth, the accumulated depth over alpha (App. A).
+    expected depth, the accumulated depth over alpha (App. A).  ``viewmats`` [C,4,4]
+    (world->camera, any device) replaces the cameras' poses; when it requires grad, the pose
+    gradient (App. A) flows back to it.
     """
     if cameras is None:
         raise ValueError("cameras are required")
     if render_mode not in RENDER_MODES:
         raise ValueError(f"render_mode must be one of {sorted(RENDER_MODES)}")
     depth = RENDER_MODES[render_mode]
+    if viewmats is not None:
+        vm = viewmats.detach().reshape(-1, 4, 4).cpu().numpy()
+        base = list(cameras.cams) if isinstance(cameras, _lib.CameraArray) else list(cameras)
+        if len(base) != vm.shape[0]:
+            raise ValueError("viewmats must hold one 4x4 matrix per camera")
+        cameras = [(*(c.as_tuple()[:2] if hasattr(c, "as_tuple") else c[:2]), vm[i],
+                    *(c.as_tuple()[3:] if hasattr(c, "as_tuple") else c[3:])) for i, c in enumerate(base)]
     cams = cameras if isinstance(cameras, _lib.CameraArray) else _lib.CameraArray(cameras)
     settings = settings or RasterSettings()
     if features is None:
@@ -266,12 +282,12 @@ def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=Non
         K = sh.shape[1]
         sh_degree = {1: 0, 4: 1, 9: 2, 16: 3}[K] if sh_degree is None else sh_degree
         img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, sh, cams,
-                                                             sh_degree, settings, state, depth)
+                                                             sh_degree, settings, state, depth, viewmats)
     else:
         if depth:
             raise ValueError("depth render modes need SH colours")
         img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, features,
-                                                             cams, None, settings, state, 0)
+                                                             cams, None, settings, state, 0, viewmats)
     if depth == 2:
         img = torch.cat([img[:, :3], edepth[:, None]], dim=1)
     if render_mode in ("D", "ED"):
