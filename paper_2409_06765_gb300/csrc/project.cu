@@ -173,7 +173,10 @@ __device__ __forceinline__ void drot(const float q[4], const float dR[9], float 
                    y * dR[7]);
 }
 
-__global__ void __launch_bounds__(256) project_bwd_kernel(
+#ifndef GS_PROJECT_BWD_MIN_BLOCKS
+#define GS_PROJECT_BWD_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(256, GS_PROJECT_BWD_MIN_BLOCKS) project_bwd_kernel(
     int N, const float *__restrict__ means, const float4 *__restrict__ quats, const float *__restrict__ log_scales,
     const float *__restrict__ logits, const __grid_constant__ CamSet cs, RasterConsts rc,
     const int *__restrict__ radii, const float2 *__restrict__ d_means2d, const float *__restrict__ d_conics,
@@ -183,6 +186,20 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     __shared__ float s_red[8 * 12];
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = n < N;
+    // every load of this Gaussian that does not depend on another is issued up front, so the
+    // radii, the parameters and the d_means read-modify-write overlap instead of chaining
+    Gauss3 g;
+    float mean[3] = {0.f, 0.f, 0.f};
+    float dm_in[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        mean[0] = means[3 * n];
+        mean[1] = means[3 * n + 1];
+        mean[2] = means[3 * n + 2];
+        dm_in[0] = d_means[3 * n];
+        dm_in[1] = d_means[3 * n + 1];
+        dm_in[2] = d_means[3 * n + 2];
+        load_gauss(n, log_scales, quats, logits, g);
+    }
     bool any = false;
     if (valid)
         for (int c = 0; c < cs.C; ++c) any |= radii[(size_t)c * N + n] > 0;
@@ -195,14 +212,6 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     }
     const bool work = valid && any;
     if (!work && !d_viewmats) return;  // with a pose gradient every thread joins the CTA sums
-    Gauss3 g;
-    float mean[3] = {0.f, 0.f, 0.f};
-    if (work) {
-        load_gauss(n, log_scales, quats, logits, g);
-        mean[0] = means[3 * n];
-        mean[1] = means[3 * n + 1];
-        mean[2] = means[3 * n + 2];
-    }
     float dmu[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // symmetric matrix gradient: xx, xy, xz, yy, yz, zz
     float d_o = 0.f;
@@ -211,10 +220,18 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const CamDev &cam = cs.cam[c];
         float pose[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // rows of [dR | dt]
         Splat2 sp;
-        if (work && radii[idx] > 0 && splat_of(g, mean, cam, rc, sp)) {
-            float2 gm = d_means2d[idx];
-            float ga = d_conics[3 * idx], gb = d_conics[3 * idx + 1], gc = d_conics[3 * idx + 2];
-            float gop = d_opac[idx];
+        float2 gm = make_float2(0.f, 0.f);
+        float ga = 0.f, gb = 0.f, gc = 0.f, gop = 0.f, gdep = 0.f;
+        const bool vis = work && radii[idx] > 0;
+        if (vis) {  // issued before the splat is recomputed, so they arrive while it runs
+            gm = d_means2d[idx];
+            ga = d_conics[3 * idx];
+            gb = d_conics[3 * idx + 1];
+            gc = d_conics[3 * idx + 2];
+            gop = d_opac[idx];
+            if (d_depths) gdep = d_depths[idx];
+        }
+        if (vis && splat_of(g, mean, cam, rc, sp)) {
             // conic scalars (a, b, c) -> matrix gradient dY = [[ga, gb/2], [gb/2, gc]];
             // dSigma' = -Y dY Y  (App. D.2)
             float Ya = sp.conic[0], Yb = sp.conic[1], Yc = sp.conic[2];
@@ -273,7 +290,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
             float dty = gm.y * fy * iz - dJ12 * fy * iz2;
             float dtz = -gm.x * fx * tx * iz2 - gm.y * fy * ty * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * tx * iz3 -
                         dJ11 * fy * iz2 + dJ12 * 2.f * fy * ty * iz3;
-            if (d_depths) dtz += d_depths[idx];
+            dtz += gdep;
             // t = R_cw mu + t_cw:  dmu = R_cw^T dt
             dmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
             dmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
@@ -297,9 +314,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         if (d_viewmats) block_sum_atomic<12>(pose, d_viewmats + 16 * c, s_red);
     }
     if (!work) return;
-    d_means[3 * n] += dmu[0];
-    d_means[3 * n + 1] += dmu[1];
-    d_means[3 * n + 2] += dmu[2];
+    d_means[3 * n] = dm_in[0] + dmu[0];
+    d_means[3 * n + 1] = dm_in[1] + dmu[1];
+    d_means[3 * n + 2] = dm_in[2] + dmu[2];
     // Sigma = M M^T, M = R S:  dM = 2 dSigma M;  dR = dM S;  dS_j = (R^T dM)_jj
     float D[9] = {dSig[0], dSig[1], dSig[2], dSig[1], dSig[3], dSig[4], dSig[2], dSig[4], dSig[5]};
     float dR[9], ds[3] = {0.f, 0.f, 0.f};

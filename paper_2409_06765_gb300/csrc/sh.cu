@@ -110,26 +110,38 @@ __device__ __forceinline__ void sh_basis_vjp(const ShConsts &k, float x, float y
 }
 
 // Copies the coefficient rows of Gaussians [n0, n0+cnt) into shared memory at row stride STRIDE.
-template <int F, int STRIDE>
+// NT threads each issue all their 16-byte loads before the first shared-memory store, so a
+// thread keeps up to ceil(NT F / 4 / NT) loads in flight instead of waiting on each in turn.
+template <int F, int STRIDE, int NT>
 __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cnt, float *s, bool vec_ok) {
-    int total = cnt * F;
+    const int total = cnt * F;
     if (vec_ok) {
-        int nvec = total / 4;
+        constexpr int V = (NT * F / 4 + NT - 1) / NT;  // float4 loads per thread for a full chunk
+        const int nvec = total / 4;
         const float4 *src4 = reinterpret_cast<const float4 *>(src);
-        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-            float4 q = src4[v];
-            int e = 4 * v;
-            s[(e / F) * STRIDE + e % F] = q.x;
-            ++e;
-            s[(e / F) * STRIDE + e % F] = q.y;
-            ++e;
-            s[(e / F) * STRIDE + e % F] = q.z;
-            ++e;
-            s[(e / F) * STRIDE + e % F] = q.w;
+        float4 q[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int v = threadIdx.x + j * NT;
+            if (v < nvec) q[j] = src4[v];
         }
-        for (int e = nvec * 4 + threadIdx.x; e < total; e += blockDim.x) s[(e / F) * STRIDE + e % F] = src[e];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int v = threadIdx.x + j * NT;
+            if (v < nvec) {
+                int e = 4 * v;
+                s[(e / F) * STRIDE + e % F] = q[j].x;
+                ++e;
+                s[(e / F) * STRIDE + e % F] = q[j].y;
+                ++e;
+                s[(e / F) * STRIDE + e % F] = q[j].z;
+                ++e;
+                s[(e / F) * STRIDE + e % F] = q[j].w;
+            }
+        }
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += NT) s[(e / F) * STRIDE + e % F] = src[e];
     } else {
-        for (int e = threadIdx.x; e < total; e += blockDim.x) s[(e / F) * STRIDE + e % F] = src[e];
+        for (int e = threadIdx.x; e < total; e += NT) s[(e / F) * STRIDE + e % F] = src[e];
     }
 }
 
@@ -144,7 +156,7 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
     int n0 = blockIdx.x * 256;
     int cnt = min(256, N - n0);
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    stage_rows<F, STRIDE, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
     __syncthreads();
     int n = n0 + threadIdx.x;
     if (n >= N) return;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
     const int n0 = blockIdx.x * kShBwdThreads;
     const int cnt = min(kShBwdThreads, N - n0);
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
     float *gr = s_grad + threadIdx.x * STRIDE;
 #pragma unroll
     for (int f = 0; f < F; ++f) gr[f] = 0.f;
