@@ -190,12 +190,12 @@ def run_ours(args):
     tuned = None
     if args.tune:
         from paper_2409_06765_gb300 import autotune
-        tuned = autotune.tune(dscene, cams, backward=True, steps=5, warmup=2,
-                              schedules=autotune.candidates(tile_order=not args.no_tile_order))
+        tuned = autotune.tune(dscene, cams, backward=True, tile_order=not args.no_tile_order)
         sched = tuned.best
     else:
         sched = Schedule(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
-                         tile_order=not args.no_tile_order)
+                         tile_order=not args.no_tile_order, bwd_batch_depth=args.bwd_batch,
+                         bwd_pixels_per_thread=args.bwd_ppt)
     kp = FramePipeline(dscene, cams, sched)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
@@ -263,7 +263,9 @@ def run_ours(args):
         leaves = [x.detach().clone().requires_grad_(True) for x in (dscene.means, dscene.quats, dscene.log_scales,
                                                                      dscene.opacity_logits, dscene.sh)]
         settings = raster.RasterSettings(tile=sched.tile, batch_depth=sched.batch_depth,
-                                         pixels_per_thread=sched.pixels_per_thread, tile_schedule=sched.tile_order)
+                                         pixels_per_thread=sched.pixels_per_thread, tile_schedule=sched.tile_order,
+                                         bwd_batch_depth=sched.params_bwd().batch_depth,
+                                         bwd_pixels_per_thread=sched.params_bwd().pixels_per_thread)
         state = raster.RasterState()
         host_target = torch.as_tensor(target_np).pin_memory()
         dev_target = torch.empty_like(target)
@@ -355,6 +357,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "gaussians": scene.n, "sh_degree": scene.sh_degree,
                    "resolution": [cams[0].width, cams[0].height], "views_per_gpu": len(cams), "tile": sched.tile,
                    "batch_depth": sched.batch_depth, "pixels_per_thread": sched.pixels_per_thread,
+                   "bwd_batch_depth": sched.params_bwd().batch_depth,
+                   "bwd_pixels_per_thread": sched.params_bwd().pixels_per_thread,
                    "schedule_from": "autotuner" if tuned else "command line",
                    "cuda_graphs": graphs, "tile_order": sched.tile_order, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
@@ -503,7 +507,7 @@ def run_multiview(dscene, steps, log):
     sizes = [(640, 480)] * 4 + [(1280, 720)] * 4 + [(1920, 1080)] * 4 + [(2560, 1440)] * 4
     cams = synth.sphere_cameras(3 + 3000, sizes)
     t0 = time.time()
-    tuned = autotune.tune(dscene, cams, backward=True, steps=3, warmup=1, log=log)
+    tuned = autotune.tune(dscene, cams, backward=True, reps=3, log=log)
     tune_s = time.time() - t0
     pipe = FramePipeline(dscene, cams, tuned.best)
     blends = pipe.count_blends()
@@ -703,6 +707,8 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--ppt", type=int, default=2, help="pixels per compositing thread (0 = library default)")
+    ap.add_argument("--bwd-batch", type=int, default=0, help="backward batch depth (0: as --batch)")
+    ap.add_argument("--bwd-ppt", type=int, default=0, help="backward pixels per thread (0: as --ppt)")
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")

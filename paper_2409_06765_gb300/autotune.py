@@ -1,14 +1,19 @@
 """Launch-schedule autotuner for the frame pipeline.
 
 The paper exposes the tile size and the per-tile batch as tunable block sizes; here they
-are the tile edge t in {8, 16, 32}, the batch depth (Gaussians staged in shared memory per
-round) in {64, 128, 256}, and the pixels each compositing thread owns.  The support rule is
-per pixel, so every schedule renders bit-identical images: tuning changes speed only.
+are the tile edge t in {8, 16, 32}, and for each compositing kernel separately the batch
+depth (Gaussians staged in shared memory per round, 64..1024) and the pixels each thread
+owns.  The support rule is per pixel, so every schedule renders bit-identical images:
+tuning changes speed only.
 
-``tune`` builds a FramePipeline per candidate, replays it as CUDA graphs and keeps the
-fastest mean step time.  Candidates that cannot run (intersection buffers beyond the int32
-index range or device memory) are recorded as failed and skipped.  Results are cached per
-workload signature (device, scene size, SH degree, camera sizes, forward-only or not).
+For each tile size ``tune`` builds one FramePipeline (the tile size fixes the intersection
+lists), times the stages before and after compositing as CUDA-graph replays, and times
+every (pixels per thread, batch depth) of the forward and of the backward compositing
+kernel on the same lists; the schedule of a tile size is its fastest forward plus its
+fastest backward, and the fastest total over tile sizes wins.  Tile sizes that cannot run
+(intersection lists beyond the int32 index range, device memory) are recorded as failed.
+Results are cached per workload signature (device, scene size, SH degree, camera sizes,
+forward-only or not).
 """
 from __future__ import annotations
 
@@ -19,29 +24,24 @@ from dataclasses import dataclass, field
 
 import torch
 
+from . import _lib
 from .pipeline import DeviceScene, FramePipeline, Schedule
 
-__all__ = ["TILE_SHAPES", "BATCH_DEPTHS", "candidates", "TuneResult", "tune", "signature"]
+__all__ = ["TILE_SHAPES", "BATCH_DEPTHS", "TuneResult", "tune", "signature"]
 
-# (tile, pixels per thread) shapes the compositing kernels are compiled for
-TILE_SHAPES = [(8, 1), (16, 1), (16, 2), (32, 2), (32, 4)]
-BATCH_DEPTHS = [64, 128, 256]
-
-
-def candidates(tile_order=True):
-    return [Schedule(tile=t, batch_depth=b, pixels_per_thread=p, tile_order=tile_order)
-            for (t, p) in TILE_SHAPES for b in BATCH_DEPTHS]
+# pixels per thread the compositing kernels are compiled for, per tile size
+TILE_SHAPES = {8: (1,), 16: (1, 2), 32: (2, 4)}
+BATCH_DEPTHS = (64, 128, 256, 512, 1024)
 
 
 @dataclass
 class TuneResult:
     best: Schedule
     best_ms: float
-    table: list = field(default_factory=list)  # (schedule dict, ms or None, note)
+    table: list = field(default_factory=list)  # dicts: tile, phase, ppt, batch, ms, note
 
     def as_dict(self):
-        return {"best": self.best.as_dict(), "best_ms": self.best_ms,
-                "table": [{"schedule": s, "ms": ms, "note": note} for s, ms, note in self.table]}
+        return {"best": self.best.as_dict(), "best_ms": self.best_ms, "table": self.table}
 
 
 _CACHE: dict = {}
@@ -53,52 +53,90 @@ def signature(scene: DeviceScene, cams, backward: bool):
     return (name, scene.n, scene.sh_degree, sizes, bool(backward))
 
 
-def _time_schedule(scene, cams, sched, backward, steps, warmup):
-    pipe = FramePipeline(scene, cams, sched, backward=backward)
+def _time(fn, reps, warmup=1):
+    for _ in range(warmup):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _tune_tile(scene, cams, tile, backward, reps, table, log):
+    pipe = FramePipeline(scene, cams, Schedule(tile=tile, batch_depth=128, pixels_per_thread=TILE_SHAPES[tile][0]),
+                         backward=backward)
     try:
+        pipe.forward()
         if backward:
-            pipe.forward()
-            pipe.d_image.normal_()
+            pipe.d_image.normal_(0.0, 1e-6)
         pipe.capture_graphs()
-        for _ in range(warmup):
-            pipe.step(graphs=True)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(steps):
-            pipe.step(graphs=True)
-        b.record()
-        torch.cuda.synchronize()
+        ms_fixed = _time(pipe.g_pre.replay, reps)
+        if backward:
+            ms_fixed += _time(pipe.g_post.replay, reps)
+        best = {}
+        for phase in (("fwd", "bwd") if backward else ("fwd",)):
+            for ppt in TILE_SHAPES[tile]:
+                for batch in BATCH_DEPTHS:
+                    params = _lib.make_params(tile=tile, batch_depth=batch, pixels_per_thread=ppt)
+                    if phase == "fwd":
+                        pipe.params = params
+                        fn = pipe._raster_fwd
+                    else:
+                        pipe.params_bwd = params
+
+                        def fn():
+                            pipe.g2d.zero_()
+                            pipe._raster_bwd()
+                    try:
+                        ms, note = _time(fn, reps), ""
+                    except RuntimeError as exc:
+                        ms, note = None, f"failed: {str(exc).splitlines()[0][:100]}"
+                    table.append(dict(tile=tile, phase=phase, ppt=ppt, batch=batch, ms=ms, note=note))
+                    if log:
+                        log(f"  tile {tile:2d} {phase} ppt {ppt} batch {batch:4d}: "
+                            + (f"{ms:.3f} ms" if ms is not None else note))
+                    if ms is not None and (phase not in best or ms < best[phase][0]):
+                        best[phase] = (ms, ppt, batch)
         if pipe.frame_overflowed():
-            return None, "intersection buffers overflowed while timing"
-        return a.elapsed_time(b) / steps, ""
+            raise RuntimeError("intersection buffers overflowed while tuning")
+        total = ms_fixed + sum(v[0] for v in best.values())
+        f = best["fwd"]
+        b = best.get("bwd", f)
+        sched = Schedule(tile=tile, batch_depth=f[2], pixels_per_thread=f[1], bwd_batch_depth=b[2],
+                         bwd_pixels_per_thread=b[1])
+        table.append(dict(tile=tile, phase="total", ms=total, fixed_ms=ms_fixed, schedule=sched.as_dict()))
+        return sched, total
     finally:
         del pipe
 
 
-def tune(scene: DeviceScene, cams, backward=True, schedules=None, steps=5, warmup=2, use_cache=True,
-         cache_file=None, log=None) -> TuneResult:
-    """Time every candidate schedule on this workload and return the fastest."""
+def tune(scene: DeviceScene, cams, backward=True, tiles=(8, 16, 32), reps=5, use_cache=True, cache_file=None,
+         log=None, tile_order=True) -> TuneResult:
+    """Time every compiled schedule on this workload and return the fastest."""
     key = signature(scene, cams, backward)
     if use_cache and key in _CACHE:
         return _CACHE[key]
-    schedules = schedules or candidates()
     table = []
     best, best_ms = None, float("inf")
-    for sched in schedules:
+    for tile in tiles:
         try:
-            ms, note = _time_schedule(scene, cams, sched, backward, steps, warmup)
+            sched, ms = _tune_tile(scene, cams, tile, backward, reps, table, log)
         except (RuntimeError, torch.OutOfMemoryError) as exc:  # GsError is a RuntimeError
-            ms, note = None, f"failed: {str(exc).splitlines()[0][:120]}"
+            table.append(dict(tile=tile, phase="total", ms=None, note=f"failed: {str(exc).splitlines()[0][:120]}"))
+            if log:
+                log(f"  tile {tile:2d}: {table[-1]['note']}")
+            sched, ms = None, None
         gc.collect()
         torch.cuda.empty_cache()
-        table.append((sched.as_dict(), ms, note))
-        if log:
-            log(f"  tile {sched.tile:2d} ppt {sched.pixels_per_thread} batch {sched.batch_depth:3d}: "
-                + (f"{ms:.3f} ms" if ms is not None else note))
         if ms is not None and ms < best_ms:
             best, best_ms = sched, ms
     if best is None:
         raise RuntimeError("no schedule could run this workload")
+    if not tile_order:
+        best = Schedule(**{**best.__dict__, "tile_order": False})
     res = TuneResult(best, best_ms, table)
     _CACHE[key] = res
     if cache_file:

@@ -142,8 +142,8 @@ static gs_status check_params(const gs_params *p, RasterConsts &rc) {
     if (p->tile != 8 && p->tile != 16 && p->tile != 32) return fail_arg("tile must be 8, 16 or 32");
     if (raster_pixels_per_thread(p->tile, p->pixels_per_thread) == 0)
         return fail_arg("pixels_per_thread: 0, or 1 for 8x8 tiles, 1 or 2 for 16x16, 2 or 4 for 32x32");
-    if (p->batch_depth < 32 || p->batch_depth > 256 || (p->batch_depth % 32) != 0)
-        return fail_arg("batch_depth must be a multiple of 32 in [32, 256]");
+    if (p->batch_depth < 32 || p->batch_depth > 1024 || (p->batch_depth % 32) != 0)
+        return fail_arg("batch_depth must be a multiple of 32 in [32, 1024]");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return fail_arg("alpha_max must be in (0, 1)");
     if (!(p->alpha_min >= 0.f && p->alpha_min <= p->alpha_max)) return fail_arg("alpha_min must be in [0, alpha_max]");
     if (!(p->T_min > 0.f && p->T_min < 1.f)) return fail_arg("T_min must be in (0, 1)");

@@ -12,6 +12,11 @@
 // up spread over the lanes -- the atomics of all V values leave in one instruction.
 #include "gs_internal.cuh"
 
+// Resident threads per SM the register allocation must allow (0: no constraint).
+#ifndef GS_RASTER_BWD_MIN_THREADS
+#define GS_RASTER_BWD_MIN_THREADS 0
+#endif
+
 namespace gs {
 
 struct BgConstB {
@@ -78,7 +83,8 @@ __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int
 }
 
 template <int TILE, int PPT, int CHC, bool ABSG>
-__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_kernel(
+__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
+                                      GS_RASTER_BWD_MIN_THREADS / RasterShape<TILE, PPT>::kThreads) raster_bwd_kernel(
     const __grid_constant__ CamSet cs, RasterConsts rc, int ch, int batch, const int2 *__restrict__ ranges,
     const int *__restrict__ values, const int *__restrict__ radii, const float2 *__restrict__ means2d,
     const float *__restrict__ conics, const float *__restrict__ opac, const float *__restrict__ colors,

@@ -10,6 +10,11 @@
 // leaves the batch, and the CTA stops when all of its pixels have (__syncthreads_count).
 #include "gs_internal.cuh"
 
+// Resident threads per SM the register allocation must allow (0: no constraint).
+#ifndef GS_RASTER_FWD_MIN_THREADS
+#define GS_RASTER_FWD_MIN_THREADS 0
+#endif
+
 namespace gs {
 
 struct BgConst {
@@ -17,7 +22,8 @@ struct BgConst {
 };
 
 template <int TILE, int PPT, int CHC, bool COUNT>
-__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_kernel(
+__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
+                                      GS_RASTER_FWD_MIN_THREADS / RasterShape<TILE, PPT>::kThreads) raster_fwd_kernel(
     const __grid_constant__ CamSet cs, RasterConsts rc, int ch, int batch, const int2 *__restrict__ ranges,
     const int *__restrict__ values, const int *__restrict__ radii, const float2 *__restrict__ means2d,
     const float *__restrict__ conics, const float *__restrict__ opac, const float *__restrict__ colors,

@@ -25,17 +25,28 @@ __all__ = ["Schedule", "DeviceScene", "FramePipeline"]
 
 @dataclass(frozen=True)
 class Schedule:
-    """Launch parameters of the pipeline; the rendered result does not depend on them."""
+    """Launch parameters of the pipeline; the rendered result does not depend on them.
+
+    The tile size fixes the intersection lists for both compositing kernels; each kernel has
+    its own batch depth and pixels per thread (bwd_* = 0: the same as the forward's)."""
     tile: int = 16
     batch_depth: int = 128
     pixels_per_thread: int = 2
     tile_order: bool = True
+    bwd_batch_depth: int = 0
+    bwd_pixels_per_thread: int = 0
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread)
 
+    def params_bwd(self) -> _lib.GsParams:
+        return _lib.make_params(tile=self.tile, batch_depth=self.bwd_batch_depth or self.batch_depth,
+                                pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread)
+
     def as_dict(self):
         return dict(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
+                    bwd_batch_depth=self.bwd_batch_depth or self.batch_depth,
+                    bwd_pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread,
                     tile_order=self.tile_order)
 
 
@@ -67,6 +78,7 @@ class FramePipeline:
         self.cams = cams if isinstance(cams, _lib.CameraArray) else _lib.CameraArray(cams)
         self.schedule = schedule
         self.params = schedule.params()
+        self.params_bwd = schedule.params_bwd()
         self.with_backward = backward
         C, N = self.cams.C, scene.n
         self.C, self.N = C, N
@@ -158,7 +170,7 @@ class FramePipeline:
                               tile_order=self.order)
 
     def _raster_bwd(self):
-        _lib.gs_rasterize_bwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii, self.means2d,
+        _lib.gs_rasterize_bwd(self.cams, self.N, self.params_bwd, 3, self.ranges, self.values, self.radii, self.means2d,
                               self.conics, self.opac, self.colors, None, self.final_T, self.last, self.d_image, None,
                               self.d_means2d, self.d_conics, self.d_opac, self.d_colors, None, tile_order=self.order)
 

@@ -37,10 +37,17 @@ class RasterSettings:
     absgrad: bool = False
     pixels_per_thread: int = 0
     tile_schedule: bool = True  # hand the longest tile lists to the GPU first (gs_tile_order)
+    bwd_batch_depth: int = 0        # backward compositing launch (0: as the forward's)
+    bwd_pixels_per_thread: int = 0
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
                                 self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread)
+
+    def params_bwd(self) -> _lib.GsParams:
+        return _lib.make_params(self.tile, self.bwd_batch_depth or self.batch_depth, self.antialiased, self.eps2d,
+                                self.near_plane, self.alpha_min, self.alpha_max, self.T_min,
+                                self.bwd_pixels_per_thread or self.pixels_per_thread)
 
 
 @dataclass
@@ -199,6 +206,7 @@ class RasterizeGaussians(torch.autograd.Function):
          last, image) = ctx.saved_tensors
         cams, settings = ctx.cams, ctx.settings
         params = settings.params()
+        params_bwd = settings.params_bwd()
         C, N = cams.C, means.shape[0]
         ch = colors.shape[-1]
         dev = means.device
@@ -214,7 +222,7 @@ class RasterizeGaussians(torch.autograd.Function):
             d_alpha = d_alpha.clone() if d_alpha is not None else torch.zeros(cams.num_pixels, device=dev)
             _lib.gs_expected_depth_bwd(image, 3, final_T, d_edepth.contiguous(), d_image, d_alpha)
         vals = values if values.numel() else torch.empty(1, dtype=torch.int32, device=dev)
-        _lib.gs_rasterize_bwd(cams, N, params, ch, ranges, vals, radii, means2d, conics, opac, colors,
+        _lib.gs_rasterize_bwd(cams, N, params_bwd, ch, ranges, vals, radii, means2d, conics, opac, colors,
                               settings.background, final_T, last, d_image, d_alpha, d_means2d, d_conics, d_opac,
                               d_colors, absgrad, tile_order=ctx.tile_order)
         if absgrad is not None:

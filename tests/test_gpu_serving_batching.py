@@ -37,11 +37,19 @@ def test_autotuner_times_every_candidate_and_caches_the_winner():
     sc = synth.clustered_scene(6000, 32, sh_degree=1, log_scale_mu=-3.3)
     ds = DeviceScene.from_host(sc)
     cams = synth.sphere_cameras(32, [(160, 96), (96, 160)])
-    res = autotune.tune(ds, cams, backward=True, steps=1, warmup=1, use_cache=False)
-    assert len(res.table) == len(autotune.TILE_SHAPES) * len(autotune.BATCH_DEPTHS)
-    ok = [ms for _, ms, _ in res.table if ms is not None]
-    assert ok and res.best_ms == min(ok)
-    again = autotune.tune(ds, cams, backward=True, steps=1, warmup=1)
+    res = autotune.tune(ds, cams, backward=True, reps=1, use_cache=False)
+    per_kernel = [r for r in res.table if r["phase"] in ("fwd", "bwd")]
+    n_shapes = sum(len(v) for v in autotune.TILE_SHAPES.values())
+    assert len(per_kernel) == 2 * n_shapes * len(autotune.BATCH_DEPTHS)
+    totals = [r["ms"] for r in res.table if r["phase"] == "total" and r["ms"] is not None]
+    assert totals and res.best_ms == min(totals)
+    # a tile size's total is its fixed stages plus its fastest forward and backward
+    for t in autotune.TILE_SHAPES:
+        tot = [r for r in res.table if r["phase"] == "total" and r["tile"] == t][0]
+        f = min(r["ms"] for r in per_kernel if r["tile"] == t and r["phase"] == "fwd")
+        b = min(r["ms"] for r in per_kernel if r["tile"] == t and r["phase"] == "bwd")
+        assert abs(tot["ms"] - (tot["fixed_ms"] + f + b)) < 1e-9
+    again = autotune.tune(ds, cams, backward=True, reps=1)
     assert autotune.tune(ds, cams, backward=True) is again  # cached by signature
     # the winner renders what the default schedule renders
     for cam in cams:
