@@ -156,6 +156,35 @@ def build_workload(name: str, rank: int):
     return scene, cams, desc
 
 
+KERNEL_SOURCES = ("paper_2409_06765_gb300/csrc/raster_fwd.cu", "paper_2409_06765_gb300/csrc/raster_bwd.cu",
+                  "paper_2409_06765_gb300/csrc/gs_internal.cuh")
+
+
+def kernel_source_hash():
+    """Hash of the compositing kernels' sources: DRAM counters recorded for another version are stale."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel, sched):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu capture (profiles/traffic.json),
+    or None when the capture is for another workload, schedule or kernel source."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as fh:
+        tr = json.load(fh)
+    if tr.get("workload") != workload or tr.get("source_hash") != kernel_source_hash():
+        return None
+    if tr.get("schedule") != sched.as_dict():
+        return None
+    return tr.get("kernels", {}).get(kernel)
+
+
 def job_totals(ms_step, blends, world, device):
     """Whole-job step time (max over ranks) and work (sum over ranks): replicas render their
     own views, so the job takes as long as its slowest rank and does the work of all."""
@@ -308,13 +337,7 @@ def run_ours(args):
     fwd_ach = blends * FWD_OPS_PER_BLEND / (t_fwd_raster / 1000.0)
     dominant = "rasterize_bwd" if t_bwd_raster >= t_fwd_raster else "rasterize_fwd"
     ach = bwd_ach if dominant == "rasterize_bwd" else fwd_ach
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as fh:
-            tr = json.load(fh)
-        if tr.get("workload") == args.workload and dominant in tr.get("kernels", {}):
-            traffic = tr["kernels"][dominant]
+    traffic = measured_traffic(args.workload, dominant, sched)
     roofline = {"bound": "alu", "kernel": dominant, "achieved": ach / 1e9, "peak": alu_peak / 1e9,
                 "unit": "Gop/s", "frac": ach / alu_peak, "traffic": traffic,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz (max SM clock)",
