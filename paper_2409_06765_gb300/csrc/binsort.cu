@@ -48,8 +48,10 @@ constexpr long long kWaitSpins = 1ll << 22;  // bound on a wait for a bulk copy
 // misc region layout (ints)
 constexpr int kMiscNeff = 0;
 constexpr int kMiscErr = 1;
-constexpr int kMiscRowsum = 64;                // [kRadix] row sums of the count matrix
-constexpr int kMiscInts = kMiscRowsum + kRadix;
+constexpr int kMiscRowsum = 64;                // [kMaxPasses][kRadix] digit totals of every pass
+constexpr int kMaxPasses = 8;                  // 4 depth passes + up to 4 tile passes
+constexpr int kFusedRowsumCols = 1024;         // passes of up to this many blocks sum digits by atomics
+constexpr int kMiscInts = kMiscRowsum + kMaxPasses * kRadix;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -133,10 +135,13 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
 // one stable LSD pass as reduce-then-scan: no CTA waits on another
 // ---------------------------------------------------------------------------
 
-// Digit counts of every kSortBlock-item block: hist[d * cols + b] (digit-major).
+// Digit counts of every kSortBlock-item block: hist[d * cols + b] (digit-major), and, when
+// rowsum is given, the pass's digit totals rowsum[d] by atomic adds (zeroed before the sort;
+// used for passes of few blocks, where the adds to one counter do not queue up).
 __global__ void __launch_bounds__(kSortThreads) block_hist_kernel(const uint32_t *__restrict__ keys,
                                                                 const int *__restrict__ n_dev, int n_host, int shift,
-                                                                int bits, int cols, int *__restrict__ hist) {
+                                                                int bits, int cols, int *__restrict__ hist,
+                                                                int *__restrict__ rowsum) {
     constexpr int W = kSortThreads / 32;
     __shared__ int s_h[W][kRadix];
     const int warp = threadIdx.x >> 5;
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(kSortThreads) block_hist_kernel(const uint32_t
 #pragma unroll
     for (int w = 0; w < W; ++w) c += s_h[w][d];
     hist[(size_t)d * cols + b] = c;
+    if (rowsum && c) atomicAdd(&rowsum[d], c);
 }
 
 // Row sums of the digit-major count matrix over its first nb = ceil(n / kSortBlock) columns.
@@ -468,39 +474,39 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, const _
 }
 
 // Exclusive scan of the per-CTA partials (one CTA); K = total; n_eff = min(K, capacity).
+// Each thread owns a contiguous segment: it sums it, the CTA scans the segment sums, and the
+// thread rewrites its segment from its exclusive start (one pass, no per-round barriers).
 __global__ void __launch_bounds__(1024) partial_scan_kernel(int G, long long *__restrict__ partials,
                                                             long long capacity, long long *__restrict__ K_out,
                                                             int *__restrict__ n_eff) {
     __shared__ long long s_w[32];
-    __shared__ long long s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < G; b0 += 1024) {
-        const int b = b0 + threadIdx.x;
-        const long long v = b < G ? partials[b] : 0;
-        long long x = v;
+    const int per = (G + 1023) / 1024;
+    const int b0 = min(G, threadIdx.x * per), b1 = min(G, b0 + per);
+    long long sum = 0;
+    for (int b = b0; b < b1; ++b) sum += partials[b];
+    long long x = sum;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_w[warp] = x;
-        __syncthreads();
-        long long wpre = 0, tot = 0;
-        for (int w = 0; w < 32; ++w) {
-            if (w < warp) wpre += s_w[w];
-            tot += s_w[w];
-        }
-        if (b < G) partials[b] = s_carry + wpre + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    long long wpre = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+        if (w < warp) wpre += s_w[w];
+        tot += s_w[w];
+    }
+    long long run = wpre + x - sum;
+    for (int b = b0; b < b1; ++b) {
+        const long long v = partials[b];
+        partials[b] = run;
+        run += v;
     }
     if (threadIdx.x == 0) {
-        const long long run = s_carry;
-        *K_out = run;
-        *n_eff = (int)(run < capacity ? run : capacity);
+        *K_out = tot;
+        *n_eff = (int)(tot < capacity ? tot : capacity);
     }
 }
 
@@ -555,10 +561,12 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
         const int len = (int)min((long long)kChunk, n - k0);
         const int j0 = chunk_start[ch];
         // the pairs of this chunk: j0, j0 + 1, ... while their first slot is inside the chunk
-        // (offsets are non-decreasing, so they form a prefix and a count gives their number)
+        // (offsets are non-decreasing, so they form a prefix and a count gives their number);
+        // they end at the pair holding the next chunk's first slot, so only those are read
+        const int j_end = (ch + 1 < nchunks) ? chunk_start[ch + 1] : CN - 1;
+        const int cand = min(P, j_end - j0 + 1);
         int np = 0;
-#pragma unroll
-        for (int s0 = 0; s0 < P; s0 += kEmitThreads) {
+        for (int s0 = 0; s0 < cand; s0 += kEmitThreads) {
             const int s = s0 + threadIdx.x;
             const int j = j0 + s;
             const long long off = (j < CN) ? offsets[j] : (1ll << 62);
@@ -584,17 +592,30 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
                 else hi = mid - 1;
             }
             int p = lo;
+            // position (kx, ky) of slot q0 in its pair's tile rectangle: one division, then the
+            // following slots step through the rectangle (a new pair starts at its corner)
+            int w = s_wc[p] & 0xffff;
+            int kk = q0 - s_off[p];
+            int ky = kk / w, kx = kk - ky * w;
 #pragma unroll
             for (int u = 0; u < kSlotsPerThread; ++u) {
                 const int q = q0 + u;
                 if (q >= len) break;
-                while (q >= s_off[p + 1]) ++p;
-                const int kk = q - s_off[p];
-                const int w = s_wc[p] & 0xffff, cam = s_wc[p] >> 16;
+                if (u > 0) {
+                    if (q >= s_off[p + 1]) {
+                        while (q >= s_off[p + 1]) ++p;
+                        w = s_wc[p] & 0xffff;
+                        kx = 0;
+                        ky = 0;
+                    } else if (++kx == w) {
+                        kx = 0;
+                        ++ky;
+                    }
+                }
+                const int cam = s_wc[p] >> 16;
                 const int tx0 = s_xy[p] & 0xffff, ty0 = s_xy[p] >> 16;
-                const int ky = kk / w;
-                const uint32_t tile = (uint32_t)(cs.cam[cam].tile_offset + (ty0 + ky) * cs.cam[cam].tiles_x + tx0 +
-                                                 (kk - ky * w));
+                const uint32_t tile =
+                    (uint32_t)(cs.cam[cam].tile_offset + (ty0 + ky) * cs.cam[cam].tiles_x + tx0 + kx);
                 s_key[q + (q >> 5)] = tile;  // padded: one bank shift per 32 slots
                 s_val[q + (q >> 5)] = s_id[p];
             }
@@ -740,10 +761,14 @@ static cudaError_t rts_pass(const uint32_t *kin, const int *vin, uint32_t *kout,
                             cudaStream_t st) {
     const int cols = (int)((max_items + kSortBlock - 1) / kSortBlock);
     if (cols <= 0) return cudaSuccess;
-    block_hist_kernel<<<cols, kSortThreads, 0, st>>>(kin, n_dev, n_host, shift, bits, cols, matrix);
+    const bool fused = cols <= kFusedRowsumCols;
+    block_hist_kernel<<<cols, kSortThreads, 0, st>>>(kin, n_dev, n_host, shift, bits, cols, matrix,
+                                                     fused ? rowsum : nullptr);
     note_launch();
-    hist_rowsum_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, matrix, rowsum);
-    note_launch();
+    if (!fused) {
+        hist_rowsum_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, matrix, rowsum);
+        note_launch();
+    }
     hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
     note_launch();
     cudaError_t e =
@@ -803,7 +828,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     for (int pass = 0; pass < 4; ++pass) {
         const bool even = (pass % 2) == 0;
         e = rts_pass(even ? dk0 : dk1, even ? dv0 : dv1, even ? dk1 : dk0, even ? dv1 : dv0, nullptr, cn, cn, 8 * pass,
-                     8, matrix, rowsum, err, st);
+                     8, matrix, rowsum + pass * kRadix, err, st);
         if (e != cudaSuccess) return e;
     }
     const int *order = dv0;  // after 4 passes the sorted pairs are back in (dk0, dv0)
@@ -828,7 +853,8 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < tpasses; ++pass) {
-        e = rts_pass(kA, vA, kB, vB, n_eff, 0, Kcap, tdigit * pass, tdigit, matrix, rowsum, err, st);
+        e = rts_pass(kA, vA, kB, vB, n_eff, 0, Kcap, tdigit * pass, tdigit, matrix, rowsum + (4 + pass) * kRadix, err,
+                     st);
         if (e != cudaSuccess) return e;
         uint32_t *tk = kA;
         kA = kB;
