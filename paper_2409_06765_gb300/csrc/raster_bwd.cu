@@ -12,10 +12,6 @@
 // up spread over the lanes -- the atomics of all V values leave in one instruction.
 #include "gs_internal.cuh"
 
-// Resident threads per SM the register allocation must allow (0: no constraint).
-#ifndef GS_RASTER_BWD_MIN_THREADS
-#define GS_RASTER_BWD_MIN_THREADS 0
-#endif
 
 namespace gs {
 
@@ -83,8 +79,7 @@ __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int
 }
 
 template <int TILE, int PPT, int CHC, bool ABSG>
-__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
-                                      GS_RASTER_BWD_MIN_THREADS / RasterShape<TILE, PPT>::kThreads) raster_bwd_kernel(
+__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_kernel(
     const __grid_constant__ CamSet cs, RasterConsts rc, int ch, int batch, const int2 *__restrict__ ranges,
     const int *__restrict__ values, const int *__restrict__ radii, const float2 *__restrict__ means2d,
     const float *__restrict__ conics, const float *__restrict__ opac, const float *__restrict__ colors,
@@ -191,20 +186,22 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
 #pragma unroll
                 for (int i = 0; i < V; ++i) v[i] = 0.f;
                 bool any = false;
+                // the PPT pixels are independent chains: evaluate all of them without branches
+                // (a pair that does not blend gets zero weight and zero dL/dalpha, so every
+                // sum below adds an exact zero and T and S stay as they were)
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (rel >= last[k] || !inx || (unsigned)(py0 + k - bx.z) > (unsigned)bx.w) continue;
+                    const bool act = rel < last[k] && inx && (unsigned)(py0 + k - bx.z) <= (unsigned)bx.w;
                     const float dy = ((float)(py0 + k) + 0.5f) - gg.y;
                     const float sigma = mahalanobis_half(dx, dy, gg.z, gg.w, hh4.x);
-                    if (sigma < 0.f) continue;
                     const float e = gauss_weight(sigma);
                     const float oe = __fmul_rn(hh4.y, e);
                     const float alpha = fminf(amax, oe);
-                    if (alpha < amin) continue;
-                    any = true;
+                    const bool take = act && !(sigma < 0.f) && !(alpha < amin);
+                    any = any || take;
                     const float ra = rcp_approx(1.f - alpha);
                     const float Tn = T[k] * ra;  // transmittance in front of this Gaussian
-                    const float w = alpha * Tn;
+                    const float w = take ? alpha * Tn : 0.f;
                     float gc = 0.f;
 #pragma unroll
                     for (int q4 = 0; q4 < C4; ++q4) {
@@ -219,10 +216,10 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
                             }
                         }
                     }
-                    float dalpha = gc * Tn - GS[k] * ra;
+                    // alpha clamped (oe > amax): no gradient through it
+                    const float dalpha = (take && !(oe > amax)) ? gc * Tn - GS[k] * ra : 0.f;
                     GS[k] += gc * w;
-                    T[k] = Tn;
-                    if (oe > amax) dalpha = 0.f;  // alpha clamped: no gradient through it
+                    T[k] = take ? Tn : T[k];
                     v[5] += e * dalpha;
                     const float dsig = -oe * dalpha;
                     // d sigma / d mu' = -conic D

@@ -10,10 +10,6 @@
 // leaves the batch, and the CTA stops when all of its pixels have (__syncthreads_count).
 #include "gs_internal.cuh"
 
-// Resident threads per SM the register allocation must allow (0: no constraint).
-#ifndef GS_RASTER_FWD_MIN_THREADS
-#define GS_RASTER_FWD_MIN_THREADS 0
-#endif
 
 namespace gs {
 
@@ -22,8 +18,7 @@ struct BgConst {
 };
 
 template <int TILE, int PPT, int CHC, bool COUNT>
-__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
-                                      GS_RASTER_FWD_MIN_THREADS / RasterShape<TILE, PPT>::kThreads) raster_fwd_kernel(
+__global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_kernel(
     const __grid_constant__ CamSet cs, RasterConsts rc, int ch, int batch, const int2 *__restrict__ ranges,
     const int *__restrict__ values, const int *__restrict__ radii, const float2 *__restrict__ means2d,
     const float *__restrict__ conics, const float *__restrict__ opac, const float *__restrict__ colors,
@@ -113,32 +108,35 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads,
                 const float2 h = make_float2(s_h[j].x, s_h[j].y);
                 const bool inx = (unsigned)(px - b.x) <= (unsigned)b.y;
                 const float dx = fx - g.x;
+                {
+                    // the PPT pixels are independent chains: evaluate all of them without
+                    // branches (the decisions become selects) so their latencies overlap
+                    const int rel = start + j - rg.x + 1;
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (done[k] || !inx || (unsigned)(py0 + k - b.z) > (unsigned)b.w) continue;
-                    if (COUNT) ++blends;
-                    const float dy = ((float)(py0 + k) + 0.5f) - g.y;
-                    const float sigma = mahalanobis_half(dx, dy, g.z, g.w, h.x);
-                    if (sigma < 0.f) continue;
-                    const float e = gauss_weight(sigma);
-                    const float alpha = fminf(amax, __fmul_rn(h.y, e));
-                    if (alpha < amin) continue;
-                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
-                    if (Tn < tmin) {
-                        done[k] = true;
-                        continue;
-                    }
-                    const float w = __fmul_rn(alpha, T[k]);
+                    for (int k = 0; k < PPT; ++k) {
+                        const bool act = !done[k] && inx && (unsigned)(py0 + k - b.z) <= (unsigned)b.w;
+                        if (COUNT) blends += act ? 1 : 0;
+                        const float dy = ((float)(py0 + k) + 0.5f) - g.y;
+                        const float sigma = mahalanobis_half(dx, dy, g.z, g.w, h.x);
+                        const float e = gauss_weight(sigma);
+                        const float alpha = fminf(amax, __fmul_rn(h.y, e));
+                        const bool blend = act && !(sigma < 0.f) && !(alpha < amin);
+                        const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                        const bool stop = blend && Tn < tmin;
+                        const bool take = blend && !stop;
+                        const float w = take ? __fmul_rn(alpha, T[k]) : 0.f;
 #pragma unroll
-                    for (int q = 0; q < C4; ++q) {
-                        const float4 v = s_c[j * C4 + q];
-                        if (4 * q + 0 < CHC) acc[k][4 * q + 0] += v.x * w;
-                        if (4 * q + 1 < CHC) acc[k][4 * q + 1] += v.y * w;
-                        if (4 * q + 2 < CHC) acc[k][4 * q + 2] += v.z * w;
-                        if (4 * q + 3 < CHC) acc[k][4 * q + 3] += v.w * w;
+                        for (int q = 0; q < C4; ++q) {
+                            const float4 v = s_c[j * C4 + q];
+                            if (4 * q + 0 < CHC) acc[k][4 * q + 0] += v.x * w;
+                            if (4 * q + 1 < CHC) acc[k][4 * q + 1] += v.y * w;
+                            if (4 * q + 2 < CHC) acc[k][4 * q + 2] += v.z * w;
+                            if (4 * q + 3 < CHC) acc[k][4 * q + 3] += v.w * w;
+                        }
+                        T[k] = take ? Tn : T[k];
+                        last[k] = take ? rel : last[k];
+                        done[k] = done[k] || stop;
                     }
-                    T[k] = Tn;
-                    last[k] = start + j - rg.x + 1;
                 }
             }
         }
