@@ -155,17 +155,27 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
     extern __shared__ float s_coef[];
     int n0 = blockIdx.x * 256;
     int cnt = min(256, N - n0);
+    int n = n0 + threadIdx.x;
+    // this Gaussian's mean and first radius are requested before the coefficient rows, so
+    // their latency overlaps the staging
+    const bool valid = n < N;
+    float mx = 0.f, my = 0.f, mz = 0.f;
+    int r0 = 0;
+    if (valid) {
+        mx = means[3 * n];
+        my = means[3 * n + 1];
+        mz = means[3 * n + 2];
+        r0 = radii[n];
+    }
     const float *src = sh + (size_t)n0 * F;
     stage_rows<F, STRIDE, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
     __syncthreads();
-    int n = n0 + threadIdx.x;
-    if (n >= N) return;
+    if (!valid) return;
     const float *cf = s_coef + threadIdx.x * STRIDE;
-    float mx = means[3 * n], my = means[3 * n + 1], mz = means[3 * n + 2];
     for (int c = 0; c < cs.C; ++c) {
         size_t idx = (size_t)c * N + n;
         float *out = colors + OS * idx;
-        if (radii[idx] <= 0) {
+        if ((c == 0 ? r0 : radii[idx]) <= 0) {
             out[0] = 0.f;
             out[1] = 0.f;
             out[2] = 0.f;
@@ -201,8 +211,11 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
 // same contiguous copy as the coefficients came in.
 constexpr int kShBwdThreads = 128;
 
-template <int DEG>
-__global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const float *__restrict__ sh,
+// ONECAM (a single camera): the gradient row of each Gaussian is written in place over its
+// staged coefficient row once the row has been used, so a CTA needs half the shared memory
+// and twice as many CTAs fit on an SM.
+template <int DEG, bool ONECAM>
+__global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(int N, const float *__restrict__ sh,
                                                                const float *__restrict__ means,
                                                                const int *__restrict__ radii,
                                                                const __grid_constant__ CamSet cs, ShConsts kc,
@@ -214,29 +227,44 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
     const int IS = d_depths ? 4 : 3;  // d_colors rows: (r, g, b) or (r, g, b, depth)
     extern __shared__ float s_coef[];
     __shared__ float s_red[(kShBwdThreads / 32) * 12];
-    float *s_grad = s_coef + kShBwdThreads * STRIDE;
+    float *s_grad = ONECAM ? s_coef : s_coef + kShBwdThreads * STRIDE;
     const int n0 = blockIdx.x * kShBwdThreads;
     const int cnt = min(kShBwdThreads, N - n0);
+    const int n = n0 + threadIdx.x;
+    const bool valid = n < N;
+    // per-Gaussian inputs are requested before the coefficient rows, so their latency
+    // overlaps the staging
+    const float mx = valid ? means[3 * n] : 0.f, my = valid ? means[3 * n + 1] : 0.f,
+                mz = valid ? means[3 * n + 2] : 0.f;
+    const int r0 = valid ? radii[n] : 0;
+    float g0[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid && r0 > 0) {
+        g0[0] = d_colors[IS * (size_t)n];
+        g0[1] = d_colors[IS * (size_t)n + 1];
+        g0[2] = d_colors[IS * (size_t)n + 2];
+        if (d_depths) g0[3] = d_colors[IS * (size_t)n + 3];
+    }
     const float *src = sh + (size_t)n0 * F;
     stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
     float *gr = s_grad + threadIdx.x * STRIDE;
+    if (!ONECAM) {
 #pragma unroll
-    for (int f = 0; f < F; ++f) gr[f] = 0.f;
+        for (int f = 0; f < F; ++f) gr[f] = 0.f;
+    }
     __syncthreads();
-    const int n = n0 + threadIdx.x;
-    const bool valid = n < N;
     const float *cf = s_coef + threadIdx.x * STRIDE;
-    const float mx = valid ? means[3 * n] : 0.f, my = valid ? means[3 * n + 1] : 0.f,
-                mz = valid ? means[3 * n + 2] : 0.f;
     float dm[3] = {0.f, 0.f, 0.f};
     for (int c = 0; c < cs.C; ++c) {  // every thread runs every camera (the pose sums are CTA-wide)
         const size_t idx = (size_t)c * N + n;
         float dv[3] = {0.f, 0.f, 0.f};  // gradient w.r.t. v = mu - centre for this camera
         const float *R = cs.cam[c].R, *t = cs.cam[c].t;
-        if (valid) {
-            if (d_depths) d_depths[idx] = radii[idx] > 0 ? d_colors[IS * idx + 3] : 0.f;
+        const int rc = c == 0 ? r0 : (valid ? radii[idx] : 0);
+        if (valid && d_depths) d_depths[idx] = rc > 0 ? (c == 0 ? g0[3] : d_colors[IS * idx + 3]) : 0.f;
+        if (ONECAM && valid && rc <= 0) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) gr[f] = 0.f;
         }
-        if (valid && radii[idx] > 0) {
+        if (valid && rc > 0) {
             const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
             const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
             const float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
@@ -251,15 +279,23 @@ __global__ void __launch_bounds__(kShBwdThreads) sh_bwd_kernel(int N, const floa
                 float raw = 0.5f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) raw += Y[k] * cf[3 * k + ch];
-                g[ch] = raw > 0.f ? d_colors[IS * idx + ch] : 0.f;  // the clamp at 0 passes no gradient
+                const float gin = c == 0 ? g0[ch] : d_colors[IS * idx + ch];
+                g[ch] = raw > 0.f ? gin : 0.f;  // the clamp at 0 passes no gradient
             }
             float w[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                gr[3 * k] += Y[k] * g[0];
-                gr[3 * k + 1] += Y[k] * g[1];
-                gr[3 * k + 2] += Y[k] * g[2];
-                w[k] = cf[3 * k] * g[0] + cf[3 * k + 1] * g[1] + cf[3 * k + 2] * g[2];
+            for (int k = 0; k < K; ++k) w[k] = cf[3 * k] * g[0] + cf[3 * k + 1] * g[1] + cf[3 * k + 2] * g[2];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {  // (in place: every read of the row is above)
+                if (ONECAM) {
+                    gr[3 * k] = Y[k] * g[0];
+                    gr[3 * k + 1] = Y[k] * g[1];
+                    gr[3 * k + 2] = Y[k] * g[2];
+                } else {
+                    gr[3 * k] += Y[k] * g[0];
+                    gr[3 * k + 1] += Y[k] * g[1];
+                    gr[3 * k + 2] += Y[k] * g[2];
+                }
             }
             if (DEG > 0) {
                 float dd[3] = {0.f, 0.f, 0.f};
@@ -334,13 +370,15 @@ static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, con
                                    const float *d_colors, float *d_sh, float *d_means, float *d_depths,
                                    float *d_viewmats, cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
-    size_t smem = 2 * kShBwdThreads * STRIDE * sizeof(float);
+    const bool one = cs.C == 1;
+    size_t smem = (one ? 1 : 2) * kShBwdThreads * STRIDE * sizeof(float);
+    auto kern = one ? sh_bwd_kernel<DEG, true> : sh_bwd_kernel<DEG, false>;
     if (smem > 48 * 1024) {
-        cudaError_t e = ensure_smem((const void *)sh_bwd_kernel<DEG>, (int)smem);
+        cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sh_bwd_kernel<DEG><<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(N, sh, means, radii, cs, make_sh_consts(), d_colors,
-                                                            d_sh, d_means, d_depths, d_viewmats);
+    kern<<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(
+        N, sh, means, radii, cs, make_sh_consts(), d_colors, d_sh, d_means, d_depths, d_viewmats);
     note_launch();
     return cudaGetLastError();
 }
