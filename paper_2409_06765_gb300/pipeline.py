@@ -106,6 +106,7 @@ class FramePipeline:
             self.d_quats, self.d_log_scales, self.d_logits = f(N, 4), f(N, 3), f(N)
             self.d_image = torch.zeros(self.P, 3, device=dev)
         self.g_pre = self.g_post = None
+        self.side = torch.cuda.Stream(dev)  # SH colours overlap the bin/sort
         self.margin = margin
         self.K = None
         if capacity is None:
@@ -155,14 +156,22 @@ class FramePipeline:
 
     # -- stages ----------------------------------------------------------------------------
     def _pre(self):
+        # project, then SH colours on a side stream while the bin/sort runs on this one: the
+        # SH kernel streams coefficients from HBM while the sort's many short, latency-bound
+        # kernels leave bandwidth idle; both only need the projection, and the compositing
+        # waits for both
         s, L = self.scene, _lib
+        main = torch.cuda.current_stream(self.device)
         L.gs_project(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.means2d,
                      self.depths, self.conics, self.radii, self.tiles, self.opac)
-        L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
         L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity, None,
                            self.values, self.ranges, self.K_out, self.workspace)
         if self.order is not None:
             L.gs_tile_order(self.cams, self.params, self.ranges, self.order)
+        main.wait_stream(self.side)
 
     def _raster_fwd(self, count=None):
         _lib.gs_rasterize_fwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii, self.means2d,
