@@ -301,11 +301,20 @@ def run_ours(args):
         cam_arr = _lib.CameraArray(cams)
 
         def e2e_step():
-            dev_target.copy_(host_target, non_blocking=True)
-            imgs, alphas, _ = raster.rasterization(*leaves, cameras=cam_arr, settings=settings, state=state)
-            loss = (imgs[0].reshape(-1, 3) - dev_target).abs().mean()
-            loss.backward()
-            return float(loss.item())
+            # one training step through the public API: target in, forward, L1 loss, backward,
+            # loss out; gradients start from None as after optimizer.zero_grad(set_to_none=True)
+            for _ in range(3):
+                for x in leaves:
+                    x.grad = None
+                dev_target.copy_(host_target, non_blocking=True)
+                imgs, alphas, _ = raster.rasterization(*leaves, cameras=cam_arr, settings=settings, state=state,
+                                                       defer_sync=True)
+                loss = (imgs[0].reshape(-1, 3) - dev_target).abs().mean()
+                loss.backward()
+                v = float(loss.item())
+                if state.check():  # the lists fit (else the buffers grew: redo the step)
+                    return v
+            raise RuntimeError("intersection lists did not settle")
 
         for _ in range(max(2, args.warmup)):
             e2e_step()
@@ -323,7 +332,8 @@ def run_ours(args):
             e2e_ms = float(t[0])
         e2e = {"value": blends_job / (e2e_ms / 1000.0), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": int(host_target.numel() * 4), "d2h_bytes_per_step": 4,
-               "api": "paper_2409_06765_gb300.raster.rasterization + L1 loss backward"}
+               "api": "paper_2409_06765_gb300.raster.rasterization(defer_sync=True) + L1 loss backward + loss.item()",
+               "redone_steps": state.redone}
 
     peaks, peak_kind = _peaks()
     clk = clocks.summary()

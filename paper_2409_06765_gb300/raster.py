@@ -52,12 +52,35 @@ class RasterSettings:
 
 @dataclass
 class RasterState:
-    """Reusable intersection buffers: grown (x1.25) when a frame needs more than they hold."""
+    """Reusable intersection buffers: grown (x1.25) when a frame needs more than they hold.
+
+    With deferred checking (``rasterization(..., defer_sync=True)``) the forward does not wait
+    for the intersection count: it is copied to host memory behind the frame and ``check()``
+    (called after any later synchronisation, e.g. reading the loss) reports whether the frame
+    fit; a frame that did not must be redone (the buffers have grown by then)."""
     capacity: int = 0
     values: torch.Tensor | None = None
     workspace: torch.Tensor | None = None
     tile_order: torch.Tensor | None = None
     ws_key: tuple = field(default_factory=tuple)
+    pending: tuple | None = None  # (pinned K copy, event, cams, N, params, device) of a deferred frame
+    redone: int = 0
+
+    def check(self) -> bool:
+        """True if the last deferred frame's lists fit; otherwise grows the buffers and returns False."""
+        if self.pending is None:
+            return True
+        K_host, ev, cams, N, params, dev = self.pending
+        self.pending = None
+        ev.synchronize()
+        K = int(K_host.item())
+        if K < 0:
+            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
+        if K <= self.capacity:
+            return True
+        self.ensure(cams, N, params, K, dev)
+        self.redone += 1
+        return False
 
     def ensure(self, cams, N, params, K, device):
         if K > self.capacity or self.values is None:
@@ -93,8 +116,11 @@ def sh_eval(cams, sh_degree, sh, means, radii, depths=None):
     return colors
 
 
-def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None = None, want_keys=False):
-    """Intersection list and tile ranges.  Reads K back to the host (one sync) to size the buffers."""
+def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None = None, want_keys=False,
+             sync=True):
+    """Intersection list and tile ranges.  With ``sync`` K is read back to the host (one sync) and the
+    buffers grown until the list fits; without it the sort runs once at the current capacity and the
+    caller checks ``K_out`` later (the compositing needs only the device-side ranges)."""
     dev = means2d.device
     state = state or RasterState()
     if state.values is None:
@@ -104,6 +130,10 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
     T = cams.num_tiles(params.tile)
     ranges = torch.empty(T, 2, dtype=torch.int32, device=dev)
     K_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    if not sync and not want_keys:
+        _lib.gs_tile_bin_sort(cams, N, params, means2d, depths, radii, state.capacity, None, state.values, ranges,
+                              K_out, state.workspace)
+        return dict(values=state.values, ranges=ranges, K=None, K_out=K_out, keys=None)
     for _ in range(2):
         keys = torch.empty(state.capacity, dtype=torch.int64, device=dev) if want_keys else None
         _lib.gs_tile_bin_sort(cams, N, params, means2d, depths, radii, state.capacity, keys, state.values, ranges,
@@ -115,7 +145,7 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
             break
         state.ensure(cams, N, params, K, dev)
     values = state.values[:K]
-    return dict(values=values, ranges=ranges, K=K, keys=None if keys is None else keys[:K])
+    return dict(values=values, ranges=ranges, K=K, K_out=K_out, keys=None if keys is None else keys[:K])
 
 
 def tile_order(cams, params, ranges):
@@ -142,7 +172,7 @@ def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, con
 
 def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_degree=0, features=None,
                  settings: RasterSettings | None = None, state: RasterState | None = None, count_blends=False,
-                 depth=False):
+                 depth=False, defer_sync=False):
     """Project, colour, bin/sort and composite.  Returns a dict of every intermediate.  With
     ``depth`` (SH colours only) the image gains a fourth channel, the accumulated depth."""
     settings = settings or RasterSettings()
@@ -154,12 +184,30 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
     else:
         colors = features
     ch = colors.shape[-1]
-    bs = bin_sort(cams, N, params, sp["means2d"], sp["depths"], sp["radii"], state)
-    order = tile_order(cams, params, bs["ranges"]) if settings.tile_schedule else None
-    image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
-                                                 sp["means2d"], sp["conics"], sp["opacities"], colors,
-                                                 settings.background, count_blends, order)
-    return dict(sp, colors=colors, values=bs["values"], ranges=bs["ranges"], K=bs["K"], image=image,
+    state = state or RasterState()
+    # the sort and the compositing are queued back to back; K is checked once the whole
+    # forward is on the stream, and the (rare) frame whose list outgrew the buffers is redone
+    for _ in range(3):
+        bs = bin_sort(cams, N, params, sp["means2d"], sp["depths"], sp["radii"], state, sync=False)
+        order = tile_order(cams, params, bs["ranges"]) if settings.tile_schedule else None
+        image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
+                                                     sp["means2d"], sp["conics"], sp["opacities"], colors,
+                                                     settings.background, count_blends, order)
+        if defer_sync:
+            K_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
+            K_host.copy_(bs["K_out"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record()
+            state.pending = (K_host, ev, cams, N, params, means.device)
+            return dict(sp, colors=colors, values=state.values, ranges=bs["ranges"], K=None, image=image,
+                        final_T=final_T, last_contrib=last, blends=blends, params=params, tile_order=order)
+        K = int(bs["K_out"].item())
+        if K < 0:
+            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
+        if K <= state.capacity:
+            break
+        state.ensure(cams, N, params, K, means.device)
+    return dict(sp, colors=colors, values=state.values[:K], ranges=bs["ranges"], K=K, image=image,
                 final_T=final_T, last_contrib=last, blends=blends, params=params, tile_order=order)
 
 
@@ -172,7 +220,7 @@ class RasterizeGaussians(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, means, quats, log_scales, opacity_logits, sh_or_features, cams, sh_degree, settings, state,
-                depth=0, viewmats=None):
+                depth=0, viewmats=None, defer_sync=False):
         use_sh = sh_degree is not None
         if depth and not use_sh:
             raise ValueError("depth rendering needs SH colours")
@@ -184,7 +232,7 @@ class RasterizeGaussians(torch.autograd.Function):
             settings = RasterSettings(**{**settings.__dict__, "background": tuple(settings.background)[:3] + (0.0,)})
         out = forward_pass(cams, means, quats, log_scales, opacity_logits, sh=sh_or_features if use_sh else None,
                            sh_degree=sh_degree if use_sh else 0, features=feats, settings=settings, state=state,
-                           depth=bool(depth))
+                           depth=bool(depth), defer_sync=defer_sync)
         edepth = torch.empty(0, device=means.device)
         if depth == 2:
             edepth = torch.empty(cams.num_pixels, device=means.device)
@@ -210,10 +258,11 @@ class RasterizeGaussians(torch.autograd.Function):
         C, N = cams.C, means.shape[0]
         ch = colors.shape[-1]
         dev = means.device
-        d_means2d = torch.zeros(C, N, 2, device=dev)
-        d_conics = torch.zeros(C, N, 3, device=dev)
-        d_opac = torch.zeros(C, N, device=dev)
-        d_colors = torch.zeros(C, N, ch, device=dev)
+        g2d = torch.zeros(C * N * (6 + ch), device=dev)  # one memset for all accumulated 2D gradients
+        d_means2d = g2d[:C * N * 2].view(C, N, 2)
+        d_conics = g2d[C * N * 2:C * N * 5].view(C, N, 3)
+        d_opac = g2d[C * N * 5:C * N * 6].view(C, N)
+        d_colors = g2d[C * N * 6:].view(C, N, ch)
         absgrad = torch.zeros(C, N, 2, device=dev) if settings.absgrad else None
         d_image = d_image.contiguous() if d_image is not None else torch.zeros(cams.num_pixels, ch, device=dev)
         d_alpha = d_alpha.contiguous() if d_alpha is not None else None
@@ -251,7 +300,7 @@ class RasterizeGaussians(torch.autograd.Function):
                             d_depths, d_means, d_quats, d_log_scales, d_logits, d_viewmats=d_view)
         if d_view is not None:
             d_view = d_view.to(ctx.viewmats_like.device).reshape(ctx.viewmats_like.shape)
-        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None, None, d_view
+        return d_means, d_quats, d_log_scales, d_logits, d_feat, None, None, None, None, None, d_view, None
 
 
 RENDER_MODES = {"RGB": 0, "D": 1, "ED": 2, "RGB+D": 1, "RGB+ED": 2}
@@ -259,7 +308,7 @@ RENDER_MODES = {"RGB": 0, "D": 1, "ED": 2, "RGB+D": 1, "RGB+ED": 2}
 
 def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=None, *, features=None,
                   sh_degree=None, settings: RasterSettings | None = None, state: RasterState | None = None,
-                  render_mode: str = "RGB", viewmats=None):
+                  render_mode: str = "RGB", viewmats=None, defer_sync: bool = False):
     """Render C cameras.  Returns (images, alphas, meta) with one [H, W, ch] / [H, W] tensor per camera.
 
     Pass SH coefficients ``sh`` [N, K, 3] (degree inferred from K) or N-dimensional
@@ -268,12 +317,16 @@ def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=Non
     "RGB"; "D" / "RGB+D" with the accumulated depth sum z alpha T; "ED" / "RGB+ED" with the
     expected depth, the accumulated depth over alpha (App. A).  ``viewmats`` [C,4,4]
     (world->camera, any device) replaces the cameras' poses; when it requires grad, the pose
-    gradient (App. A) flows back to it.
+    gradient (App. A) flows back to it.  ``defer_sync`` (needs ``state``): do not wait for the
+    intersection count; call ``state.check()`` after the next synchronisation and redo the frame
+    when it returns False.
     """
     if cameras is None:
         raise ValueError("cameras are required")
     if render_mode not in RENDER_MODES:
         raise ValueError(f"render_mode must be one of {sorted(RENDER_MODES)}")
+    if defer_sync and state is None:
+        raise ValueError("defer_sync needs a RasterState to report through")
     depth = RENDER_MODES[render_mode]
     if viewmats is not None:
         vm = viewmats.detach().reshape(-1, 4, 4).cpu().numpy()
@@ -290,12 +343,13 @@ def rasterization(means, quats, log_scales, opacity_logits, sh=None, cameras=Non
         K = sh.shape[1]
         sh_degree = {1: 0, 4: 1, 9: 2, 16: 3}[K] if sh_degree is None else sh_degree
         img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, sh, cams,
-                                                             sh_degree, settings, state, depth, viewmats)
+                                                             sh_degree, settings, state, depth, viewmats,
+                                                             defer_sync)
     else:
         if depth:
             raise ValueError("depth render modes need SH colours")
         img, alpha, radii, edepth = RasterizeGaussians.apply(means, quats, log_scales, opacity_logits, features,
-                                                             cams, None, settings, state, 0, viewmats)
+                                                             cams, None, settings, state, 0, viewmats, defer_sync)
     if depth == 2:
         img = torch.cat([img[:, :3], edepth[:, None]], dim=1)
     if render_mode in ("D", "ED"):

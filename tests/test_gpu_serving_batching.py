@@ -134,3 +134,22 @@ def test_backward_memory_holds_no_per_blend_state():
     per_pixel = 4 * (3 + 1 + 1 + 3)        # image, final T, last contributor, dL/dimage
     fixed = pa.device_bytes - (pa.values.numel() * 4 + pa.workspace.numel())
     assert fixed <= N * (per_gauss + per_pair) + P * per_pixel + 64 * 1024
+
+
+def test_deferred_count_check_redoes_a_frame_that_outgrew_the_buffers():
+    import torch as _t
+    from paper_2409_06765_gb300 import raster
+    sc = synth.clustered_scene(20000, 48, sh_degree=1, log_scale_mu=-3.2)
+    cam = synth.sphere_cameras(48, [(200, 150)])[0]
+    ds = DeviceScene.from_host(sc)
+    leaves = [ds.means, ds.quats, ds.log_scales, ds.opacity_logits, ds.sh]
+    ref = raster.rasterization(*leaves, cameras=[cam])[0][0].cpu().numpy()
+    state = raster.RasterState()
+    state.capacity = 1024  # far below this frame's intersection count
+    state.values = _t.empty(1024, dtype=_t.int32, device="cuda")
+    raster.rasterization(*leaves, cameras=[cam], state=state, defer_sync=True)
+    _t.cuda.synchronize()
+    assert state.check() is False and state.capacity > 1024 and state.redone == 1
+    img = raster.rasterization(*leaves, cameras=[cam], state=state, defer_sync=True)[0][0].cpu().numpy()
+    assert state.check() is True
+    np.testing.assert_array_equal(img, ref)
