@@ -652,14 +652,34 @@ def oracle_setup(scene, cam):
     return sp, colors
 
 
-def cpu_baseline(scene, cam, target_np, pixels, gauss_sample=100_000, setup=None, kp_blends=None, seed=99):
+def _pixel_stages(sp, colors, cam, target_np, pp):
+    """The oracle's per-pixel stages (compositing forward and backward) on pixel list ``pp``."""
+    import oracle
+    P = cam.width * cam.height
+    t = time.perf_counter()
+    r = oracle.render_splats(sp, colors, cam.width, cam.height, pixels=pp)
+    d_img = np.sign(r["color"] - target_np[pp]) / (P * 3)
+    oracle.render_splats_bwd(sp, colors, cam.width, cam.height, d_img, pixels=pp)
+    return time.perf_counter() - t, r
+
+
+def oracle_fixed_cost(sp, colors, cam, target_np, reps=3):
+    """Per-call cost of the per-pixel stages that does not scale with pixels (the depth sort of
+    every Gaussian in each call): the fastest of a few one-pixel calls."""
+    from paper_2409_06765_gb300 import synth
+    pix = synth.sample_pixels(cam.width, cam.height, 1, seed=7)
+    return min(_pixel_stages(sp, colors, cam, target_np, pix)[0] for _ in range(reps))
+
+
+def cpu_baseline(scene, cam, target_np, pixels, gauss_sample=100_000, setup=None, kp_blends=None, seed=99,
+                 t_fixed=None):
     """The FP64 oracle, as it stands, on a bounded sample of one view, extrapolated to the view.
 
     Per-Gaussian stages (projection, SH, their backward) run on a seeded subset of
     ``gauss_sample`` Gaussians and scale linearly in N.  Per-pixel stages (brute-force
-    compositing over all depth-sorted Gaussians, forward and backward) run on a seeded
-    pixel sample; the one-off cost of a call (its depth sort) is timed with a one-pixel
-    call and the rest scales linearly in pixels.
+    compositing over all depth-sorted Gaussians, forward and backward, OpenMP over pixels) run
+    on a seeded pixel sample; the per-call fixed cost (``t_fixed``: the depth sort inside each
+    call) is measured separately and the rest scales linearly in pixels.
     """
     import oracle
     from paper_2409_06765_gb300 import synth
@@ -677,24 +697,21 @@ def cpu_baseline(scene, cam, target_np, pixels, gauss_sample=100_000, setup=None
     oracle.project_bwd(sub, cam, np.full((G, 2), 1e-3), np.full((G, 3), 1e-3), np.full(G, 1e-3))
     t_gauss = (time.perf_counter() - t0) * N / G
     sp, colors = setup if setup is not None else oracle_setup(scene, cam)
+    if t_fixed is None:
+        t_fixed = oracle_fixed_cost(sp, colors, cam, target_np)
     pix = synth.sample_pixels(cam.width, cam.height, pixels, seed=seed)
-
-    def pixel_stages(pp):
-        t = time.perf_counter()
-        r = oracle.render_splats(sp, colors, cam.width, cam.height, pixels=pp)
-        d_img = np.sign(r["color"] - target_np[pp]) / (P * 3)
-        oracle.render_splats_bwd(sp, colors, cam.width, cam.height, d_img, pixels=pp)
-        return time.perf_counter() - t, r
-    t_one, _ = pixel_stages(pix[:1])
-    t_many, r = pixel_stages(pix)
-    per_pixel = max(t_many - t_one, 0.0) / max(len(pix) - 1, 1)
-    t_view = t_gauss + max(t_one - per_pixel, 0.0) + per_pixel * P
+    t_many, r = _pixel_stages(sp, colors, cam, target_np, pix)
+    per_pixel = (t_many - t_fixed) / len(pix)
+    if per_pixel <= 0.0:  # timing noise above the pixel work: bound it by the whole call
+        per_pixel = t_many / len(pix)
+    t_view = t_gauss + t_fixed + per_pixel * P
     sample_blends = int(r["blends"].sum())
     blends_view = kp_blends if kp_blends is not None else sample_blends * P / len(pix)
     return {"value": blends_view / t_view, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "ms_per_view_extrapolated": t_view * 1000.0,
             "sample": f"per-Gaussian stages on {G} of {N} Gaussians (x{N / G:.1f}); per-pixel fwd+bwd on {len(pix)} "
-                      f"of {P} pixels (seed {seed}), {per_pixel * 1e3:.3f} ms/pixel, extrapolated linearly",
+                      f"of {P} pixels (seed {seed}), {per_pixel * 1e3:.3f} ms/pixel after a {t_fixed * 1e3:.0f} ms "
+                      f"per-call fixed cost, extrapolated linearly",
             "sample_blends": sample_blends}
 
 
@@ -710,9 +727,15 @@ def run_reference(args):
     rng = np.random.default_rng(5)
     target_np = rng.uniform(0.0, 1.0, (cam.width * cam.height, 3)).astype(np.float32)
     setup = oracle_setup(scene, cam)
+    t_fixed = oracle_fixed_cost(*setup, cam, target_np)
+    # each step is a bounded sample sized so that warm-up + steps take about --ref-budget seconds
+    per_step = args.ref_budget / (args.warmup + args.steps)
+    pixels = int(np.clip(per_step / max(t_fixed, 1e-3) * 32, 8, args.ref_pixels))
+    gauss = int(np.clip(per_step * 100_000, 5_000, 50_000))
     results = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(scene, cam, target_np, args.ref_pixels, gauss_sample=50_000, setup=setup, seed=99 + k)
+        r = cpu_baseline(scene, cam, target_np, pixels, gauss_sample=gauss, setup=setup, seed=99 + k,
+                         t_fixed=t_fixed)
         if k >= args.warmup:
             results.append(r)
     t_view = float(np.mean([r["ms_per_view_extrapolated"] for r in results]))
@@ -743,7 +766,8 @@ def main():
     ap.add_argument("--bwd-batch", type=int, default=0, help="backward batch depth (0: as --batch)")
     ap.add_argument("--bwd-ppt", type=int, default=0, help="backward pixels per thread (0: as --ppt)")
     ap.add_argument("--cpu-pixels", type=int, default=1024)
-    ap.add_argument("--ref-pixels", type=int, default=128)
+    ap.add_argument("--ref-pixels", type=int, default=256, help="largest pixel sample of a reference step")
+    ap.add_argument("--ref-budget", type=float, default=150.0, help="seconds the reference steps may take")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every stage directly instead of graph replays")
