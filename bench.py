@@ -224,7 +224,8 @@ def run_ours(args):
     else:
         sched = Schedule(tile=args.tile, batch_depth=args.batch, pixels_per_thread=args.ppt,
                          tile_order=not args.no_tile_order, bwd_batch_depth=args.bwd_batch,
-                         bwd_pixels_per_thread=args.bwd_ppt)
+                         bwd_pixels_per_thread=args.bwd_ppt, persistent=bool(args.persistent & 1),
+                         bwd_persistent=bool(args.persistent & 2))
     kp = FramePipeline(dscene, cams, sched)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
@@ -294,7 +295,8 @@ def run_ours(args):
         settings = raster.RasterSettings(tile=sched.tile, batch_depth=sched.batch_depth,
                                          pixels_per_thread=sched.pixels_per_thread, tile_schedule=sched.tile_order,
                                          bwd_batch_depth=sched.params_bwd().batch_depth,
-                                         bwd_pixels_per_thread=sched.params_bwd().pixels_per_thread)
+                                         bwd_pixels_per_thread=sched.params_bwd().pixels_per_thread,
+                                         persistent=sched.persistent, bwd_persistent=sched.bwd_persistent)
         state = raster.RasterState()
         host_target = torch.as_tensor(target_np).pin_memory()
         dev_target = torch.empty_like(target)
@@ -392,6 +394,7 @@ def run_ours(args):
                    "batch_depth": sched.batch_depth, "pixels_per_thread": sched.pixels_per_thread,
                    "bwd_batch_depth": sched.params_bwd().batch_depth,
                    "bwd_pixels_per_thread": sched.params_bwd().pixels_per_thread,
+                   "persistent_launch": [bool(sched.persistent), bool(sched.bwd_persistent)],
                    "schedule_from": "autotuner" if tuned else "command line",
                    "cuda_graphs": graphs, "tile_order": sched.tile_order, "intersections_K": kp.K, "blends_per_view": blends,
                    "l2": "inputs (708 MB of parameters) exceed L2; no flush", "parallelism": f"replicas x{world}"},
@@ -765,6 +768,8 @@ def main():
     ap.add_argument("--ppt", type=int, default=2, help="pixels per compositing thread (0 = library default)")
     ap.add_argument("--bwd-batch", type=int, default=0, help="backward batch depth (0: as --batch)")
     ap.add_argument("--bwd-ppt", type=int, default=0, help="backward pixels per thread (0: as --ppt)")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="persistent compositing launches: 1 forward, 2 backward, 3 both")
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=256, help="largest pixel sample of a reference step")
     ap.add_argument("--ref-budget", type=float, default=150.0, help="seconds the reference steps may take")

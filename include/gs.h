@@ -78,6 +78,9 @@ typedef struct gs_params {
     float alpha_min;      /* a (pixel, Gaussian) pair with alpha < alpha_min is skipped */
     float alpha_max;      /* alpha = min(alpha_max, o * exp(-sigma)) */
     float T_min;          /* a Gaussian that would bring T below T_min is excluded and ends the pixel */
+    int32_t persistent;   /* compositing launch: 0 = one CTA per tile; 1 = as many CTAs as fit on the GPU,
+                             each taking the next tile of tile_order (heaviest first) until none is left;
+                             needs the tile_order of gs_tile_order.  Changes the schedule only. */
 } gs_params;
 
 GS_API void gs_default_params(gs_params *params);
@@ -236,7 +239,9 @@ GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int32_t C, int3
 /* of a launch whose per-tile work is uneven (clustered scenes, many views).  */
 /*                                                                          */
 /* in : tile_ranges [T,2] from gs_tile_bin_sort                              */
-/* out: tile_order [T] int32, a permutation of 0..T-1 (T = gs_num_tiles)     */
+/* out: tile_order [T + 4] int32: a permutation of 0..T-1 (T = gs_num_tiles),*/
+/*      then four work counters of the persistent compositing launches,      */
+/*      zeroed here (each launch leaves them zero again when it ends)         */
 /* One CTA, no scratch; never synchronises.                                  */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_tile_order(const gs_camera *cams, int32_t C, const gs_params *params,
@@ -260,9 +265,11 @@ GS_API gs_status gs_tile_order(const gs_camera *cams, int32_t C, const gs_params
 /*      blend_count (optional device int64, NULL to skip): += the number of   */
 /*      (pixel, Gaussian) pairs whose alpha was evaluated.                    */
 /* channels: 1..GS_MAX_CHANNELS; 1,2,3,4,8,16,32,64 use specialised kernels.  */
-/* tile_order (optional device int32 [T], NULL for 0..T-1): the order in      */
+/* tile_order (optional device int32 [T + 4], NULL for 0..T-1): the order in */
 /*      which tiles are handed to the GPU (gs_tile_order: heaviest first);    */
-/*      it must be a permutation of 0..T-1.  Results do not depend on it.     */
+/*      a permutation of 0..T-1 followed by the persistent launches' work     */
+/*      counters (required when params->persistent).  Results do not depend  */
+/*      on it.                                                                */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                            int32_t channels, const int32_t *tile_ranges, const int32_t *values,

@@ -2,14 +2,15 @@
 
 The paper exposes the tile size and the per-tile batch as tunable block sizes; here they
 are the tile edge t in {8, 16, 32}, and for each compositing kernel separately the batch
-depth (Gaussians staged in shared memory per round, 64..1024) and the pixels each thread
-owns.  The support rule is per pixel, so every schedule renders bit-identical images:
-tuning changes speed only.
+depth (Gaussians staged in shared memory per round, 64..1024), the pixels each thread owns,
+and the launch form (one CTA per tile, or one persistent launch of as many CTAs as fit that
+take tiles heaviest first).  The support rule is per pixel, so every schedule renders
+bit-identical images: tuning changes speed only.
 
 For each tile size ``tune`` builds one FramePipeline (the tile size fixes the intersection
 lists), times the stages before and after compositing as CUDA-graph replays, and times
-every (pixels per thread, batch depth) of the forward and of the backward compositing
-kernel on the same lists; the schedule of a tile size is its fastest forward plus its
+every (pixels per thread, batch depth, launch form) of the forward and of the backward
+compositing kernel on the same lists; the schedule of a tile size is its fastest forward plus its
 fastest backward, and the fastest total over tile sizes wins.  Tile sizes that cannot run
 (intersection lists beyond the int32 index range, device memory) are recorded as failed.
 Results are cached per workload signature (device, scene size, SH degree, camera sizes,
@@ -77,36 +78,36 @@ def _tune_tile(scene, cams, tile, backward, reps, table, log):
         if backward:
             ms_fixed += _time(pipe.g_post.replay, reps)
         best = {}
+        shapes = [(p, b, q) for p in TILE_SHAPES[tile] for b in BATCH_DEPTHS for q in (False, True)]
         for phase in (("fwd", "bwd") if backward else ("fwd",)):
-            for ppt in TILE_SHAPES[tile]:
-                for batch in BATCH_DEPTHS:
-                    params = _lib.make_params(tile=tile, batch_depth=batch, pixels_per_thread=ppt)
-                    if phase == "fwd":
-                        pipe.params = params
-                        fn = pipe._raster_fwd
-                    else:
-                        pipe.params_bwd = params
+            for ppt, batch, pers in shapes:
+                params = _lib.make_params(tile=tile, batch_depth=batch, pixels_per_thread=ppt, persistent=pers)
+                if phase == "fwd":
+                    pipe.params = params
+                    fn = pipe._raster_fwd
+                else:
+                    pipe.params_bwd = params
 
-                        def fn():
-                            pipe.g2d.zero_()
-                            pipe._raster_bwd()
-                    try:
-                        ms, note = _time(fn, reps), ""
-                    except RuntimeError as exc:
-                        ms, note = None, f"failed: {str(exc).splitlines()[0][:100]}"
-                    table.append(dict(tile=tile, phase=phase, ppt=ppt, batch=batch, ms=ms, note=note))
-                    if log:
-                        log(f"  tile {tile:2d} {phase} ppt {ppt} batch {batch:4d}: "
-                            + (f"{ms:.3f} ms" if ms is not None else note))
-                    if ms is not None and (phase not in best or ms < best[phase][0]):
-                        best[phase] = (ms, ppt, batch)
+                    def fn():
+                        pipe.g2d.zero_()
+                        pipe._raster_bwd()
+                try:
+                    ms, note = _time(fn, reps), ""
+                except RuntimeError as exc:
+                    ms, note = None, f"failed: {str(exc).splitlines()[0][:100]}"
+                table.append(dict(tile=tile, phase=phase, ppt=ppt, batch=batch, persistent=pers, ms=ms, note=note))
+                if log:
+                    log(f"  tile {tile:2d} {phase} ppt {ppt} batch {batch:4d}{' persistent' if pers else ''}: "
+                        + (f"{ms:.3f} ms" if ms is not None else note))
+                if ms is not None and (phase not in best or ms < best[phase][0]):
+                    best[phase] = (ms, ppt, batch, pers)
         if pipe.frame_overflowed():
             raise RuntimeError("intersection buffers overflowed while tuning")
         total = ms_fixed + sum(v[0] for v in best.values())
         f = best["fwd"]
         b = best.get("bwd", f)
         sched = Schedule(tile=tile, batch_depth=f[2], pixels_per_thread=f[1], bwd_batch_depth=b[2],
-                         bwd_pixels_per_thread=b[1])
+                         bwd_pixels_per_thread=b[1], persistent=f[3], bwd_persistent=b[3])
         table.append(dict(tile=tile, phase="total", ms=total, fixed_ms=ms_fixed, schedule=sched.as_dict()))
         return sched, total
     finally:
@@ -136,7 +137,7 @@ def tune(scene: DeviceScene, cams, backward=True, tiles=(8, 16, 32), reps=5, use
     if best is None:
         raise RuntimeError("no schedule could run this workload")
     if not tile_order:
-        best = Schedule(**{**best.__dict__, "tile_order": False})
+        best = Schedule(**{**best.__dict__, "tile_order": False, "persistent": False, "bwd_persistent": False})
     res = TuneResult(best, best_ms, table)
     _CACHE[key] = res
     if cache_file:

@@ -683,6 +683,7 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(int T, const int2 *__r
     __shared__ int s_cnt[64];
     __shared__ int s_cur[64];
     if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < 4) order[T + threadIdx.x] = 0;  // work counters of persistent compositing launches
     __syncthreads();
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         const int2 r = ranges[t];

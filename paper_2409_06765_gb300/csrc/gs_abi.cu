@@ -40,6 +40,38 @@ int raster_pixels_per_thread(int tile, int ppt);
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int persistent_grid(const void *kernel, int threads, int smem, int work) {
+    struct Entry {
+        int dev;
+        const void *kernel;
+        int smem;
+        int ctas;
+    };
+    static std::mutex mu;
+    static Entry table[256];
+    static int used = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return work;
+    int ctas = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < used; ++i)
+            if (table[i].dev == dev && table[i].kernel == kernel && table[i].smem == smem) ctas = table[i].ctas;
+    }
+    if (ctas == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm <= 0) {
+            cudaGetLastError();
+            return work;  // fall back to one CTA per work item
+        }
+        ctas = per_sm * sms;
+        std::lock_guard<std::mutex> lock(mu);
+        if (used < 256) table[used++] = Entry{dev, kernel, smem, ctas};
+    }
+    return ctas < work ? ctas : work;
+}
+
 cudaError_t ensure_smem(const void *kernel, int bytes) {
     struct Entry {
         int dev;
@@ -156,6 +188,8 @@ static gs_status check_params(const gs_params *p, RasterConsts &rc) {
     rc.T_min = p->T_min;
     rc.antialiased = p->antialiased ? 1 : 0;
     rc.tile_order = nullptr;
+    rc.work = nullptr;
+    if (p->persistent != 0 && p->persistent != 1) return fail_arg("persistent must be 0 or 1");
     return GS_OK;
 }
 
@@ -183,6 +217,7 @@ void gs_default_params(gs_params *p) {
     p->batch_depth = 256;
     p->antialiased = 0;
     p->pixels_per_thread = 0;
+    p->persistent = 0;
     p->eps2d = 0.3f;
     p->near_plane = 0.01f;
     p->alpha_min = 1.f / 255.f;
@@ -377,6 +412,10 @@ gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     if (blend_count && !aligned(blend_count, 8)) return fail_arg("blend_count must be 8-byte aligned");
     rc.tile_order = tile_order;
+    if (params->persistent) {
+        if (!tile_order) return fail_arg("a persistent launch needs the tile_order of gs_tile_order");
+        rc.work = const_cast<int32_t *>(tile_order) + cs.total_tiles;  // counters 0, 1
+    }
     cudaError_t e = launch_raster_fwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, image, final_T, last_contrib,
                                       (unsigned long long *)blend_count, (cudaStream_t)stream);
@@ -411,6 +450,10 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
     if (absgrad && !aligned(absgrad, 8)) return fail_arg("absgrad must be 8-byte aligned");
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     rc.tile_order = tile_order;
+    if (params->persistent) {
+        if (!tile_order) return fail_arg("a persistent launch needs the tile_order of gs_tile_order");
+        rc.work = const_cast<int32_t *>(tile_order) + cs.total_tiles + 2;  // counters 2, 3
+    }
     cudaError_t e = launch_raster_bwd(cs, rc, channels, params->batch_depth, ppt, tile_ranges, values, radii, means2d,
                                       conics, opacities, colors, background, final_T, last_contrib, d_image, d_alpha,
                                       d_means2d, d_conics, d_opacities, d_colors, absgrad, (cudaStream_t)stream);

@@ -19,6 +19,10 @@ void set_last_error(const char *text);
 // can stall the host until the device is idle, which would serialise eager launches.
 cudaError_t ensure_smem(const void *kernel, int bytes);
 
+// CTAs of `kernel` (threads, dynamic shared memory) that fit on the current device at once,
+// capped at `work` items: the grid of a persistent launch.  Cached per (device, kernel, smem).
+int persistent_grid(const void *kernel, int threads, int smem, int work);
+
 constexpr int kMaxCams = GS_MAX_CAMERAS;
 
 // Per-camera constants, passed to kernels by value (a __grid_constant__ CamSet).
@@ -50,7 +54,30 @@ struct RasterConsts {
     float eps2d, near_plane, alpha_min, alpha_max, T_min;
     int antialiased;
     const int *tile_order;  // compositing: CTA b renders tile tile_order[b] (NULL: tile b)
+    int *work;              // persistent compositing: [next index, CTAs finished] (NULL: one CTA per tile)
 };
+
+// Persistent compositing: the next index into tile_order for this CTA (read by every thread),
+// or total when the work is exhausted.  Uses one shared int of the caller.
+__device__ __forceinline__ int next_work_item(int *work, int *s_next) {
+    if (threadIdx.x == 0) *s_next = atomicAdd(work, 1);
+    __syncthreads();
+    const int i = *s_next;
+    __syncthreads();
+    return i;
+}
+
+// Persistent compositing: the last CTA to finish resets the counters for the next launch.
+__device__ __forceinline__ void finish_work(int *work) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {  // every CTA has taken its last index
+            work[0] = 0;
+            work[1] = 0;
+        }
+    }
+}
 
 // Sums v[0..V) over the CTA and adds the totals to dst[0..V) with one atomic each (thread
 // k adds value k).  Every thread of the CTA must call it; s_red holds V * (warps) floats.

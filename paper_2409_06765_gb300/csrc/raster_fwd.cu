@@ -33,8 +33,19 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
     int4 *s_b = reinterpret_cast<int4 *>(s_h + batch);
     float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
 
-    const int gt = tile_of_block(rc, cs.total_tiles);
-    if (gt < 0) return;  // uniform over the CTA
+    __shared__ int s_next;
+    for (int round = 0;; ++round) {
+    int gt;
+    if (rc.work) {  // persistent: tiles in tile_order, heaviest first, until none is left
+        const int i = next_work_item(rc.work, &s_next);
+        if (i >= cs.total_tiles) break;
+        gt = rc.tile_order[i];
+        if ((unsigned)gt >= (unsigned)cs.total_tiles) continue;  // uniform over the CTA
+    } else {
+        if (round > 0) break;
+        gt = tile_of_block(rc, cs.total_tiles);
+        if (gt < 0) break;  // uniform over the CTA
+    }
     const int c = camera_of_tile(cs, gt);
     const CamDev &cam = cs.cam[c];
     const int local = gt - cam.tile_offset;
@@ -158,6 +169,9 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
         for (int o = 16; o > 0; o >>= 1) blends += __shfl_down_sync(0xffffffffu, blends, o);
         if (lane == 0 && blends) atomicAdd(blend_count, blends);
     }
+    __syncthreads();  // the next tile reuses the shared memory
+    }
+    if (rc.work) finish_work(rc.work);
 }
 
 // Shared memory of one compositing batch: geometry, conic/opacity/cut, box, colour (padded to float4).
@@ -179,7 +193,10 @@ static cudaError_t launch_fwd_t(const CamSet &cs, const RasterConsts &rc, int ch
         if (e != cudaSuccess) return e;
     }
     if (cs.total_tiles == 0) return cudaSuccess;
-    kern<<<cs.total_tiles, RasterShape<TILE, PPT>::kThreads, smem, st>>>(
+    const int grid = rc.work ? persistent_grid((const void *)kern, RasterShape<TILE, PPT>::kThreads, (int)smem,
+                                               cs.total_tiles)
+                             : cs.total_tiles;
+    kern<<<grid, RasterShape<TILE, PPT>::kThreads, smem, st>>>(
         cs, rc, ch, batch, (const int2 *)ranges, values, radii, (const float2 *)means2d, conics, opac, colors, bg,
         image, final_T, last_contrib, blend_count);
     note_launch();

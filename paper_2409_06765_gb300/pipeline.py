@@ -35,19 +35,23 @@ class Schedule:
     tile_order: bool = True
     bwd_batch_depth: int = 0
     bwd_pixels_per_thread: int = 0
+    persistent: bool = False      # forward compositing as one persistent launch (needs tile_order)
+    bwd_persistent: bool = False  # backward likewise
 
     def params(self) -> _lib.GsParams:
-        return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread)
+        return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
+                                persistent=self.persistent and self.tile_order)
 
     def params_bwd(self) -> _lib.GsParams:
         return _lib.make_params(tile=self.tile, batch_depth=self.bwd_batch_depth or self.batch_depth,
-                                pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread)
+                                pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread,
+                                persistent=self.bwd_persistent and self.tile_order)
 
     def as_dict(self):
         return dict(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
                     bwd_batch_depth=self.bwd_batch_depth or self.batch_depth,
                     bwd_pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread,
-                    tile_order=self.tile_order)
+                    tile_order=self.tile_order, persistent=self.persistent, bwd_persistent=self.bwd_persistent)
 
 
 class DeviceScene:
@@ -92,7 +96,7 @@ class FramePipeline:
         self.T = self.cams.num_tiles(schedule.tile)
         self.image, self.final_T, self.last = f(self.P, 3), f(self.P), i(self.P)
         self.ranges = i(self.T, 2)
-        self.order = i(self.T) if schedule.tile_order else None
+        self.order = i(self.T + 4) if schedule.tile_order else None  # order, then the work counters
         self.K_out = torch.zeros(1, dtype=torch.int64, device=dev)
         if backward:
             # 2D gradients in one allocation so that one memset clears them

@@ -39,15 +39,19 @@ class RasterSettings:
     tile_schedule: bool = True  # hand the longest tile lists to the GPU first (gs_tile_order)
     bwd_batch_depth: int = 0        # backward compositing launch (0: as the forward's)
     bwd_pixels_per_thread: int = 0
+    persistent: bool = False        # compositing as persistent launches over tile_schedule's order
+    bwd_persistent: bool = False
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
-                                self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread)
+                                self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread,
+                                persistent=self.persistent and self.tile_schedule)
 
     def params_bwd(self) -> _lib.GsParams:
         return _lib.make_params(self.tile, self.bwd_batch_depth or self.batch_depth, self.antialiased, self.eps2d,
                                 self.near_plane, self.alpha_min, self.alpha_max, self.T_min,
-                                self.bwd_pixels_per_thread or self.pixels_per_thread)
+                                self.bwd_pixels_per_thread or self.pixels_per_thread,
+                                persistent=self.bwd_persistent and self.tile_schedule)
 
 
 @dataclass
@@ -150,7 +154,7 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
 
 def tile_order(cams, params, ranges):
     """Launch order of the compositing kernels: longest tile lists first."""
-    order = torch.empty(ranges.shape[0], dtype=torch.int32, device=ranges.device)
+    order = torch.empty(ranges.shape[0] + 4, dtype=torch.int32, device=ranges.device)  # + work counters
     _lib.gs_tile_order(cams, params, ranges, order)
     return order
 

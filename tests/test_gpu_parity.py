@@ -196,9 +196,11 @@ def test_tile_order_is_a_permutation_longest_first_and_changes_nothing():
     cams = synth.sphere_cameras(12, [(200, 120), (96, 64), (333, 201)])
     plain = gpu_render(sc, cams, settings=raster.RasterSettings(tile_schedule=False))[0]
     ordered = gpu_render(sc, cams, settings=raster.RasterSettings(tile_schedule=True))[0]
-    order = ordered["tile_order"].cpu().numpy()
     rg = ordered["ranges"].cpu().numpy()
     T = rg.shape[0]
+    full = ordered["tile_order"].cpu().numpy()
+    assert full.shape[0] == T + 4 and np.all(full[T:] == 0)  # the order, then zeroed work counters
+    order = full[:T]
     assert np.array_equal(np.sort(order), np.arange(T))
     lengths = rg[order, 1] - rg[order, 0]
     buckets = np.array([_bucket(n) for n in lengths])
@@ -406,3 +408,23 @@ def test_absgrad_matches_oracle():
     sp = ref_f["splats"]
     g2 = oracle.render_splats_bwd(sp, ref_f["colors"], cam.width, cam.height, d_img, want_absgrad=True)
     assert rel_l2(ag, g2["absgrad"]) < 1e-3
+
+
+def test_persistent_launches_render_the_same_and_reset_their_counters():
+    sc = synth.clustered_scene(15000, 14, sh_degree=2, log_scale_mu=-3.3)
+    cams = synth.sphere_cameras(14, [(160, 120), (96, 64), (211, 133)])
+    base = gpu_render(sc, cams, settings=raster.RasterSettings(tile_schedule=True))[0]
+    st = raster.RasterSettings(tile_schedule=True, persistent=True, bwd_persistent=True)
+    for _ in range(2):  # a second launch must find its counters zeroed by the first
+        out = gpu_render(sc, cams, settings=st)[0]
+        for k in ("image", "final_T", "last_contrib"):
+            np.testing.assert_array_equal(out[k].cpu().numpy(), base[k].cpu().numpy())
+        T = out["ranges"].shape[0]
+        assert np.all(out["tile_order"][T:].cpu().numpy() == 0)
+    rng = np.random.default_rng(15)
+    P = sum(c.width * c.height for c in cams)
+    g = rng.normal(size=(P, 3)).astype(np.float32)
+    a = gpu_grads(sc, cams, g, settings=raster.RasterSettings())[0]
+    b = gpu_grads(sc, cams, g, settings=st)[0]
+    for k in a:
+        assert rel_l2(b[k], a[k]) <= 1e-5, k

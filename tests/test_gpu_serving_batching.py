@@ -40,7 +40,7 @@ def test_autotuner_times_every_candidate_and_caches_the_winner():
     res = autotune.tune(ds, cams, backward=True, reps=1, use_cache=False)
     per_kernel = [r for r in res.table if r["phase"] in ("fwd", "bwd")]
     n_shapes = sum(len(v) for v in autotune.TILE_SHAPES.values())
-    assert len(per_kernel) == 2 * n_shapes * len(autotune.BATCH_DEPTHS)
+    assert len(per_kernel) == 2 * n_shapes * len(autotune.BATCH_DEPTHS) * 2  # x one-CTA-per-tile / persistent
     totals = [r["ms"] for r in res.table if r["phase"] == "total" and r["ms"] is not None]
     assert totals and res.best_ms == min(totals)
     # a tile size's total is its fixed stages plus its fastest forward and backward
