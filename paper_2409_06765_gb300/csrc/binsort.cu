@@ -822,7 +822,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     note_launch();
     // stage 1: depth order of all (camera, Gaussian) pairs
     const int eb = (cn + 255) / 256;
-    depth_keys_kernel<<<G, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0);
+    depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -867,7 +867,10 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     // (kA, vA) now hold the sorted list; vA == values
     zero_ints_kernel<<<(2 * T + 255) / 256, 256, 0, st>>>(2 * T, tile_ranges);
     note_launch();
-    ranges_kernel<<<G, 256, 0, st>>>(n_eff, T, cn, kA, vA, depths, (int2 *)tile_ranges, keys64);
+    // one thread per 4 entries of the largest possible list (threads past the real count exit)
+    const long long rq = (Kcap + 3) / 4;
+    ranges_kernel<<<(unsigned)((rq + 255) / 256 > 0 ? (rq + 255) / 256 : 1), 256, 0, st>>>(
+        n_eff, T, cn, kA, vA, depths, (int2 *)tile_ranges, keys64);
     note_launch();
     report_error_kernel<<<1, 32, 0, st>>>(err, K_out);
     note_launch();
