@@ -99,10 +99,6 @@ __global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restri
     }
 }
 
-// Reports a timed-out bulk-copy wait (never expected) through K_out.
-__global__ void report_error_kernel(const int *__restrict__ err, long long *__restrict__ K_out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && *err) *K_out = -1;
-}
 
 // ---------------------------------------------------------------------------
 // stage 1 keys
@@ -116,7 +112,9 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
                                                          const float2 *__restrict__ means2d,
                                                          const float *__restrict__ depths,
                                                          const int *__restrict__ radii, uint32_t *__restrict__ keys,
-                                                         int *__restrict__ vals) {
+                                                         int *__restrict__ vals, int *__restrict__ misc) {
+    if (blockIdx.x == 0)  // the sort's counters, digit totals and error flag start at zero
+        for (int i = threadIdx.x; i < kMiscInts; i += blockDim.x) misc[i] = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < CN; i += gridDim.x * blockDim.x) {
         const int r = radii[i];
         bool ok = r > 0;
@@ -446,11 +444,14 @@ __device__ __forceinline__ bool tile_rect(const CamSet &cs, int N, int i, const 
 
 // Tiles touched by each pair, in depth order, their sum per CTA, and each pair's tile
 // rectangle packed as (tx0 | ty0 << 16, width | camera << 16) for the emission.
-__global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, const __grid_constant__ CamSet cs,
+__global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, int *__restrict__ tile_ranges,
+                                                          const __grid_constant__ CamSet cs,
                                                           const int *__restrict__ order,
                                                           const float2 *__restrict__ means2d,
                                                           const int *__restrict__ radii, int *__restrict__ counts,
                                                           int2 *__restrict__ rects, long long *__restrict__ partials) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * T; i += gridDim.x * blockDim.x)
+        tile_ranges[i] = 0;  // empty tiles read (0, 0); the ranges kernel fills the others later
     __shared__ long long s_w[8];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     int cnt = 0;
@@ -632,7 +633,10 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
 // Tile boundaries of the sorted list; each thread looks at 4 consecutive entries.
 __global__ void ranges_kernel(const int *__restrict__ n_dev, int T, int CN, const uint32_t *__restrict__ tkeys,
                               const int *__restrict__ vals, const float *__restrict__ depths,
-                              int2 *__restrict__ ranges, unsigned long long *__restrict__ keys64) {
+                              int2 *__restrict__ ranges, unsigned long long *__restrict__ keys64,
+                              const int *__restrict__ err, long long *__restrict__ K_out) {
+    // a timed-out bulk-copy wait in any pass (never expected) is reported through K_out
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *err) *K_out = -1;
     const int n = *n_dev;
     const int nq = (n + 3) / 4;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -817,12 +821,9 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     const int bits = tile_bits(T);
     const int tpasses = (bits + 6) / 7;                // passes of at most 7 bits
     const int tdigit = (bits + tpasses - 1) / tpasses;  // equal digit widths
-    // n_eff, error flag
-    zero_ints_kernel<<<(kMiscInts + 255) / 256, 256, 0, st>>>(kMiscInts, misc);
-    note_launch();
     // stage 1: depth order of all (camera, Gaussian) pairs
     const int eb = (cn + 255) / 256;
-    depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0);
+    depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0, misc);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -834,7 +835,8 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     }
     const int *order = dv0;  // after 4 passes the sorted pairs are back in (dk0, dv0)
     // stage 2: tile counts, offsets, balanced emission, stable sort by tile id
-    count_tiles_kernel<<<eb, 256, 0, st>>>(cn, N, cs, order, (const float2 *)means2d, radii, counts, rects, partials);
+    count_tiles_kernel<<<eb, 256, 0, st>>>(cn, N, T, tile_ranges, cs, order, (const float2 *)means2d, radii, counts,
+                                           rects, partials);
     note_launch();
     partial_scan_kernel<<<1, 1024, 0, st>>>(eb, partials, Kcap, K_out, n_eff);
     note_launch();
@@ -865,14 +867,10 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
         vB = tv;
     }
     // (kA, vA) now hold the sorted list; vA == values
-    zero_ints_kernel<<<(2 * T + 255) / 256, 256, 0, st>>>(2 * T, tile_ranges);
-    note_launch();
     // one thread per 4 entries of the largest possible list (threads past the real count exit)
     const long long rq = (Kcap + 3) / 4;
     ranges_kernel<<<(unsigned)((rq + 255) / 256 > 0 ? (rq + 255) / 256 : 1), 256, 0, st>>>(
-        n_eff, T, cn, kA, vA, depths, (int2 *)tile_ranges, keys64);
-    note_launch();
-    report_error_kernel<<<1, 32, 0, st>>>(err, K_out);
+        n_eff, T, cn, kA, vA, depths, (int2 *)tile_ranges, keys64, err, K_out);
     note_launch();
     return cudaGetLastError();
 }
