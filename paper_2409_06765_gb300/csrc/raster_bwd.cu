@@ -78,6 +78,62 @@ __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int
     }
 }
 
+#ifndef GS_BWD_SMEM_REDUCE
+#define GS_BWD_SMEM_REDUCE 1
+#endif
+
+// The shared-memory reduction pays off where a warp covers few pixels per Gaussian (1 or 2 per
+// thread: more reductions per blend); with 4 pixels per thread the butterfly is faster.
+template <int PPT>
+__host__ __device__ constexpr bool smem_reduce() {
+    return GS_BWD_SMEM_REDUCE && PPT <= 2;
+}
+
+// Warp sum of the V values through a per-warp [8][32] shared transpose: for each group of 8
+// values every lane stores its 8 values (value-major), then lane l sums value l / 4 over the 8
+// lanes 8 (l % 4) .. 8 (l % 4) + 7 with two 16-byte loads and finishes with two shuffles, so a
+// group costs 8 stores, 2 loads, 2 shuffles and 9 adds per lane instead of a shuffle butterfly
+// with a select per value and step.  A group of at most two values uses plain butterflies.
+template <int V, int OFF, bool ABSG>
+__device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, int lane, int id, int ch,
+                                            float *d_means2d, float *d_conics, float *d_opac, float *d_colors,
+                                            float *absgrad) {
+    if constexpr (OFF < V) {
+        constexpr int n = (V - OFF) < 8 ? (V - OFF) : 8;
+        if constexpr (n <= 2) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                float x = v[OFF + i];
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 8 * i) {
+                    float *slot = grad_slot<ABSG>(OFF + i, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+                    if (slot) atomicAdd(slot, x);
+                }
+            }
+        } else {
+            __syncwarp();  // every lane has read the previous group
+#pragma unroll
+            for (int i = 0; i < n; ++i) s_red[i * 32 + lane] = v[OFF + i];
+            __syncwarp();
+            const int q = lane >> 2, c = lane & 3;
+            float t = 0.f;
+            if (q < n) {
+                const float4 a = *reinterpret_cast<const float4 *>(s_red + q * 32 + 8 * c);
+                const float4 b = *reinterpret_cast<const float4 *>(s_red + q * 32 + 8 * c + 4);
+                t = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+            }
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            if (c == 0 && q < n) {
+                float *slot = grad_slot<ABSG>(OFF + q, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+                if (slot) atomicAdd(slot, t);
+            }
+        }
+        reduce_smem<V, OFF + 8, ABSG>(v, s_red, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+    }
+}
+
 template <int TILE, int PPT, int CHC, bool ABSG>
 __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_kernel(
     const __grid_constant__ CamSet cs, RasterConsts rc, int ch, int batch, const int2 *__restrict__ ranges,
@@ -97,6 +153,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     float4 *s_h = s_g + batch;
     int4 *s_b = reinterpret_cast<int4 *>(s_h + batch);
     float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
+    float *s_red = reinterpret_cast<float *>(s_c + (size_t)batch * C4) + (threadIdx.x >> 5) * (8 * 32);
     __shared__ int s_max;
 
     __shared__ int s_next;
@@ -247,8 +304,12 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                     v[4] += 0.5f * dsig * dy * dy;
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
-                reduce_chunks<V, 0, ABSG>(v, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac, d_colors,
-                                          absgrad);
+                if constexpr (smem_reduce<PPT>())
+                    reduce_smem<V, 0, ABSG>(v, s_red, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
+                                            d_colors, absgrad);
+                else
+                    reduce_chunks<V, 0, ABSG>(v, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
+                                              d_colors, absgrad);
             }
         }
     }
@@ -257,9 +318,11 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     if (rc.work) finish_work(rc.work);
 }
 
-size_t raster_bwd_smem(int batch, int chc) {
+// staged batch (splat, box, colours) + (shared-memory reduction) one [8][32] float buffer per warp
+size_t raster_bwd_smem(int batch, int chc, int threads, bool reduce_buffers) {
     const int c4 = (chc + 3) / 4;
-    return (size_t)batch * (2 * sizeof(float4) + sizeof(int4) + c4 * sizeof(float4));
+    return (size_t)batch * (2 * sizeof(float4) + sizeof(int4) + c4 * sizeof(float4)) +
+           (reduce_buffers ? (size_t)(threads / 32) * 8 * 32 * sizeof(float) : 0);
 }
 
 template <int TILE, int PPT, int CHC, bool ABSG>
@@ -269,9 +332,9 @@ static cudaError_t launch_bwd_t(const CamSet &cs, const RasterConsts &rc, int ch
                                 const int *last_contrib, const float *d_image, const float *d_alpha,
                                 float *d_means2d, float *d_conics, float *d_opac, float *d_colors, float *absgrad,
                                 cudaStream_t st) {
-    const size_t smem = raster_bwd_smem(batch, CHC);
+    const size_t smem = raster_bwd_smem(batch, CHC, RasterShape<TILE, PPT>::kThreads, smem_reduce<PPT>());
     auto kern = raster_bwd_kernel<TILE, PPT, CHC, ABSG>;
-    if (smem > 48 * 1024) {
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
         cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -188,7 +188,7 @@ static cudaError_t launch_fwd_t(const CamSet &cs, const RasterConsts &rc, int ch
                                 cudaStream_t st) {
     const size_t smem = raster_fwd_smem(batch, CHC);
     auto kern = raster_fwd_kernel<TILE, PPT, CHC, COUNT>;
-    if (smem > 48 * 1024) {
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
         cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -112,23 +112,31 @@ __device__ __forceinline__ void sh_basis_vjp(const ShConsts &k, float x, float y
 // Copies the coefficient rows of Gaussians [n0, n0+cnt) into shared memory at row stride STRIDE.
 // NT threads each issue all their 16-byte loads before the first shared-memory store, so a
 // thread keeps up to ceil(NT F / 4 / NT) loads in flight instead of waiting on each in turn.
+// Rows whose flag in `ok` (shared memory, one per row) is zero are not read: their Gaussian is
+// culled in every camera, so neither its colour nor its gradient uses the coefficients.
 template <int F, int STRIDE, int NT>
-__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cnt, float *s, bool vec_ok) {
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cnt, float *s, bool vec_ok,
+                                           const unsigned char *ok) {
     const int total = cnt * F;
     if (vec_ok) {
         constexpr int V = (NT * F / 4 + NT - 1) / NT;  // float4 loads per thread for a full chunk
         const int nvec = total / 4;
         const float4 *src4 = reinterpret_cast<const float4 *>(src);
         float4 q[V];
+        unsigned take = 0u;  // bit j: load j is issued
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int v = threadIdx.x + j * NT;
-            if (v < nvec) q[j] = src4[v];
+            // a 16-byte load may straddle two rows when F is not a multiple of 4
+            if (v < nvec && (ok[(4 * v) / F] | ok[(4 * v + 3) / F])) {
+                q[j] = src4[v];
+                take |= 1u << j;
+            }
         }
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int v = threadIdx.x + j * NT;
-            if (v < nvec) {
+            if (take & (1u << j)) {
                 int e = 4 * v;
                 s[(e / F) * STRIDE + e % F] = q[j].x;
                 ++e;
@@ -139,9 +147,11 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cn
                 s[(e / F) * STRIDE + e % F] = q[j].w;
             }
         }
-        for (int e = nvec * 4 + threadIdx.x; e < total; e += NT) s[(e / F) * STRIDE + e % F] = src[e];
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += NT)
+            if (ok[e / F]) s[(e / F) * STRIDE + e % F] = src[e];
     } else {
-        for (int e = threadIdx.x; e < total; e += NT) s[(e / F) * STRIDE + e % F] = src[e];
+        for (int e = threadIdx.x; e < total; e += NT)
+            if (ok[e / F]) s[(e / F) * STRIDE + e % F] = src[e];
     }
 }
 
@@ -167,8 +177,15 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
         mz = means[3 * n + 2];
         r0 = radii[n];
     }
+    __shared__ unsigned char s_ok[256];
+    {
+        bool seen = r0 > 0;
+        for (int c = 1; c < cs.C && valid && !seen; ++c) seen = radii[(size_t)c * N + n] > 0;
+        s_ok[threadIdx.x] = seen;
+    }
+    __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    stage_rows<F, STRIDE, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
     __syncthreads();
     if (!valid) return;
     const float *cf = s_coef + threadIdx.x * STRIDE;
@@ -244,8 +261,15 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
         g0[2] = d_colors[IS * (size_t)n + 2];
         if (d_depths) g0[3] = d_colors[IS * (size_t)n + 3];
     }
+    __shared__ unsigned char s_ok[kShBwdThreads];
+    {
+        bool seen = r0 > 0;
+        for (int c = 1; c < cs.C && valid && !seen; ++c) seen = radii[(size_t)c * N + n] > 0;
+        s_ok[threadIdx.x] = seen;
+    }
+    __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
     float *gr = s_grad + threadIdx.x * STRIDE;
     if (!ONECAM) {
 #pragma unroll
@@ -356,7 +380,7 @@ static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, con
                                    float *colors, const float *depths, cudaStream_t st) {
     constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
     size_t smem = 256 * STRIDE * sizeof(float);
-    if (smem > 48 * 1024) {
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
         cudaError_t e = ensure_smem((const void *)sh_fwd_kernel<DEG>, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -373,7 +397,7 @@ static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, con
     const bool one = cs.C == 1;
     size_t smem = (one ? 1 : 2) * kShBwdThreads * STRIDE * sizeof(float);
     auto kern = one ? sh_bwd_kernel<DEG, true> : sh_bwd_kernel<DEG, false>;
-    if (smem > 48 * 1024) {
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
         cudaError_t e = ensure_smem((const void *)kern, (int)smem);
         if (e != cudaSuccess) return e;
     }
