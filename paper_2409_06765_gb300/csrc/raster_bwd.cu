@@ -57,8 +57,23 @@ __device__ __forceinline__ float *grad_slot(int idx, int id, int ch, float *d_me
     return q < ch ? d_colors + (size_t)id * ch + q : nullptr;
 }
 
+// Factor applied to the warp total of value `idx`: 1 / log2(e) for the mean (and absgrad)
+// terms when they are summed in units of log2(e) (SG).
+template <bool ABSG, bool SG>
+__device__ __forceinline__ float total_scale(int idx) {
+    return (SG && (idx < 2 || (ABSG && idx >= 6 && idx < 8))) ? kLn2 : 1.f;
+}
+
+// With the pre-scaled conic, the mean gradient of each pixel is either summed in units of
+// log2(e) and rescaled once on the warp totals (4 pixels per thread), or computed from the
+// conic recovered once per Gaussian (1 or 2 pixels per thread); each is the faster there.
+template <int PPT>
+__host__ __device__ constexpr bool scaled_grad() {
+    return GS_SCALED_CONIC && PPT >= 4;
+}
+
 // Reduces values [OFF, min(OFF + 32, V)) of v over the warp and adds them to global memory.
-template <int V, int OFF, bool ABSG>
+template <int V, int OFF, bool ABSG, bool SG>
 __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int id, int ch, float *d_means2d,
                                               float *d_conics, float *d_opac, float *d_colors, float *absgrad) {
     if constexpr (OFF < V) {
@@ -72,9 +87,9 @@ __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int
         const int idx = lane / group;
         if ((lane % group) == 0 && idx < n) {
             float *slot = grad_slot<ABSG>(OFF + idx, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
-            if (slot) atomicAdd(slot, tot);
+            if (slot) atomicAdd(slot, tot * total_scale<ABSG, SG>(OFF + idx));
         }
-        reduce_chunks<V, OFF + 32, ABSG>(v, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+        reduce_chunks<V, OFF + 32, ABSG, SG>(v, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
     }
 }
 
@@ -94,7 +109,7 @@ __host__ __device__ constexpr bool smem_reduce() {
 // lanes 8 (l % 4) .. 8 (l % 4) + 7 with two 16-byte loads and finishes with two shuffles, so a
 // group costs 8 stores, 2 loads, 2 shuffles and 9 adds per lane instead of a shuffle butterfly
 // with a select per value and step.  A group of at most two values uses plain butterflies.
-template <int V, int OFF, bool ABSG>
+template <int V, int OFF, bool ABSG, bool SG>
 __device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, int lane, int id, int ch,
                                             float *d_means2d, float *d_conics, float *d_opac, float *d_colors,
                                             float *absgrad) {
@@ -108,7 +123,7 @@ __device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, i
                 for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 if (lane == 8 * i) {
                     float *slot = grad_slot<ABSG>(OFF + i, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
-                    if (slot) atomicAdd(slot, x);
+                    if (slot) atomicAdd(slot, x * total_scale<ABSG, SG>(OFF + i));
                 }
             }
         } else {
@@ -127,10 +142,10 @@ __device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, i
             t += __shfl_xor_sync(0xffffffffu, t, 2);
             if (c == 0 && q < n) {
                 float *slot = grad_slot<ABSG>(OFF + q, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
-                if (slot) atomicAdd(slot, t);
+                if (slot) atomicAdd(slot, t * total_scale<ABSG, SG>(OFF + q));
             }
         }
-        reduce_smem<V, OFF + 8, ABSG>(v, s_red, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+        reduce_smem<V, OFF + 8, ABSG, SG>(v, s_red, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
     }
 }
 
@@ -148,6 +163,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     constexpr int C4 = (CHC + 3) / 4;
     constexpr int NA = ABSG ? 2 : 0;
     constexpr int V = 6 + NA + CHC;
+    constexpr bool SG = scaled_grad<PPT>();
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *s_g = reinterpret_cast<float4 *>(smem);
     float4 *s_h = s_g + batch;
@@ -250,6 +266,15 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 const float4 hh4 = s_h[j];
                 const bool inx = (unsigned)(px - bx.x) <= (unsigned)bx.y;
                 const float dx = fx - gg.x;
+                // per Gaussian: the mean gradient of a pixel is dsig (+-) (Bx + Mx dy, By + My dy)
+#if GS_SCALED_CONIC
+                const float Mx = SG ? gg.w : gg.w * -kLn2;
+                const float My = SG ? 2.f * hh4.x : hh4.x * (-2.f * kLn2);
+                const float Bx = SG ? 2.f * gg.z * dx : gg.z * (-2.f * kLn2) * dx;
+                const float By = Mx * dx;
+#else
+                const float Mx = gg.w, My = hh4.x, Bx = gg.z * dx, By = gg.w * dx;
+#endif
                 float v[V];
 #pragma unroll
                 for (int i = 0; i < V; ++i) v[i] = 0.f;
@@ -261,11 +286,18 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 for (int k = 0; k < PPT; ++k) {
                     const bool act = rel < last[k] && inx && (unsigned)(py0 + k - bx.z) <= (unsigned)bx.w;
                     const float dy = ((float)(py0 + k) + 0.5f) - gg.y;
+#if GS_SCALED_CONIC
+                    const float pe = gauss_exponent(dx, dy, gg.z, gg.w, hh4.x);  // -log2(e) sigma
+                    const float e = ex2_approx(pe);
+                    const bool neg = pe > 0.f;  // sigma < 0
+#else
                     const float sigma = mahalanobis_half(dx, dy, gg.z, gg.w, hh4.x);
                     const float e = gauss_weight(sigma);
+                    const bool neg = sigma < 0.f;
+#endif
                     const float oe = __fmul_rn(hh4.y, e);
                     const float alpha = fminf(amax, oe);
-                    const bool take = act && !(sigma < 0.f) && !(alpha < amin);
+                    const bool take = act && !neg && !(alpha < amin);
                     any = any || take;
                     const float ra = rcp_approx(1.f - alpha);
                     const float Tn = T[k] * ra;  // transmittance in front of this Gaussian
@@ -291,8 +323,11 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                     v[5] += e * dalpha;
                     const float dsig = -oe * dalpha;
                     // d sigma / d mu' = -conic D
-                    const float gx = -dsig * (gg.z * dx + gg.w * dy);
-                    const float gy = -dsig * (gg.w * dx + hh4.x * dy);
+                    // (with SG: -conic D = (2 a' dx + b' dy, b' dx + 2 c' dy) / log2(e) for the staged
+                    // (a', b', c'), and the 1 / log2(e) is applied to the warp totals)
+                    const float sd = SG ? dsig : -dsig;
+                    const float gx = sd * (Mx * dy + Bx);
+                    const float gy = sd * (My * dy + By);
                     v[0] += gx;
                     v[1] += gy;
                     if (ABSG) {
@@ -305,11 +340,11 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 if constexpr (smem_reduce<PPT>())
-                    reduce_smem<V, 0, ABSG>(v, s_red, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
-                                            d_colors, absgrad);
+                    reduce_smem<V, 0, ABSG, SG>(v, s_red, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics,
+                                                d_opac, d_colors, absgrad);
                 else
-                    reduce_chunks<V, 0, ABSG>(v, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
-                                              d_colors, absgrad);
+                    reduce_chunks<V, 0, ABSG, SG>(v, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
+                                                  d_colors, absgrad);
             }
         }
     }
