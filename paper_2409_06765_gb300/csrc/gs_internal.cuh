@@ -153,36 +153,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// sigma = 1/2 D^T conic D for conic [[a,b],[b,c]], written with explicit roundings so the
-// forward and the backward kernels obtain bit-identical values.
-__device__ __forceinline__ float mahalanobis_half(float dx, float dy, float ca, float cb, float cc) {
-    float xx = __fmul_rn(dx, dx);
-    float yy = __fmul_rn(dy, dy);
-    float xy = __fmul_rn(dx, dy);
-    float s = __fmaf_rn(ca, xx, __fmul_rn(cc, yy));
-    return __fmaf_rn(0.5f, s, __fmul_rn(cb, xy));
-}
-
-// exp(-sigma) = 2^(-sigma log2 e)
-__device__ __forceinline__ float gauss_weight(float sigma) {
-    return ex2_approx(__fmul_rn(-1.4426950408889634f, sigma));
-}
-
-#ifndef GS_SCALED_CONIC
-#define GS_SCALED_CONIC 1
-#endif
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
-// With GS_SCALED_CONIC the compositing kernels stage the conic pre-scaled,
+// The compositing kernels stage the conic pre-scaled,
 // (a', b', c') = -log2(e) (a / 2, b, c / 2), so that the exponent of the Gaussian weight,
 // p = -log2(e) sigma = a' dx^2 + b' dx dy + c' dy^2, and exp(-sigma) = 2^p cost two
 // multiplications less per pixel; explicit roundings keep forward and backward bit-identical.
-__device__ __forceinline__ float gauss_exponent(float dx, float dy, float a, float b, float c) {
-    const float xx = __fmul_rn(dx, dx);
-    const float yy = __fmul_rn(dy, dy);
-    const float xy = __fmul_rn(dx, dy);
+__device__ __forceinline__ float gauss_exponent_parts(float xx, float yy, float xy, float a, float b, float c) {
     return __fmaf_rn(a, xx, __fmaf_rn(c, yy, __fmul_rn(b, xy)));
+}
+__device__ __forceinline__ float gauss_exponent(float dx, float dy, float a, float b, float c) {
+    return gauss_exponent_parts(__fmul_rn(dx, dx), __fmul_rn(dy, dy), __fmul_rn(dx, dy), a, b, c);
 }
 
 // Launch shape of the compositing kernels: PPT pixels per thread stacked along y, so a
@@ -233,13 +215,8 @@ __device__ __forceinline__ void stage_splat(int id, const float2 *__restrict__ m
     support_span(m.y, r, y0, y1);
     const float o = opac[id];
     const float cut = !(o >= alpha_min) ? -1.f : (alpha_min > 0.f ? __logf(o / alpha_min) : 3.0e38f);
-#if GS_SCALED_CONIC
     g = make_float4(m.x, m.y, -0.5f * kLog2e * conics[3 * id], -kLog2e * conics[3 * id + 1]);
     h = make_float4(-0.5f * kLog2e * conics[3 * id + 2], o, cut, __int_as_float(id));
-#else
-    g = make_float4(m.x, m.y, conics[3 * id], conics[3 * id + 1]);
-    h = make_float4(conics[3 * id + 2], o, cut, __int_as_float(id));
-#endif
     box = make_int4(x0, x1 - x0, y0, y1 - y0);
 }
 
@@ -258,11 +235,7 @@ __device__ __forceinline__ bool may_blend(const float4 &g, const float4 &h, cons
     // minimum of sigma(p) = 1/2 (p-m)^T [[a,b],[b,c]] (p-m) over the rectangle of pixel centres
     const float x0 = (float)rx0 + 0.5f - g.x, x1 = (float)rx1 + 0.5f - g.x;
     const float y0 = (float)ry0 + 0.5f - g.y, y1 = (float)ry1 + 0.5f - g.y;
-#if GS_SCALED_CONIC  // back to the conic (the margin below dwarfs the rounding of the round trip)
     const float a = g.z * (-2.f * kLn2), bb = g.w * (-kLn2), c = h.x * (-2.f * kLn2);
-#else
-    const float a = g.z, bb = g.w, c = h.x;
-#endif
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
     const float ia = 1.f / a, ic = 1.f / c;
     float best = 3.0e38f;

@@ -61,6 +61,7 @@ __device__ __forceinline__ float *grad_slot(int idx, int id, int ch, float *d_me
 // terms when they are summed in units of log2(e) (SG).
 template <bool ABSG, bool SG>
 __device__ __forceinline__ float total_scale(int idx) {
+    if (idx == 2 || idx == 4) return 0.5f;  // dsig dx^2 and dsig dy^2 are summed unhalved
     return (SG && (idx < 2 || (ABSG && idx >= 6 && idx < 8))) ? kLn2 : 1.f;
 }
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ float total_scale(int idx) {
 // conic recovered once per Gaussian (1 or 2 pixels per thread); each is the faster there.
 template <int PPT>
 __host__ __device__ constexpr bool scaled_grad() {
-    return GS_SCALED_CONIC && PPT >= 4;
+    return PPT >= 4;
 }
 
 // Reduces values [OFF, min(OFF + 32, V)) of v over the warp and adds them to global memory.
@@ -266,15 +267,12 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 const float4 hh4 = s_h[j];
                 const bool inx = (unsigned)(px - bx.x) <= (unsigned)bx.y;
                 const float dx = fx - gg.x;
+                const float xx = __fmul_rn(dx, dx);
                 // per Gaussian: the mean gradient of a pixel is dsig (+-) (Bx + Mx dy, By + My dy)
-#if GS_SCALED_CONIC
                 const float Mx = SG ? gg.w : gg.w * -kLn2;
                 const float My = SG ? 2.f * hh4.x : hh4.x * (-2.f * kLn2);
                 const float Bx = SG ? 2.f * gg.z * dx : gg.z * (-2.f * kLn2) * dx;
                 const float By = Mx * dx;
-#else
-                const float Mx = gg.w, My = hh4.x, Bx = gg.z * dx, By = gg.w * dx;
-#endif
                 float v[V];
 #pragma unroll
                 for (int i = 0; i < V; ++i) v[i] = 0.f;
@@ -286,15 +284,10 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 for (int k = 0; k < PPT; ++k) {
                     const bool act = rel < last[k] && inx && (unsigned)(py0 + k - bx.z) <= (unsigned)bx.w;
                     const float dy = ((float)(py0 + k) + 0.5f) - gg.y;
-#if GS_SCALED_CONIC
-                    const float pe = gauss_exponent(dx, dy, gg.z, gg.w, hh4.x);  // -log2(e) sigma
+                    const float yy = __fmul_rn(dy, dy), xy = __fmul_rn(dx, dy);
+                    const float pe = gauss_exponent_parts(xx, yy, xy, gg.z, gg.w, hh4.x);  // -log2(e) sigma
                     const float e = ex2_approx(pe);
                     const bool neg = pe > 0.f;  // sigma < 0
-#else
-                    const float sigma = mahalanobis_half(dx, dy, gg.z, gg.w, hh4.x);
-                    const float e = gauss_weight(sigma);
-                    const bool neg = sigma < 0.f;
-#endif
                     const float oe = __fmul_rn(hh4.y, e);
                     const float alpha = fminf(amax, oe);
                     const bool take = act && !neg && !(alpha < amin);
@@ -334,9 +327,10 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                         v[6] += fabsf(gx);
                         v[7] += fabsf(gy);
                     }
-                    v[2] += 0.5f * dsig * dx * dx;
-                    v[3] += dsig * dx * dy;
-                    v[4] += 0.5f * dsig * dy * dy;
+                    // d sigma / d conic = (dx^2 / 2, dx dy, dy^2 / 2): the halves are applied to the warp totals
+                    v[2] += dsig * xx;
+                    v[3] += dsig * xy;
+                    v[4] += dsig * yy;
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 if constexpr (smem_reduce<PPT>())

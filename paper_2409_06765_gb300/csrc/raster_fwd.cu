@@ -128,18 +128,12 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
                         const bool act = !done[k] && inx && (unsigned)(py0 + k - b.z) <= (unsigned)b.w;
                         if (COUNT) blends += act ? 1 : 0;
                         const float dy = ((float)(py0 + k) + 0.5f) - g.y;
-#if GS_SCALED_CONIC
                         const float pe = gauss_exponent(dx, dy, g.z, g.w, h.x);  // -log2(e) sigma
                         const float e = ex2_approx(pe);
                         const bool neg = pe > 0.f;  // sigma < 0
-#else
-                        const float sigma = mahalanobis_half(dx, dy, g.z, g.w, h.x);
-                        const float e = gauss_weight(sigma);
-                        const bool neg = sigma < 0.f;
-#endif
                         const float alpha = fminf(amax, __fmul_rn(h.y, e));
                         const bool blend = act && !neg && !(alpha < amin);
-                        const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                        const float Tn = __fmaf_rn(-T[k], alpha, T[k]);  // T (1 - alpha)
                         const bool stop = blend && Tn < tmin;
                         const bool take = blend && !stop;
                         const float w = take ? __fmul_rn(alpha, T[k]) : 0.f;
