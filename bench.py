@@ -307,15 +307,16 @@ def run_ours(args):
         def e2e_step():
             # one training step through the public API: target in, forward, L1 loss, backward,
             # loss out; gradients start from None as after optimizer.zero_grad(set_to_none=True).
-            # The target's copy runs on a copy stream while the forward renders; the loss waits for it.
+            # The forward is queued first; the target's copy then runs on a copy stream while the
+            # forward renders, and the loss waits for it.
             for _ in range(3):
                 for x in leaves:
                     x.grad = None
-                with torch.cuda.stream(copy_stream):
-                    dev_target.copy_(host_target, non_blocking=True)
-                    copied.record(copy_stream)
                 imgs, alphas, _ = raster.rasterization(*leaves, cameras=cam_arr, settings=settings, state=state,
                                                        defer_sync=True)
+                with torch.cuda.stream(copy_stream):  # (the previous step's loss.item() has synchronised)
+                    dev_target.copy_(host_target, non_blocking=True)
+                    copied.record(copy_stream)
                 torch.cuda.current_stream().wait_event(copied)
                 loss = (imgs[0].reshape(-1, 3) - dev_target).abs().mean()
                 loss.backward()
