@@ -440,6 +440,12 @@ def measure_alu_peaks(torch, _lib, sm_count):
 
 
 STAGES = ("project", "sh", "bin_sort", "rasterize_fwd", "rasterize_bwd", "sh_bwd", "project_bwd")
+STAGES_FUSED = ("project", "sh", "bin_sort", "rasterize_fwd", "rasterize_bwd", "sh_project_bwd")
+
+
+def stages_of(kp):
+    """The stages of a pipeline: one camera runs the SH and projection backward as one kernel."""
+    return STAGES_FUSED if getattr(kp, "fused_bwd", False) else STAGES
 
 
 def stage_breakdown(kp, steps):
@@ -462,7 +468,9 @@ def stage_breakdown(kp, steps):
         "project_bwd": lambda: L.gs_project_bwd(kp.cams, sc.means, sc.quats, sc.log_scales, sc.opacity_logits,
                                                 kp.params, kp.radii, kp.d_means2d, kp.d_conics, kp.d_opac, None,
                                                 kp.d_means, kp.d_quats, kp.d_log_scales, kp.d_logits),
+        "sh_project_bwd": kp._post,
     }
+    STAGES = stages_of(kp)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -513,13 +521,16 @@ def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
         "sh_bwd": CN * 16 + vis * (12 + ncoef * 4) + N * (ncoef * 4 + 12),
         # parameters + d_means in, 2D gradients + radius per pair in; d_quats, d_log_scales, d_logits, d_means out
         "project_bwd": N * (44 + 12) + CN * 28 + N * 44,
+        # one kernel for both (one camera): parameters once, radius, d_colors and 2D gradients of the pair,
+        # visible coefficients in; d_sh, d_means, d_quats, d_log_scales, d_logits out
+        "sh_project_bwd": N * 44 + CN * 40 + vis * ncoef * 4 + N * (ncoef * 4 + 44),
     }
     out = {k: {"bound": "hbm", "bytes": int(v), "bound_ms": v / hbm_bps * 1000.0} for k, v in byt.items()}
     out["rasterize_fwd"] = {"bound": "alu", "ops": blends * FWD_OPS_PER_BLEND,
                             "bound_ms": blends * FWD_OPS_PER_BLEND / alu_ops * 1000.0}
     out["rasterize_bwd"] = {"bound": "alu", "ops": blends * BWD_OPS_PER_BLEND,
                             "bound_ms": blends * BWD_OPS_PER_BLEND / alu_ops * 1000.0}
-    return {k: out[k] for k in STAGES}
+    return {k: out[k] for k in stages_of(kp)}
 
 
 # ------------------------------------------------------------------------------------------

@@ -347,6 +347,25 @@ GS_API gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, con
                          float *d_log_scales, float *d_opacity_logits, float *d_viewmats,
                                 void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* gs_sh_project_bwd -- gs_sh_eval_bwd followed by gs_project_bwd for ONE     */
+/* camera (C == 1), without depth or pose gradients, in one kernel: the same  */
+/* chain rule (App. C.1 differentiated; App. D.2-D.4), each Gaussian's        */
+/* parameters, radius and mean read once, and d_means written once.           */
+/* in : sh [N,K,3], means [N,3], quats [N,4] (16-byte aligned), log_scales    */
+/*      [N,3], opacity_logits [N], radii [N], d_colors [N,3], d_means2d [N,2] */
+/*      (8-byte aligned), d_conics [N,3], d_opacities [N]                     */
+/* out: d_sh [N,K,3], d_means [N,3], d_quats [N,4] (16-byte aligned),        */
+/*      d_log_scales [N,3], d_opacity_logits [N], all OVERWRITTEN (zeros for  */
+/*      Gaussians the camera culls).  GS_ERR_ARG when C != 1.                 */
+/* ------------------------------------------------------------------------ */
+GS_API gs_status gs_sh_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                                   int32_t sh_degree, const float *sh, const float *means, const float *quats,
+                                   const float *log_scales, const float *opacity_logits, const int32_t *radii,
+                                   const float *d_colors, const float *d_means2d, const float *d_conics,
+                                   const float *d_opacities, float *d_sh, float *d_means, float *d_quats,
+                                   float *d_log_scales, float *d_opacity_logits, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

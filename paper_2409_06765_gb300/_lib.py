@@ -29,6 +29,7 @@ EXPORTED = (
     "gs_sh_eval", "gs_tile_bin_sort_workspace", "gs_tile_bin_sort", "gs_rasterize_fwd", "gs_rasterize_bwd",
     "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc", "gs_probe_peak",
     "gs_tile_order", "gs_sh_eval_depth", "gs_sh_eval_depth_bwd", "gs_expected_depth", "gs_expected_depth_bwd",
+    "gs_sh_project_bwd",
 )
 GS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_sh_eval_bwd": (_I32, [_CAM, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
             "gs_project_bwd": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                       _P, _P]),
+            "gs_sh_project_bwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32] + [_P] * 15 + [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -368,6 +370,22 @@ def gs_sh_eval_bwd(cams: CameraArray, sh_degree: int, sh, means, radii, d_colors
                                _dev(d_sh, "f32", "d_sh"), _dev(d_means, "f32", "d_means"),
                                _dev(d_viewmats, "f32", "d_viewmats", optional=True), _stream(stream))
     _check(st, "gs_sh_eval_bwd")
+
+
+def gs_sh_project_bwd(cams: CameraArray, params: GsParams, sh_degree: int, sh, means, quats, log_scales,
+                      opacity_logits, radii, d_colors, d_means2d, d_conics, d_opacities, d_sh, d_means, d_quats,
+                      d_log_scales, d_opacity_logits, stream=None):
+    N = means.shape[0]
+    st = load().gs_sh_project_bwd(cams.ptr, cams.C, N, ctypes.byref(params), sh_degree, _dev(sh, "f32", "sh"),
+                                  _dev(means, "f32", "means"), _dev(quats, "f32", "quats"),
+                                  _dev(log_scales, "f32", "log_scales"),
+                                  _dev(opacity_logits, "f32", "opacity_logits"), _dev(radii, "i32", "radii"),
+                                  _dev(d_colors, "f32", "d_colors"), _dev(d_means2d, "f32", "d_means2d"),
+                                  _dev(d_conics, "f32", "d_conics"), _dev(d_opacities, "f32", "d_opacities"),
+                                  _dev(d_sh, "f32", "d_sh"), _dev(d_means, "f32", "d_means"),
+                                  _dev(d_quats, "f32", "d_quats"), _dev(d_log_scales, "f32", "d_log_scales"),
+                                  _dev(d_opacity_logits, "f32", "d_opacity_logits"), _stream(stream))
+    _check(st, "gs_sh_project_bwd")
 
 
 def gs_project_bwd(cams: CameraArray, means, quats, log_scales, opacity_logits, params: GsParams, radii, d_means2d,

@@ -17,6 +17,10 @@ cudaError_t launch_project_bwd(const CamSet &, const RasterConsts &, int, const 
                                float *, float *, float *, float *, float *, cudaStream_t);
 cudaError_t launch_sh_fwd(const CamSet &, int, int, const float *, const float *, const int *, float *, const float *,
                           cudaStream_t);
+cudaError_t launch_sh_project_bwd(const CamSet &, const RasterConsts &, int, int, const float *, const float *,
+                                  const float *, const float *, const float *, const int *, const float *,
+                                  const float *, const float *, const float *, float *, float *, float *, float *,
+                                  float *, cudaStream_t);
 cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *, const int *, const float *, float *,
                           float *, float *, float *, cudaStream_t);
 cudaError_t launch_expected_depth(long long, const float *, int, int, const float *, float *, cudaStream_t);
@@ -515,6 +519,33 @@ gs_status gs_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const floa
                                        d_opacities, d_depths, d_means, d_quats, d_log_scales, d_opacity_logits,
                                        d_viewmats, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project_bwd");
+}
+
+gs_status gs_sh_project_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params, int32_t sh_degree,
+                            const float *sh, const float *means, const float *quats, const float *log_scales,
+                            const float *opacity_logits, const int32_t *radii, const float *d_colors,
+                            const float *d_means2d, const float *d_conics, const float *d_opacities, float *d_sh,
+                            float *d_means, float *d_quats, float *d_log_scales, float *d_opacity_logits,
+                            void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (C != 1) return fail_arg("gs_sh_project_bwd takes one camera (use gs_sh_eval_bwd + gs_project_bwd)");
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(quats); GS_NONNULL(log_scales); GS_NONNULL(opacity_logits);
+    GS_NONNULL(radii); GS_NONNULL(d_colors); GS_NONNULL(d_means2d); GS_NONNULL(d_conics); GS_NONNULL(d_opacities);
+    GS_NONNULL(d_sh); GS_NONNULL(d_means); GS_NONNULL(d_quats); GS_NONNULL(d_log_scales);
+    GS_NONNULL(d_opacity_logits);
+    if (!aligned(quats, 16) || !aligned(d_quats, 16)) return fail_arg("quats/d_quats must be 16-byte aligned");
+    if (!aligned(d_means2d, 8)) return fail_arg("d_means2d must be 8-byte aligned");
+    cudaError_t e = launch_sh_project_bwd(cs, rc, sh_degree, N, sh, means, quats, log_scales, opacity_logits, radii,
+                                          d_colors, d_means2d, d_conics, d_opacities, d_sh, d_means, d_quats,
+                                          d_log_scales, d_opacity_logits, (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_sh_project_bwd");
 }
 
 }  // extern "C"

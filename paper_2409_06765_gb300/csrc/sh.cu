@@ -5,7 +5,7 @@
 // row), and every thread loops over the cameras of the call.
 #include <math.h>
 
-#include "gs_internal.cuh"
+#include "project_math.cuh"
 
 namespace gs {
 
@@ -228,6 +228,10 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
 // same contiguous copy as the coefficients came in.
 constexpr int kShBwdThreads = 128;
 
+#ifndef GS_SH_PROJECT_BWD_MIN_BLOCKS
+#define GS_SH_PROJECT_BWD_MIN_BLOCKS 5  // 96 registers, no spills: five 128-thread CTAs per SM
+#endif
+
 // ONECAM (a single camera): the gradient row of each Gaussian is written in place over its
 // staged coefficient row once the row has been used, so a CTA needs half the shared memory
 // and twice as many CTAs fit on an SM.
@@ -375,6 +379,150 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
     }
 }
 
+// SH backward and projection backward of one camera in one kernel: the coefficient rows
+// stream through shared memory as in sh_bwd_kernel (gradient rows written in place), and
+// each thread then runs the projection chain of its Gaussian (App. D.2-D.4) with the
+// colour-path mean gradient still in registers, so d_means is written once and the
+// Gaussian's parameters, radius and mean are read once for both.  Every per-Gaussian input
+// of a visible Gaussian is requested before the coefficient rows.
+template <int DEG>
+__global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) sh_project_bwd_kernel(
+    int N, const float *__restrict__ sh, const float *__restrict__ means, const float4 *__restrict__ quats,
+    const float *__restrict__ log_scales, const float *__restrict__ logits, const int *__restrict__ radii,
+    const __grid_constant__ CamSet cs, ShConsts kc, RasterConsts rc, const float *__restrict__ d_colors,
+    const float2 *__restrict__ d_means2d, const float *__restrict__ d_conics, const float *__restrict__ d_opac,
+    float *__restrict__ d_sh, float *__restrict__ d_means, float4 *__restrict__ d_quats,
+    float *__restrict__ d_log_scales, float *__restrict__ d_logits) {
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    extern __shared__ float s_coef[];
+    __shared__ unsigned char s_ok[kShBwdThreads];
+    const int n0 = blockIdx.x * kShBwdThreads;
+    const int cnt = min(kShBwdThreads, N - n0);
+    const int n = n0 + threadIdx.x;
+    const bool valid = n < N;
+    const int r0 = valid ? radii[n] : 0;
+    const bool vis = r0 > 0;
+    float mean[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        mean[0] = means[3 * n];
+        mean[1] = means[3 * n + 1];
+        mean[2] = means[3 * n + 2];
+    }
+    float g0[3] = {0.f, 0.f, 0.f};
+    float2 gm = make_float2(0.f, 0.f);
+    float ga = 0.f, gb = 0.f, gc = 0.f, gop = 0.f;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+    float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, lg = 0.f;
+    if (vis) {
+        g0[0] = d_colors[3 * (size_t)n];
+        g0[1] = d_colors[3 * (size_t)n + 1];
+        g0[2] = d_colors[3 * (size_t)n + 2];
+        gm = d_means2d[n];
+        ga = d_conics[3 * (size_t)n];
+        gb = d_conics[3 * (size_t)n + 1];
+        gc = d_conics[3 * (size_t)n + 2];
+        gop = d_opac[n];
+        q = quats[n];
+        ls0 = log_scales[3 * (size_t)n];
+        ls1 = log_scales[3 * (size_t)n + 1];
+        ls2 = log_scales[3 * (size_t)n + 2];
+        lg = logits[n];
+    }
+    s_ok[threadIdx.x] = vis;
+    __syncthreads();
+    const float *src = sh + (size_t)n0 * F;
+    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    __syncthreads();
+    float *row = s_coef + threadIdx.x * STRIDE;  // coefficients, then (in place) their gradient
+    const CamDev &cam = cs.cam[0];
+    float dm[3] = {0.f, 0.f, 0.f};
+    if (vis) {
+        const float *R = cam.R, *t = cam.t;
+        const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+        const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+        const float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+        const float vx = mean[0] - ox, vy = mean[1] - oy, vz = mean[2] - oz;
+        const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float x = vx * il, y = vy * il, z = vz * il;
+        float Y[K];
+        sh_eval_basis<DEG>(kc, x, y, z, Y);
+        float g[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) raw += Y[k] * row[3 * k + ch];
+            g[ch] = raw > 0.f ? g0[ch] : 0.f;  // the clamp at 0 passes no gradient
+        }
+        float w[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = row[3 * k] * g[0] + row[3 * k + 1] * g[1] + row[3 * k + 2] * g[2];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {  // (in place: every read of the row is above)
+            row[3 * k] = Y[k] * g[0];
+            row[3 * k + 1] = Y[k] * g[1];
+            row[3 * k + 2] = Y[k] * g[2];
+        }
+        if (DEG > 0) {
+            float dd[3] = {0.f, 0.f, 0.f};
+            sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
+            const float p = x * dd[0] + y * dd[1] + z * dd[2];
+            dm[0] = (dd[0] - x * p) * il;
+            dm[1] = (dd[1] - y * p) * il;
+            dm[2] = (dd[2] - z * p) * il;
+        }
+    } else if (valid) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) row[f] = 0.f;
+    }
+    if (valid) {
+        float dls[3] = {0.f, 0.f, 0.f}, dl = 0.f;
+        float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vis) {
+            Gauss3 gs3;
+            gauss_from(q, ls0, ls1, ls2, lg, gs3);
+            Splat2 sp;
+            float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, d_o = 0.f, pose[12];
+            if (splat_of(gs3, mean, cam, rc, sp))
+                splat_bwd<false>(gs3, mean, cam, rc, sp, gm, ga, gb, gc, gop, 0.f, dmu, dSig, d_o, pose);
+            dm[0] += dmu[0];
+            dm[1] += dmu[1];
+            dm[2] += dmu[2];
+            gauss_bwd(gs3, dSig, d_o, dls, dq, dl);
+        }
+        d_means[3 * n] = dm[0];
+        d_means[3 * n + 1] = dm[1];
+        d_means[3 * n + 2] = dm[2];
+        d_quats[n] = dq;
+        d_log_scales[3 * n] = dls[0];
+        d_log_scales[3 * n + 1] = dls[1];
+        d_log_scales[3 * n + 2] = dls[2];
+        d_logits[n] = dl;
+    }
+    __syncthreads();
+    float *dst = d_sh + (size_t)n0 * F;
+    const int total = cnt * F;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        const int nvec = total / 4;
+        float4 *dst4 = reinterpret_cast<float4 *>(dst);
+        for (int v = threadIdx.x; v < nvec; v += kShBwdThreads) {
+            int e = 4 * v;
+            float4 o;
+            o.x = s_coef[(e / F) * STRIDE + e % F];
+            ++e;
+            o.y = s_coef[(e / F) * STRIDE + e % F];
+            ++e;
+            o.z = s_coef[(e / F) * STRIDE + e % F];
+            ++e;
+            o.w = s_coef[(e / F) * STRIDE + e % F];
+            dst4[v] = o;
+        }
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_coef[(e / F) * STRIDE + e % F];
+    } else {
+        for (int e = threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_coef[(e / F) * STRIDE + e % F];
+    }
+}
+
 template <int DEG>
 static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
                                    float *colors, const float *depths, cudaStream_t st) {
@@ -426,6 +574,45 @@ cudaError_t launch_sh_bwd(const CamSet &cs, int deg, int N, const float *sh, con
         case 2: return launch_sh_bwd_t<2>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
         default: return launch_sh_bwd_t<3>(cs, N, sh, means, radii, d_colors, d_sh, d_means, d_depths, d_viewmats, st);
     }
+}
+
+template <int DEG>
+static cudaError_t launch_sh_project_bwd_t(const CamSet &cs, const RasterConsts &rc, int N, const float *sh,
+                                           const float *means, const float *quats, const float *log_scales,
+                                           const float *logits, const int *radii, const float *d_colors,
+                                           const float *d_means2d, const float *d_conics, const float *d_opac,
+                                           float *d_sh, float *d_means, float *d_quats, float *d_log_scales,
+                                           float *d_logits, cudaStream_t st) {
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    const size_t smem = kShBwdThreads * STRIDE * sizeof(float);
+    auto kern = sh_project_bwd_kernel<DEG>;
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+        cudaError_t e = ensure_smem((const void *)kern, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(N + kShBwdThreads - 1) / kShBwdThreads, kShBwdThreads, smem, st>>>(
+        N, sh, means, (const float4 *)quats, log_scales, logits, radii, cs, make_sh_consts(), rc, d_colors,
+        (const float2 *)d_means2d, d_conics, d_opac, d_sh, d_means, (float4 *)d_quats, d_log_scales, d_logits);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sh_project_bwd(const CamSet &cs, const RasterConsts &rc, int deg, int N, const float *sh,
+                                  const float *means, const float *quats, const float *log_scales,
+                                  const float *logits, const int *radii, const float *d_colors,
+                                  const float *d_means2d, const float *d_conics, const float *d_opac, float *d_sh,
+                                  float *d_means, float *d_quats, float *d_log_scales, float *d_logits,
+                                  cudaStream_t st) {
+#define GS_SPB(D)                                                                                                \
+    return launch_sh_project_bwd_t<D>(cs, rc, N, sh, means, quats, log_scales, logits, radii, d_colors, d_means2d, \
+                                      d_conics, d_opac, d_sh, d_means, d_quats, d_log_scales, d_logits, st)
+    switch (deg) {
+        case 0: GS_SPB(0);
+        case 1: GS_SPB(1);
+        case 2: GS_SPB(2);
+        default: GS_SPB(3);
+    }
+#undef GS_SPB
 }
 
 }  // namespace gs

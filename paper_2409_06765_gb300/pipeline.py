@@ -37,6 +37,7 @@ class Schedule:
     bwd_pixels_per_thread: int = 0
     persistent: bool = False      # forward compositing as one persistent launch (needs tile_order)
     bwd_persistent: bool = False  # backward likewise
+    fused_bwd: bool = True        # one camera: SH and projection backward as one kernel
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
@@ -51,7 +52,8 @@ class Schedule:
         return dict(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
                     bwd_batch_depth=self.bwd_batch_depth or self.batch_depth,
                     bwd_pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread,
-                    tile_order=self.tile_order, persistent=self.persistent, bwd_persistent=self.bwd_persistent)
+                    tile_order=self.tile_order, persistent=self.persistent, bwd_persistent=self.bwd_persistent,
+                    fused_bwd=self.fused_bwd)
 
 
 class DeviceScene:
@@ -187,8 +189,17 @@ class FramePipeline:
                               self.conics, self.opac, self.colors, None, self.final_T, self.last, self.d_image, None,
                               self.d_means2d, self.d_conics, self.d_opac, self.d_colors, None, tile_order=self.order)
 
+    @property
+    def fused_bwd(self) -> bool:
+        return self.C == 1 and self.schedule.fused_bwd
+
     def _post(self):
         s, L = self.scene, _lib
+        if self.fused_bwd:
+            L.gs_sh_project_bwd(self.cams, self.params, s.sh_degree, s.sh, s.means, s.quats, s.log_scales,
+                                s.opacity_logits, self.radii, self.d_colors, self.d_means2d, self.d_conics, self.d_opac,
+                                self.d_sh, self.d_means, self.d_quats, self.d_log_scales, self.d_logits)
+            return
         L.gs_sh_eval_bwd(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.d_colors, self.d_sh, self.d_means)
         L.gs_project_bwd(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.radii,
                          self.d_means2d, self.d_conics, self.d_opac, None, self.d_means, self.d_quats,

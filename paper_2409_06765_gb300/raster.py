@@ -284,6 +284,15 @@ class RasterizeGaussians(torch.autograd.Function):
         d_depths = None
         want_pose = ctx.viewmats_like is not None and ctx.needs_input_grad[10]
         d_view = torch.zeros(C, 4, 4, device=dev) if want_pose else None
+        if ctx.use_sh and C == 1 and not ctx.depth and d_view is None:
+            # one camera: SH and projection backward in one kernel
+            d_sh = torch.empty_like(shf)
+            d_quats = torch.empty(N, 4, device=dev)
+            d_log_scales = torch.empty(N, 3, device=dev)
+            d_logits = torch.empty(N, device=dev)
+            _lib.gs_sh_project_bwd(cams, params, ctx.sh_degree, shf, means, quats, log_scales, logits, radii, d_colors,
+                                   d_means2d, d_conics, d_opac, d_sh, d_means, d_quats, d_log_scales, d_logits)
+            return d_means, d_quats, d_log_scales, d_logits, d_sh, None, None, None, None, None, None, None
         if ctx.use_sh:
             d_sh = torch.empty_like(shf)
             if ctx.depth:

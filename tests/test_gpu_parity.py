@@ -428,3 +428,39 @@ def test_persistent_launches_render_the_same_and_reset_their_counters():
     b = gpu_grads(sc, cams, g, settings=st)[0]
     for k in a:
         assert rel_l2(b[k], a[k]) <= 1e-5, k
+
+
+@pytest.mark.parametrize("deg,aa", [(0, False), (1, False), (2, True), (3, False), (3, True)])
+def test_fused_sh_projection_backward_matches_the_two_calls(deg, aa):
+    """gs_sh_project_bwd (one camera) against gs_sh_eval_bwd followed by gs_project_bwd."""
+    sc, cam = _mid_scene(n=20000, seed=41 + deg, deg=deg)
+    d = dev_scene(sc)
+    ca = _lib.CameraArray([cam])
+    p = _lib.make_params(antialiased=aa)
+    N = sc.n
+    sp = raster.project(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], p)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    rnd = lambda *shape: torch.randn(*shape, device="cuda", generator=gen)
+    d_colors, d_m2, d_con, d_op = rnd(1, N, 3), rnd(1, N, 2), rnd(1, N, 3) * 1e-2, rnd(1, N)
+    e = lambda *shape: torch.full(shape, float("nan"), device="cuda")  # every output must be written
+    a = dict(d_sh=e(*d["sh"].shape), d_means=e(N, 3), d_quats=e(N, 4), d_ls=e(N, 3), d_lg=e(N))
+    _lib.gs_sh_eval_bwd(ca, d["sh_degree"], d["sh"], d["means"], sp["radii"], d_colors, a["d_sh"], a["d_means"])
+    _lib.gs_project_bwd(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], p, sp["radii"], d_m2, d_con,
+                        d_op, None, a["d_means"], a["d_quats"], a["d_ls"], a["d_lg"])
+    b = dict(d_sh=e(*d["sh"].shape), d_means=e(N, 3), d_quats=e(N, 4), d_ls=e(N, 3), d_lg=e(N))
+    _lib.gs_sh_project_bwd(ca, p, d["sh_degree"], d["sh"], d["means"], d["quats"], d["log_scales"],
+                           d["opacity_logits"], sp["radii"], d_colors, d_m2, d_con, d_op, b["d_sh"], b["d_means"],
+                           b["d_quats"], b["d_ls"], b["d_lg"])
+    torch.cuda.synchronize()
+    vis = (sp["radii"][0] > 0).cpu().numpy()
+    assert 0 < vis.sum() < N  # both visible and culled Gaussians
+    for k in a:
+        x, y = a[k].cpu().numpy(), b[k].cpu().numpy()
+        assert np.isfinite(y).all(), k
+        assert rel_l2(y, x) <= 1e-6, (k, rel_l2(y, x))
+    assert (b["d_sh"].cpu().numpy()[~vis] == 0).all() and (b["d_means"].cpu().numpy()[~vis] == 0).all()
+    # more than one camera is refused
+    with pytest.raises(_lib.GsError):
+        _lib.gs_sh_project_bwd(_lib.CameraArray([cam, cam]), p, d["sh_degree"], d["sh"], d["means"], d["quats"],
+                               d["log_scales"], d["opacity_logits"], sp["radii"], d_colors, d_m2, d_con, d_op,
+                               b["d_sh"], b["d_means"], b["d_quats"], b["d_ls"], b["d_lg"])
