@@ -162,10 +162,10 @@ class FramePipeline:
 
     # -- stages ----------------------------------------------------------------------------
     def _pre(self):
-        # project, then SH colours on a side stream while the bin/sort runs on this one: the
-        # SH kernel streams coefficients from HBM while the sort's many short, latency-bound
-        # kernels leave bandwidth idle; both only need the projection, and the compositing
-        # waits for both
+        # project, then SH colours (and the zeroing of the 2D gradient buffer) on a side stream
+        # while the bin/sort runs on this one: the SH kernel streams coefficients from HBM while
+        # the sort's many short, latency-bound kernels leave bandwidth idle; both only need the
+        # projection, and the compositing waits for both
         s, L = self.scene, _lib
         main = torch.cuda.current_stream(self.device)
         L.gs_project(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.means2d,
@@ -173,6 +173,8 @@ class FramePipeline:
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
             L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
+            if self.with_backward:
+                self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
         L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity, None,
                            self.values, self.ranges, self.K_out, self.workspace)
         if self.order is not None:
@@ -211,8 +213,6 @@ class FramePipeline:
         side = torch.cuda.Stream(self.device)
         side.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(side):  # warm-up on the capture stream
-            if self.with_backward:
-                self.g2d.zero_()
             self._pre()
             if self.with_backward:
                 self._post()
@@ -221,8 +221,6 @@ class FramePipeline:
         n0 = _lib.gs_kernel_launches()
         self.g_pre = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.g_pre):
-            if self.with_backward:
-                self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
             self._pre()
         if self.with_backward:
             self.g_post = torch.cuda.CUDAGraph()
@@ -238,8 +236,6 @@ class FramePipeline:
         if graphs:
             self.g_pre.replay()
         else:
-            if self.with_backward:
-                self.g2d.zero_()
             self._pre()
         if events:
             events[0].record()
