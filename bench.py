@@ -170,9 +170,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def kernel_schedule(kernel, sched):
+    """The launch shape one compositing kernel runs with (its own entry of the schedule)."""
+    d = sched.as_dict()
+    if kernel == "rasterize_fwd":
+        return dict(tile=d["tile"], pixels_per_thread=d["pixels_per_thread"], batch_depth=d["batch_depth"],
+                    persistent=d["persistent"])
+    return dict(tile=d["tile"], pixels_per_thread=d["bwd_pixels_per_thread"], batch_depth=d["bwd_batch_depth"],
+                persistent=d["bwd_persistent"])
+
+
 def measured_traffic(workload, kernel, sched):
     """DRAM bytes per launch of ``kernel`` from the committed ncu capture (profiles/traffic.json),
-    or None when the capture is for another workload, schedule or kernel source."""
+    or None when the capture is for another workload, launch shape of that kernel or kernel source."""
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(prof):
         return None
@@ -180,9 +190,10 @@ def measured_traffic(workload, kernel, sched):
         tr = json.load(fh)
     if tr.get("workload") != workload or tr.get("source_hash") != kernel_source_hash():
         return None
-    if tr.get("schedule") != sched.as_dict():
+    k = tr.get("kernels", {}).get(kernel)
+    if not k or k.get("schedule") != kernel_schedule(kernel, sched):
         return None
-    return tr.get("kernels", {}).get(kernel)
+    return k.get("bytes")
 
 
 def job_totals(ms_step, blends, world, device):
