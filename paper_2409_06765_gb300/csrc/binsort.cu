@@ -43,6 +43,7 @@ constexpr int kSortBlock = kSortThreads * kSortIPT;  // items per block of a pas
 constexpr int kChunk = 1024;             // emission chunk (output slots)
 constexpr int kEmitThreads = 256;
 constexpr int kSlotsPerThread = kChunk / kEmitThreads;
+static_assert(kSlotsPerThread == 4, "emission stores a thread's slots as one 16-byte store");
 constexpr long long kWaitSpins = 1ll << 22;  // bound on a wait for a bulk copy
 
 // misc region layout (ints)
@@ -550,11 +551,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
     // tile-less pairs (offset n_eff or beyond) are never inside a chunk
     constexpr int P = kChunk;
     __shared__ int s_off[P + 1];  // first slot of each pair, relative to the chunk
-    __shared__ int s_xy[P];       // tx0 | ty0 << 16
-    __shared__ int s_wc[P];       // rectangle width | camera << 16
+    __shared__ int s_base[P];     // global tile id of the rectangle's first tile
+    __shared__ int s_wt[P];       // rectangle width | the camera's tiles per row << 16
     __shared__ int s_id[P];
-    __shared__ uint32_t s_key[kChunk + kChunk / 32];
-    __shared__ int s_val[kChunk + kChunk / 32];
     const int n = *n_eff;
     const int nchunks = (n + kChunk - 1) / kChunk;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {  // normally one chunk per CTA
@@ -574,16 +573,18 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
             const bool in = off < k0 + len;
             if (in) {
                 const int2 rc = rects[j];
+                const CamDev &cam = cs.cam[rc.y >> 16];
                 s_off[s] = (int)(off - k0);  // negative for the pair that straddles into the chunk
-                s_xy[s] = rc.x;
-                s_wc[s] = rc.y;
+                s_base[s] = cam.tile_offset + (rc.x >> 16) * cam.tiles_x + (rc.x & 0xffff);
+                s_wt[s] = (rc.y & 0xffff) | (cam.tiles_x << 16);
                 s_id[s] = order[j];
             }
             np += __syncthreads_count(in);
         }
         if (threadIdx.x == 0) s_off[np] = 1 << 30;
         __syncthreads();
-        // each thread fills kSlotsPerThread consecutive slots
+        // each thread fills kSlotsPerThread consecutive slots and stores them as one 16-byte
+        // store per array (consecutive threads, consecutive 16-byte pieces)
         const int q0 = threadIdx.x * kSlotsPerThread;
         if (q0 < len) {
             int lo = 0, hi = np - 1;  // last pair whose first slot is <= q0
@@ -595,38 +596,46 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(
             int p = lo;
             // position (kx, ky) of slot q0 in its pair's tile rectangle: one division, then the
             // following slots step through the rectangle (a new pair starts at its corner)
-            int w = s_wc[p] & 0xffff;
-            int kk = q0 - s_off[p];
-            int ky = kk / w, kx = kk - ky * w;
+            int w = s_wt[p] & 0xffff, tx = s_wt[p] >> 16;
+            const int kk = q0 - s_off[p];
+            const int ky = kk / w;
+            int kx = kk - ky * w;
+            int tile = s_base[p] + ky * tx + kx;
+            uint32_t key[kSlotsPerThread];
+            int val[kSlotsPerThread];
 #pragma unroll
             for (int u = 0; u < kSlotsPerThread; ++u) {
                 const int q = q0 + u;
-                if (q >= len) break;
-                if (u > 0) {
+                if (u > 0 && q < len) {
                     if (q >= s_off[p + 1]) {
                         while (q >= s_off[p + 1]) ++p;
-                        w = s_wc[p] & 0xffff;
+                        w = s_wt[p] & 0xffff;
+                        tx = s_wt[p] >> 16;
                         kx = 0;
-                        ky = 0;
+                        tile = s_base[p];
                     } else if (++kx == w) {
                         kx = 0;
-                        ++ky;
+                        tile += tx - w + 1;  // first tile of the next row of the rectangle
+                    } else {
+                        ++tile;
                     }
                 }
-                const int cam = s_wc[p] >> 16;
-                const int tx0 = s_xy[p] & 0xffff, ty0 = s_xy[p] >> 16;
-                const uint32_t tile =
-                    (uint32_t)(cs.cam[cam].tile_offset + (ty0 + ky) * cs.cam[cam].tiles_x + tx0 + kx);
-                s_key[q + (q >> 5)] = tile;  // padded: one bank shift per 32 slots
-                s_val[q + (q >> 5)] = s_id[p];
+                key[u] = (uint32_t)tile;
+                val[u] = s_id[p];
+            }
+            if (q0 + kSlotsPerThread <= len) {  // k0 and q0 are multiples of 4: 16-byte aligned
+                *reinterpret_cast<uint4 *>(tkeys + k0 + q0) = make_uint4(key[0], key[1], key[2], key[3]);
+                *reinterpret_cast<int4 *>(tvals + k0 + q0) = make_int4(val[0], val[1], val[2], val[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kSlotsPerThread; ++u)
+                    if (q0 + u < len) {
+                        tkeys[k0 + q0 + u] = key[u];
+                        tvals[k0 + q0 + u] = val[u];
+                    }
             }
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < len; q += kEmitThreads) {
-            tkeys[k0 + q] = s_key[q + (q >> 5)];
-            tvals[k0 + q] = s_val[q + (q >> 5)];
-        }
-        __syncthreads();
+        __syncthreads();  // the next chunk reuses the shared arrays
     }
 }
 
