@@ -424,15 +424,12 @@ __global__ void __launch_bounds__(kTmaThreads, 2) scatter_tma_kernel(const uint3
 // stage 2: tile counts, offsets, chunk starts, balanced emission
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool tile_rect(const CamSet &cs, int N, int i, const float2 *__restrict__ means2d,
-                                          const int *__restrict__ radii, int &c, int &tx0, int &tx1, int &ty0,
-                                          int &ty1) {
-    if ((unsigned)i >= (unsigned)(cs.C * N)) return false;
-    const int r = radii[i];
-    if (r <= 0) return false;
+// Tile rectangle of pair i from its radius r and 2D mean m (false when it touches no tile).
+__device__ __forceinline__ bool tile_rect_of(const CamSet &cs, int N, int i, int r, float2 m, int &c, int &tx0,
+                                             int &tx1, int &ty0, int &ty1) {
+    if ((unsigned)i >= (unsigned)(cs.C * N) || r <= 0) return false;
     c = i / N;
     const CamDev &cam = cs.cam[c];
-    const float2 m = means2d[i];
     int x0, x1, y0, y1;
     if (!pixel_box(m.x, m.y, r, cam.W, cam.H, x0, x1, y0, y1)) return false;
     const int t = cs.tile;
@@ -443,8 +440,13 @@ __device__ __forceinline__ bool tile_rect(const CamSet &cs, int N, int i, const 
     return true;
 }
 
+constexpr int kPairsPerThread = 4;                            // consecutive pairs per thread
+constexpr int kPairsPerCta = 256 * kPairsPerThread;           // pairs per CTA of the count/offset kernels
+
 // Tiles touched by each pair, in depth order, their sum per CTA, and each pair's tile
-// rectangle packed as (tx0 | ty0 << 16, width | camera << 16) for the emission.
+// rectangle packed as (tx0 | ty0 << 16, width | camera << 16) for the emission.  A thread
+// owns kPairsPerThread consecutive pairs: all their indices, then all their radii and means
+// are requested before any is used, so the two dependent gathers overlap.
 __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, int *__restrict__ tile_ranges,
                                                           const __grid_constant__ CamSet cs,
                                                           const int *__restrict__ order,
@@ -454,19 +456,47 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * T; i += gridDim.x * blockDim.x)
         tile_ranges[i] = 0;  // empty tiles read (0, 0); the ranges kernel fills the others later
     __shared__ long long s_w[8];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int cnt = 0;
-    if (j < CN) {
-        int c = 0, tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
-        const bool ok = tile_rect(cs, N, order[j], means2d, radii, c, tx0, tx1, ty0, ty1);
-        cnt = ok ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
-        counts[j] = cnt;
-        rects[j] = make_int2(tx0 | (ty0 << 16), (ok ? tx1 - tx0 + 1 : 1) | (c << 16));
-    }
-    long long s = cnt;
+    const int j0 = blockIdx.x * kPairsPerCta + threadIdx.x * kPairsPerThread;
+    int id[kPairsPerThread], r[kPairsPerThread];
+    float2 m[kPairsPerThread];
+    if (j0 + kPairsPerThread <= CN) {  // j0 is a multiple of 4 and order 16-byte aligned
+        const int4 v = *reinterpret_cast<const int4 *>(order + j0);
+        id[0] = v.x, id[1] = v.y, id[2] = v.z, id[3] = v.w;
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+        for (int u = 0; u < kPairsPerThread; ++u) id[u] = j0 + u < CN ? order[j0 + u] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kPairsPerThread; ++u) {
+        const bool ok = (unsigned)id[u] < (unsigned)CN;
+        r[u] = ok ? radii[id[u]] : 0;
+        m[u] = ok ? means2d[id[u]] : make_float2(0.f, 0.f);
+    }
+    int cnt[kPairsPerThread];
+    int2 rc[kPairsPerThread];
+#pragma unroll
+    for (int u = 0; u < kPairsPerThread; ++u) {
+        int c = 0, tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+        const bool ok = tile_rect_of(cs, N, id[u], r[u], m[u], c, tx0, tx1, ty0, ty1);
+        cnt[u] = ok ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
+        rc[u] = make_int2(tx0 | (ty0 << 16), (ok ? tx1 - tx0 + 1 : 1) | (c << 16));
+    }
+    if (j0 + kPairsPerThread <= CN) {
+        *reinterpret_cast<int4 *>(counts + j0) = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
+        *reinterpret_cast<int4 *>(rects + j0) = make_int4(rc[0].x, rc[0].y, rc[1].x, rc[1].y);
+        *reinterpret_cast<int4 *>(rects + j0 + 2) = make_int4(rc[2].x, rc[2].y, rc[3].x, rc[3].y);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kPairsPerThread; ++u)
+            if (j0 + u < CN) {
+                counts[j0 + u] = cnt[u];
+                rects[j0 + u] = rc[u];
+            }
+    }
+    long long sum = (long long)cnt[0] + cnt[1] + cnt[2] + cnt[3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
     __syncthreads();
     if (threadIdx.x == 0) {
         long long t = 0;
@@ -520,9 +550,17 @@ __global__ void __launch_bounds__(256) offsets_kernel(int CN, const int *__restr
                                                       int *__restrict__ chunk_start) {
     __shared__ long long s_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cnt = j < CN ? counts[j] : 0;
-    long long x = cnt;
+    const int j0 = blockIdx.x * kPairsPerCta + threadIdx.x * kPairsPerThread;
+    int cnt[kPairsPerThread];
+    if (j0 + kPairsPerThread <= CN) {
+        const int4 v = *reinterpret_cast<const int4 *>(counts + j0);
+        cnt[0] = v.x, cnt[1] = v.y, cnt[2] = v.z, cnt[3] = v.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < kPairsPerThread; ++u) cnt[u] = j0 + u < CN ? counts[j0 + u] : 0;
+    }
+    const long long mine = (long long)cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    long long x = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -532,13 +570,18 @@ __global__ void __launch_bounds__(256) offsets_kernel(int CN, const int *__restr
     __syncthreads();
     long long wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
-    if (j >= CN) return;
-    const long long off = partials[blockIdx.x] + wpre + x - cnt;
-    offsets[j] = off;
+    long long off = partials[blockIdx.x] + wpre + x - mine;
     const long long limit = *n_eff;
-    if (cnt > 0 && off < limit) {
-        const long long end = min(off + cnt, limit);
-        for (long long c = (off + kChunk - 1) / kChunk; c * kChunk < end; ++c) chunk_start[c] = j;
+#pragma unroll
+    for (int u = 0; u < kPairsPerThread; ++u) {
+        const int j = j0 + u;
+        if (j >= CN) break;
+        offsets[j] = off;
+        if (cnt[u] > 0 && off < limit) {
+            const long long end = min(off + cnt[u], limit);
+            for (long long c = (off + kChunk - 1) / kChunk; c * kChunk < end; ++c) chunk_start[c] = j;
+        }
+        off += cnt[u];
     }
 }
 
@@ -844,12 +887,13 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     }
     const int *order = dv0;  // after 4 passes the sorted pairs are back in (dk0, dv0)
     // stage 2: tile counts, offsets, balanced emission, stable sort by tile id
-    count_tiles_kernel<<<eb, 256, 0, st>>>(cn, N, T, tile_ranges, cs, order, (const float2 *)means2d, radii, counts,
+    const int pb = (cn + kPairsPerCta - 1) / kPairsPerCta;  // CTAs of the count and offset kernels
+    count_tiles_kernel<<<pb, 256, 0, st>>>(cn, N, T, tile_ranges, cs, order, (const float2 *)means2d, radii, counts,
                                            rects, partials);
     note_launch();
-    partial_scan_kernel<<<1, 1024, 0, st>>>(eb, partials, Kcap, K_out, n_eff);
+    partial_scan_kernel<<<1, 1024, 0, st>>>(pb, partials, Kcap, K_out, n_eff);
     note_launch();
-    offsets_kernel<<<eb, 256, 0, st>>>(cn, counts, partials, n_eff, offsets, chunk_start);
+    offsets_kernel<<<pb, 256, 0, st>>>(cn, counts, partials, n_eff, offsets, chunk_start);
     note_launch();
     // choose buffers so that the last pass writes into the caller's `values`
     uint32_t *kA = tk0, *kB = tk1;
