@@ -116,7 +116,36 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
                                                          int *__restrict__ vals, int *__restrict__ misc) {
     if (blockIdx.x == 0)  // the sort's counters, digit totals and error flag start at zero
         for (int i = threadIdx.x; i < kMiscInts; i += blockDim.x) misc[i] = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < CN; i += gridDim.x * blockDim.x) {
+    // four consecutive pairs per thread: 16-byte loads of radii, depths and means, 16-byte stores
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= CN) return;
+    const bool vec = ((reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(depths) |
+                       reinterpret_cast<uintptr_t>(means2d)) & 15) == 0;  // (caller arrays: usually aligned)
+    if (vec && i0 + 4 <= CN) {  // i0 is a multiple of 4: 16-byte loads and stores
+        const int4 r = *reinterpret_cast<const int4 *>(radii + i0);
+        const float4 d = *reinterpret_cast<const float4 *>(depths + i0);
+        const float4 m01 = *reinterpret_cast<const float4 *>(means2d + i0);
+        const float4 m23 = *reinterpret_cast<const float4 *>(means2d + i0 + 2);
+        const int rr[4] = {r.x, r.y, r.z, r.w};
+        const float dd[4] = {d.x, d.y, d.z, d.w};
+        const float2 mm[4] = {make_float2(m01.x, m01.y), make_float2(m01.z, m01.w), make_float2(m23.x, m23.y),
+                              make_float2(m23.z, m23.w)};
+        uint32_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bool ok = rr[u] > 0;
+            if (ok) {
+                const CamDev &cam = cs.cam[(i0 + u) / N];
+                int x0, x1, y0, y1;
+                ok = pixel_box(mm[u].x, mm[u].y, rr[u], cam.W, cam.H, x0, x1, y0, y1);
+            }
+            k[u] = ok ? __float_as_uint(dd[u]) : 0xffffffffu;
+        }
+        *reinterpret_cast<uint4 *>(keys + i0) = make_uint4(k[0], k[1], k[2], k[3]);
+        *reinterpret_cast<int4 *>(vals + i0) = make_int4(i0, i0 + 1, i0 + 2, i0 + 3);
+        return;
+    }
+    for (int i = i0; i < min(CN, i0 + 4); ++i) {  // the ragged end, or unaligned inputs
         const int r = radii[i];
         bool ok = r > 0;
         if (ok) {
@@ -874,7 +903,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     const int tpasses = (bits + 6) / 7;                // passes of at most 7 bits
     const int tdigit = (bits + tpasses - 1) / tpasses;  // equal digit widths
     // stage 1: depth order of all (camera, Gaussian) pairs
-    const int eb = (cn + 255) / 256;
+    const int eb = (cn + 1023) / 1024;  // four pairs per thread
     depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0, misc);
     note_launch();
     cudaError_t e = cudaGetLastError();
