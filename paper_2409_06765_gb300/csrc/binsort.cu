@@ -227,6 +227,36 @@ __global__ void __launch_bounds__(kSortThreads) hist_rowsum_kernel(const int *__
 
 // hist[d * cols + b] <- global start of digit d for block b:
 // sum_{d' < d} rowsum[d'] + sum_{b' < b} hist[d * cols + b'].
+// Rows of up to 256 * MAXSEG blocks: every thread loads its whole segment into registers (all
+// loads in flight at once) and rewrites it from there.
+template <int MAXSEG>
+__global__ void __launch_bounds__(kSortThreads) hist_scan_reg_kernel(const int *__restrict__ n_dev, int n_host,
+                                                                   int cols, const int *__restrict__ rowsum,
+                                                                   int *__restrict__ hist) {
+    __shared__ int s_tmp[8];
+    const int n = n_dev ? *n_dev : n_host;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int d = blockIdx.x;
+    int *row = hist + (size_t)d * cols;
+    const int seg = (nb + kSortThreads - 1) / kSortThreads;  // <= MAXSEG (checked by the host)
+    const int b0 = threadIdx.x * seg, b1 = min(nb, b0 + seg);
+    int v[MAXSEG];
+#pragma unroll
+    for (int k = 0; k < MAXSEG; ++k) v[k] = b0 + k < b1 ? row[b0 + k] : 0;
+    const int pre = threadIdx.x < d ? rowsum[threadIdx.x] : 0;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < MAXSEG; ++k) s += v[k];
+    int base, tot;
+    block_exclusive_scan(pre, base, s_tmp);
+    int run = base + block_exclusive_scan(s, tot, s_tmp);
+#pragma unroll
+    for (int k = 0; k < MAXSEG; ++k) {
+        if (b0 + k < b1) row[b0 + k] = run;
+        run += v[k];
+    }
+}
+
 __global__ void __launch_bounds__(kSortThreads) hist_scan_kernel(const int *__restrict__ n_dev, int n_host, int cols,
                                                                const int *__restrict__ rowsum, int *__restrict__ hist) {
     __shared__ int s_tmp[8];
@@ -855,7 +885,12 @@ static cudaError_t rts_pass(const uint32_t *kin, const int *vin, uint32_t *kout,
         hist_rowsum_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, matrix, rowsum);
         note_launch();
     }
-    hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+    if (cols <= kSortThreads * 4)
+        hist_scan_reg_kernel<4><<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+    else if (cols <= kSortThreads * 32)
+        hist_scan_reg_kernel<32><<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+    else
+        hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
     note_launch();
     cudaError_t e =
         ensure_smem((const void *)scatter_tma_kernel, (int)kTmaSmem);
