@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) scatter_tma_kernel(const uint3
         if (threadIdx.x == 0 && next < nb) issue(next, buf ^ 1);
         for (int i = threadIdx.x; i < W * kRadix; i += kTmaThreads) {
             (&s_warp[0][0])[i] = 0;
-            (&s_peer[0][0])[i] = 0u;
+            if (it == 0) (&s_peer[0][0])[i] = 0u;  // the ranking leaves every peer mask at zero again
         }
         const bool landed = mbar_wait_bounded(&s_bar[buf], (unsigned)(it >> 1) & 1u, err);
         uint32_t *ik = s_in_k + buf * kSortBlock;
@@ -435,11 +435,13 @@ __global__ void __launch_bounds__(kTmaThreads, 2) scatter_tma_kernel(const uint3
             const int d = threadIdx.x;
             int run = 0;
             if (d < kRadix) {
+                int c[W];  // all W counts in flight before the prefix is written back
+#pragma unroll
+                for (int w = 0; w < W; ++w) c[w] = s_warp[w][d];
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const int c = s_warp[w][d];
                     s_warp[w][d] = run;
-                    run += c;
+                    run += c[w];
                 }
             }
             int tot;
