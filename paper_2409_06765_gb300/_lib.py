@@ -184,19 +184,27 @@ def _dev(t, kind, name, optional=False):
         if optional:
             return None
         raise ValueError(f"{name} is required")
+    if isinstance(t, torch.Tensor) and t.is_cuda and t.dtype is _DT[kind] and t.is_contiguous():
+        return ctypes.c_void_p(t.data_ptr())
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if t.dtype != _DT[kind]:
         raise TypeError(f"{name} must be {_DT[kind]}, got {t.dtype}")
-    if not t.is_contiguous():
-        raise ValueError(f"{name} must be contiguous")
-    return ctypes.c_void_p(t.data_ptr())
+    raise ValueError(f"{name} must be contiguous")
+
+
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_cur_device = getattr(torch._C, "_cuda_getDevice", None)
 
 
 def _stream(stream):
+    """The cudaStream_t to launch on: the given stream, else the current stream of the current
+    device (queried through torch's raw handle, which skips the Python stream object)."""
     if stream is None:
+        if _raw_stream is not None and _cur_device is not None:
+            return ctypes.c_void_p(_raw_stream(_cur_device()))
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 

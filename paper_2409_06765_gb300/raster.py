@@ -43,15 +43,29 @@ class RasterSettings:
     bwd_persistent: bool = False
 
     def params(self) -> _lib.GsParams:
-        return _lib.make_params(self.tile, self.batch_depth, self.antialiased, self.eps2d, self.near_plane,
-                                self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread,
-                                persistent=self.persistent and self.tile_schedule)
+        return _cached_params(self.tile, self.batch_depth, bool(self.antialiased), self.eps2d, self.near_plane,
+                              self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread,
+                              bool(self.persistent and self.tile_schedule))
 
     def params_bwd(self) -> _lib.GsParams:
-        return _lib.make_params(self.tile, self.bwd_batch_depth or self.batch_depth, self.antialiased, self.eps2d,
-                                self.near_plane, self.alpha_min, self.alpha_max, self.T_min,
-                                self.bwd_pixels_per_thread or self.pixels_per_thread,
-                                persistent=self.bwd_persistent and self.tile_schedule)
+        return _cached_params(self.tile, self.bwd_batch_depth or self.batch_depth, bool(self.antialiased), self.eps2d,
+                              self.near_plane, self.alpha_min, self.alpha_max, self.T_min,
+                              self.bwd_pixels_per_thread or self.pixels_per_thread,
+                              bool(self.bwd_persistent and self.tile_schedule))
+
+
+_PARAMS: dict = {}
+
+
+def _cached_params(*key) -> _lib.GsParams:
+    """One launch-parameter struct per distinct setting (the calls only read it)."""
+    p = _PARAMS.get(key)
+    if p is None:
+        tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent = key
+        p = _lib.make_params(tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent=persistent)
+        if len(_PARAMS) < 256:
+            _PARAMS[key] = p
+    return p
 
 
 @dataclass
@@ -100,10 +114,12 @@ class RasterState:
 
 def project(cams, means, quats, log_scales, opacity_logits, params):
     C, N, dev = cams.C, means.shape[0], means.device
-    out = dict(means2d=torch.empty(C, N, 2, device=dev), depths=torch.empty(C, N, device=dev),
-               conics=torch.empty(C, N, 3, device=dev), radii=torch.empty(C, N, dtype=torch.int32, device=dev),
-               tiles_touched=torch.empty(C, N, dtype=torch.int32, device=dev),
-               opacities=torch.empty(C, N, device=dev))
+    CN = C * N
+    f = torch.empty(7 * CN, device=dev)  # means2d | depths | conics | opacities, one allocation
+    i = torch.empty(2 * CN, dtype=torch.int32, device=dev)  # radii | tiles touched
+    out = dict(means2d=f[:2 * CN].view(C, N, 2), depths=f[2 * CN:3 * CN].view(C, N),
+               conics=f[3 * CN:6 * CN].view(C, N, 3), opacities=f[6 * CN:].view(C, N),
+               radii=i[:CN].view(C, N), tiles_touched=i[CN:].view(C, N))
     _lib.gs_project(cams, means, quats, log_scales, opacity_logits, params, out["means2d"], out["depths"],
                     out["conics"], out["radii"], out["tiles_touched"], out["opacities"])
     return out
