@@ -125,10 +125,10 @@ def project(cams, means, quats, log_scales, opacity_logits, params):
     return out
 
 
-def sh_eval(cams, sh_degree, sh, means, radii, depths=None):
+def sh_eval(cams, sh_degree, sh, means, radii, depths=None, out=None):
     """SH colours [C,N,3]; with ``depths``, (r, g, b, z) rows [C,N,4] for depth rendering (App. A)."""
     ch = 3 if depths is None else 4
-    colors = torch.empty(cams.C, means.shape[0], ch, device=means.device)
+    colors = torch.empty(cams.C, means.shape[0], ch, device=means.device) if out is None else out
     if depths is None:
         _lib.gs_sh_eval(cams, sh_degree, sh, means, radii, colors)
     else:
@@ -190,6 +190,22 @@ def rasterize_fwd(cams, N, params, channels, ranges, values, radii, means2d, con
     return image, final_T, last, blends
 
 
+_SIDE: dict = {}
+SIDE_STREAM_MIN_PAIRS = 1 << 18  # (camera, Gaussian) pairs from which SH runs beside the sort
+
+
+def _side_stream(main: torch.cuda.Stream) -> torch.cuda.Stream:
+    """A side stream for work that overlaps the sort, one per launching stream (so frames on
+    different streams never wait on each other's side work)."""
+    key = main.cuda_stream
+    st = _SIDE.get(key)
+    if st is None:
+        if len(_SIDE) >= 64:
+            _SIDE.clear()
+        st = _SIDE[key] = torch.cuda.Stream(device=main.device)
+    return st
+
+
 def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_degree=0, features=None,
                  settings: RasterSettings | None = None, state: RasterState | None = None, count_blends=False,
                  depth=False, defer_sync=False):
@@ -199,7 +215,17 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
     params = settings.params()
     N = means.shape[0]
     sp = project(cams, means, quats, log_scales, opacity_logits, params)
-    if features is None:
+    side = None
+    if features is None and cams.C * N >= SIDE_STREAM_MIN_PAIRS:
+        # SH colours on a side stream while the bin/sort runs on this one (both need only the
+        # projection; the compositing waits for both).  The buffer is taken on this stream.
+        colors = torch.empty(cams.C, N, 4 if depth else 3, device=means.device)
+        main = torch.cuda.current_stream(means.device)
+        side = _side_stream(main)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            sh_eval(cams, sh_degree, sh, means, sp["radii"], sp["depths"] if depth else None, out=colors)
+    elif features is None:  # small frames: the stream switch costs more than the overlap gains
         colors = sh_eval(cams, sh_degree, sh, means, sp["radii"], sp["depths"] if depth else None)
     else:
         colors = features
@@ -210,6 +236,9 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
     for _ in range(3):
         bs = bin_sort(cams, N, params, sp["means2d"], sp["depths"], sp["radii"], state, sync=False)
         order = tile_order(cams, params, bs["ranges"]) if settings.tile_schedule else None
+        if side is not None:
+            torch.cuda.current_stream(means.device).wait_stream(side)
+            side = None
         image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
                                                      sp["means2d"], sp["conics"], sp["opacities"], colors,
                                                      settings.background, count_blends, order)
