@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     constexpr int NA = ABSG ? 2 : 0;
     constexpr int V = 6 + NA + CHC;
     constexpr bool SG = scaled_grad<PPT>();
+    // lanes with 2 or 4 pixels (one column) sum per-pixel moments; absgrad needs per-pixel terms
+    constexpr bool MOMENTS = !ABSG && PPT >= 2;
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *s_g = reinterpret_cast<float4 *>(smem);
     float4 *s_h = s_g + batch;
@@ -276,6 +278,10 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 float v[V];
 #pragma unroll
                 for (int i = 0; i < V; ++i) v[i] = 0.f;
+                // (MOMENTS) the lane's pixels share dx: sum dsig, dsig dy and dsig dy^2 over them and
+                // form the mean and conic terms once per Gaussian instead of per pixel:
+                // sum gx = s (Mx S1 + Bx S0), sum dsig dx^2 = dx^2 S0, sum dsig dx dy = dx S1
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f;
                 bool any = false;
                 // the PPT pixels are independent chains: evaluate all of them without branches
                 // (a pair that does not blend gets zero weight and zero dL/dalpha, so every
@@ -318,19 +324,33 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                     // d sigma / d mu' = -conic D
                     // (with SG: -conic D = (2 a' dx + b' dy, b' dx + 2 c' dy) / log2(e) for the staged
                     // (a', b', c'), and the 1 / log2(e) is applied to the warp totals)
-                    const float sd = SG ? dsig : -dsig;
-                    const float gx = sd * (Mx * dy + Bx);
-                    const float gy = sd * (My * dy + By);
-                    v[0] += gx;
-                    v[1] += gy;
-                    if (ABSG) {
-                        v[6] += fabsf(gx);
-                        v[7] += fabsf(gy);
+                    if constexpr (MOMENTS) {
+                        S0 += dsig;
+                        S1 += dsig * dy;
+                        S2 += dsig * yy;
+                    } else {
+                        const float sd = SG ? dsig : -dsig;
+                        const float gx = sd * (Mx * dy + Bx);
+                        const float gy = sd * (My * dy + By);
+                        v[0] += gx;
+                        v[1] += gy;
+                        if (ABSG) {
+                            v[6] += fabsf(gx);
+                            v[7] += fabsf(gy);
+                        }
+                        // d sigma / d conic = (dx^2 / 2, dx dy, dy^2 / 2): the halves are applied to the warp totals
+                        v[2] += dsig * xx;
+                        v[3] += dsig * xy;
+                        v[4] += dsig * yy;
                     }
-                    // d sigma / d conic = (dx^2 / 2, dx dy, dy^2 / 2): the halves are applied to the warp totals
-                    v[2] += dsig * xx;
-                    v[3] += dsig * xy;
-                    v[4] += dsig * yy;
+                }
+                if constexpr (MOMENTS) {
+                    const float s0 = SG ? S0 : -S0, s1 = SG ? S1 : -S1;
+                    v[0] = Mx * s1 + Bx * s0;
+                    v[1] = My * s1 + By * s0;
+                    v[2] = xx * S0;
+                    v[3] = dx * S1;
+                    v[4] = S2;
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 if constexpr (smem_reduce<PPT>())
