@@ -157,14 +157,19 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // The compositing kernels stage the conic pre-scaled,
-// (a', b', c') = -log2(e) (a / 2, b, c / 2), so that the exponent of the Gaussian weight,
-// p = -log2(e) sigma = a' dx^2 + b' dx dy + c' dy^2, and exp(-sigma) = 2^p cost two
-// multiplications less per pixel; explicit roundings keep forward and backward bit-identical.
-__device__ __forceinline__ float gauss_exponent_parts(float xx, float yy, float xy, float a, float b, float c) {
-    return __fmaf_rn(a, xx, __fmaf_rn(c, yy, __fmul_rn(b, xy)));
+// (a', b', c') = -log2(e) (a / 2, b, c / 2), so that the exponent of the Gaussian weight is
+// p = -log2(e) sigma = a' dx^2 + b' dx dy + c' dy^2 and exp(-sigma) = 2^p.  A thread's pixels
+// share dx (one column), so per Gaussian it forms a' dx^2 and b' dx once and per pixel
+// evaluates p = (c' dy + b' dx) dy + a' dx^2 with two FMAs.  Forward and backward use these
+// same explicitly rounded steps, so they obtain bit-identical weights.
+struct GaussRow {
+    float axx, bdx, c;
+};
+__device__ __forceinline__ GaussRow gauss_row(float dx, float a, float b, float c) {
+    return GaussRow{__fmul_rn(a, __fmul_rn(dx, dx)), __fmul_rn(b, dx), c};
 }
-__device__ __forceinline__ float gauss_exponent(float dx, float dy, float a, float b, float c) {
-    return gauss_exponent_parts(__fmul_rn(dx, dx), __fmul_rn(dy, dy), __fmul_rn(dx, dy), a, b, c);
+__device__ __forceinline__ float gauss_exponent(const GaussRow &r, float dy) {
+    return __fmaf_rn(__fmaf_rn(r.c, dy, r.bdx), dy, r.axx);
 }
 
 // Launch shape of the compositing kernels: PPT pixels per thread stacked along y, so a

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 const bool inx = (unsigned)(px - bx.x) <= (unsigned)bx.y;
                 const float dx = fx - gg.x;
                 const float xx = __fmul_rn(dx, dx);
+                const GaussRow gr = gauss_row(dx, gg.z, gg.w, hh4.x);
                 // per Gaussian: the mean gradient of a pixel is dsig (+-) (Bx + Mx dy, By + My dy)
                 const float Mx = SG ? gg.w : gg.w * -kLn2;
                 const float My = SG ? 2.f * hh4.x : hh4.x * (-2.f * kLn2);
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                     const bool act = rel < last[k] && inx && (unsigned)(py0 + k - bx.z) <= (unsigned)bx.w;
                     const float dy = ((float)(py0 + k) + 0.5f) - gg.y;
                     const float yy = __fmul_rn(dy, dy), xy = __fmul_rn(dx, dy);
-                    const float pe = gauss_exponent_parts(xx, yy, xy, gg.z, gg.w, hh4.x);  // -log2(e) sigma
+                    const float pe = gauss_exponent(gr, dy);  // -log2(e) sigma
                     const float e = ex2_approx(pe);
                     const bool neg = pe > 0.f;  // sigma < 0
                     const float oe = __fmul_rn(hh4.y, e);

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
                 const float2 h = make_float2(s_h[j].x, s_h[j].y);
                 const bool inx = (unsigned)(px - b.x) <= (unsigned)b.y;
                 const float dx = fx - g.x;
+                const GaussRow gr = gauss_row(dx, g.z, g.w, h.x);
                 {
                     // the PPT pixels are independent chains: evaluate all of them without
                     // branches (the decisions become selects) so their latencies overlap
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
                         const bool act = !done[k] && inx && (unsigned)(py0 + k - b.z) <= (unsigned)b.w;
                         if (COUNT) blends += act ? 1 : 0;
                         const float dy = ((float)(py0 + k) + 0.5f) - g.y;
-                        const float pe = gauss_exponent(dx, dy, g.z, g.w, h.x);  // -log2(e) sigma
+                        const float pe = gauss_exponent(gr, dy);  // -log2(e) sigma
                         const float e = ex2_approx(pe);
                         const bool neg = pe > 0.f;  // sigma < 0
                         const float alpha = fminf(amax, __fmul_rn(h.y, e));
