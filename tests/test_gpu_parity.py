@@ -464,3 +464,19 @@ def test_fused_sh_projection_backward_matches_the_two_calls(deg, aa):
         _lib.gs_sh_project_bwd(_lib.CameraArray([cam, cam]), p, d["sh_degree"], d["sh"], d["means"], d["quats"],
                                d["log_scales"], d["opacity_logits"], sp["radii"], d_colors, d_m2, d_con, d_op,
                                b["d_sh"], b["d_means"], b["d_quats"], b["d_ls"], b["d_lg"])
+
+
+def test_autograd_forward_with_colours_beside_the_sort_matches_the_serial_path(monkeypatch):
+    """Frames of 256k+ pairs evaluate SH on a side stream while the sort runs; the image and
+    the gradients must equal the single-stream path's."""
+    sc = synth.clustered_scene(300_000, 17, sh_degree=3, log_scale_mu=-4.0)
+    cam = synth.sphere_cameras(17, [(160, 120)])[0]
+    assert sc.n >= raster.SIDE_STREAM_MIN_PAIRS
+    P = cam.width * cam.height
+    g = np.random.default_rng(18).normal(size=(P, 3)).astype(np.float32)
+    a, img_a, _ = gpu_grads(sc, [cam], g)
+    monkeypatch.setattr(raster, "SIDE_STREAM_MIN_PAIRS", 1 << 40)
+    b, img_b, _ = gpu_grads(sc, [cam], g)
+    np.testing.assert_array_equal(img_a, img_b)
+    for k in a:
+        assert rel_l2(a[k], b[k]) <= 1e-6, k
