@@ -480,3 +480,36 @@ def test_autograd_forward_with_colours_beside_the_sort_matches_the_serial_path(m
     np.testing.assert_array_equal(img_a, img_b)
     for k in a:
         assert rel_l2(a[k], b[k]) <= 1e-6, k
+
+
+def test_bin_sort_with_unaligned_depth_and_radius_arrays():
+    """Inputs that are not 16-byte aligned take the scalar path of the depth-key kernel and
+    give the same lists."""
+    sc, cam = _mid_scene(n=30001, seed=19)
+    ref = oracle.project(sc, cam)
+    m = ref["means2d"].astype(np.float32)[None]
+    d = ref["depths"].astype(np.float32)[None]
+    r = ref["radii"][None]
+    K0, keys0, vals0, ranges0 = _gpu_bin_sort([cam], m, d, r, 16)
+    ca = _lib.CameraArray([cam])
+    p = _lib.make_params(tile=16)
+    N = d.shape[1]
+    dev = "cuda"
+    mm = torch.as_tensor(m, device=dev)
+    # depths and radii one element into larger buffers: 4-byte but not 16-byte aligned
+    dd = torch.zeros(N + 1, device=dev)
+    dd[1:] = torch.as_tensor(d[0], device=dev)
+    rr = torch.zeros(N + 1, dtype=torch.int32, device=dev)
+    rr[1:] = torch.as_tensor(r[0], device=dev)
+    Kcap = K0 + 1024
+    keys = torch.empty(Kcap, dtype=torch.int64, device=dev)
+    values = torch.empty(Kcap, dtype=torch.int32, device=dev)
+    ranges = torch.empty(ca.num_tiles(16), 2, dtype=torch.int32, device=dev)
+    K_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(_lib.gs_tile_bin_sort_workspace(ca, N, p, Kcap), dtype=torch.uint8, device=dev)
+    _lib.gs_tile_bin_sort(ca, N, p, mm, dd[1:].view(1, N), rr[1:].view(1, N), Kcap, keys, values, ranges, K_out, ws)
+    torch.cuda.synchronize()
+    assert int(K_out.item()) == K0
+    np.testing.assert_array_equal(values[:K0].cpu().numpy(), vals0)
+    np.testing.assert_array_equal(keys[:K0].cpu().numpy().view(np.uint64), keys0)
+    np.testing.assert_array_equal(ranges.cpu().numpy(), ranges0)
