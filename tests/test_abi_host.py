@@ -85,6 +85,12 @@ def test_host_validation_rejects_bad_arguments_before_any_launch():
     assert st == _lib.GS_ERR_CAPACITY
     # tile order: NULL output
     assert lib.gs_tile_order(cams.ptr, 1, ctypes.byref(p), fake, null, null) == _lib.GS_ERR_ARG
+    # fused SH + projection backward: one camera only, SH degree, NULL output
+    cams2 = _lib.CameraArray([synth.make_camera(32, 32, (0, 0, 4))] * 2)
+    assert lib.gs_sh_project_bwd(cams2.ptr, 2, 10, ctypes.byref(p), 3, *[fake] * 15, null) == _lib.GS_ERR_ARG
+    assert b"one camera" in lib.gs_last_error()
+    assert lib.gs_sh_project_bwd(cams.ptr, 1, 10, ctypes.byref(p), 4, *[fake] * 15, null) == _lib.GS_ERR_ARG
+    assert lib.gs_sh_project_bwd(cams.ptr, 1, 10, ctypes.byref(p), 3, *[fake] * 14, null, null) == _lib.GS_ERR_ARG
 
 
 def _support_span_f32(m, r):
