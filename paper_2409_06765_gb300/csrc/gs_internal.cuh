@@ -242,7 +242,8 @@ __device__ __forceinline__ bool may_blend(const float4 &g, const float4 &h, cons
     const float y0 = (float)ry0 + 0.5f - g.y, y1 = (float)ry1 + 0.5f - g.y;
     const float a = g.z * (-2.f * kLn2), bb = g.w * (-kLn2), c = h.x * (-2.f * kLn2);
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-    const float ia = 1.f / a, ic = 1.f / c;
+    // (approximate reciprocals only place the minimising point; the margin below covers them)
+    const float ia = rcp_approx(a), ic = rcp_approx(c);
     float best = 3.0e38f;
     // vertical edges: dx fixed, minimise over dy
 #pragma unroll
