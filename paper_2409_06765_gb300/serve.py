@@ -167,6 +167,9 @@ class Server:
         self.overflows = 0
         self.batches = 0
         self.waits_for_memory = 0
+        # pinned host buffers per stream (a stream carries one batch at a time): allocating
+        # page-locked memory per batch costs milliseconds and stalls the loop
+        self._pinned = {}
 
     # capacity of a batch's intersection buffers from the scene's intersections per pixel
     def _capacity(self, sid, reqs, hint=0):
@@ -188,8 +191,7 @@ class Server:
         with torch.cuda.stream(stream):
             pipe = FramePipeline(scene, cams, self.schedule, backward=False, capacity=cap)
             pipe.forward()
-            host_img = torch.empty(pipe.image.shape, dtype=torch.float32, pin_memory=True)
-            host_k = torch.empty(1, dtype=torch.int64, pin_memory=True)
+            host_img, host_k = self._host_buffers(stream, pipe.image.shape)
             host_img.copy_(pipe.image, non_blocking=True)
             host_k.copy_(pipe.K_out, non_blocking=True)
             ev = torch.cuda.Event()
@@ -197,6 +199,19 @@ class Server:
         self.batches += 1
         return _Batch(sid, reqs, pipe, stream, ev, host_img, host_k, nbytes, cap, now,
                       offsets=pipe.cams.pixel_offsets())
+
+    def _host_buffers(self, stream, shape):
+        """The stream's pinned image buffer (grown when a batch needs more) and count slot."""
+        n = 1
+        for d in shape:
+            n *= int(d)
+        img, k = self._pinned.get(stream.cuda_stream, (None, None))
+        if img is None or img.numel() < n:  # grow geometrically: few page-locked allocations
+            img = torch.empty(max(n, 2 * (img.numel() if img is not None else 0), 1 << 20), dtype=torch.float32,
+                              pin_memory=True)
+            k = k if k is not None else torch.empty(1, dtype=torch.int64, pin_memory=True)
+            self._pinned[stream.cuda_stream] = (img, k)
+        return img[:n].view(shape), k
 
     def serve(self, requests, realtime=True, poll_sleep=50e-6):
         """Serve a trace; returns the results in completion order.  With realtime=False every
