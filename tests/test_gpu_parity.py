@@ -478,8 +478,8 @@ def test_autograd_forward_with_colours_beside_the_sort_matches_the_serial_path(m
     monkeypatch.setattr(raster, "SIDE_STREAM_MIN_PAIRS", 1 << 40)
     b, img_b, _ = gpu_grads(sc, [cam], g)
     np.testing.assert_array_equal(img_a, img_b)
-    for k in a:
-        assert rel_l2(a[k], b[k]) <= 1e-6, k
+    for k in a:  # gradients: the atomic sums of the backward may add in another order
+        assert rel_l2(a[k], b[k]) <= 1e-5, k
 
 
 def test_bin_sort_with_unaligned_depth_and_radius_arrays():
