@@ -237,29 +237,34 @@ __device__ __forceinline__ bool may_blend(const float4 &g, const float4 &h, cons
                                           int ry1) {
     if (!box_hits(b, rx0, rx1, ry0, ry1)) return false;
     if (!(h.z >= 0.f)) return false;
-    // minimum of sigma(p) = 1/2 (p-m)^T [[a,b],[b,c]] (p-m) over the rectangle of pixel centres
+    // the minimum of sigma(p) = 1/2 (p-m)^T [[a,b],[b,c]] (p-m) over the rectangle of pixel
+    // centres, taken as the maximum of the staged exponent p = a' dx^2 + b' dx dy + c' dy^2
+    // = -log2(e) sigma (a', c' < 0: concave), which is on the boundary unless the mean is inside
     const float x0 = (float)rx0 + 0.5f - g.x, x1 = (float)rx1 + 0.5f - g.x;
     const float y0 = (float)ry0 + 0.5f - g.y, y1 = (float)ry1 + 0.5f - g.y;
-    const float a = g.z * (-2.f * kLn2), bb = g.w * (-kLn2), c = h.x * (-2.f * kLn2);
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-    // (approximate reciprocals only place the minimising point; the margin below covers them)
+    const float a = g.z, bb = g.w, c = h.x;
+    // (approximate reciprocals only place the maximising point; the margin below covers them)
     const float ia = rcp_approx(a), ic = rcp_approx(c);
-    float best = 3.0e38f;
-    // vertical edges: dx fixed, minimise over dy
+    float best = -3.0e38f;
+    // vertical edges: dx fixed, dp/ddy = b' dx + 2 c' dy = 0
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const float dx = e ? x1 : x0;
-        const float dy = fminf(fmaxf(-bb * dx * ic, y0), y1);
-        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + bb * dx * dy);
+        const float bdx = bb * dx;
+        const float dy = fminf(fmaxf(-0.5f * bdx * ic, y0), y1);
+        best = fmaxf(best, fmaf(fmaf(c, dy, bdx), dy, a * dx * dx));
     }
-    // horizontal edges: dy fixed, minimise over dx
+    // horizontal edges: dy fixed, dp/ddx = 2 a' dx + b' dy = 0
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const float dy = e ? y1 : y0;
-        const float dx = fminf(fmaxf(-bb * dy * ia, x0), x1);
-        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + bb * dx * dy);
+        const float bdy = bb * dy;
+        const float dx = fminf(fmaxf(-0.5f * bdy * ia, x0), x1);
+        best = fmaxf(best, fmaf(fmaf(a, dx, bdy), dx, c * dy * dy));
     }
-    return best <= h.z * 1.001f + 1e-3f;
+    // sigma_min <= cut (1 + 1e-3) + 1e-3, a margin far above float32 rounding
+    return best >= -(h.z * 1.001f + 1e-3f) * kLog2e;
 }
 
 }  // namespace gs
