@@ -27,7 +27,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.timeout(120)
 def test_two_replicas_report_max_time_and_total_work():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
