@@ -118,6 +118,23 @@ def test_off_axis_isotropic_closed_form():
     np.testing.assert_allclose(p["cov2d"][0], expect, rtol=1e-12)
 
 
+def test_unequal_focal_lengths_and_principal_point_closed_form():
+    # K = [[fx, 0, cx], [0, fy, cy], [0, 0, 1]] (App. E, with the printed fy/fy, cx/cx read as
+    # fx/fy, cx/cy): x uses only fx and cx, y only fy and cy.  With the identity pose and
+    # J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]], an isotropic Gaussian of scale s gives
+    # Sigma' = s^2 J J^T = s^2 [[fx^2 (z^2 + x^2)/z^4, fx fy x y/z^4], [., fy^2 (z^2 + y^2)/z^4]]
+    x, y, z, s = 0.35, -0.2, 2.0, 0.04
+    fx, fy, cx, cy = 70.0, 45.0, 31.0, 18.0
+    sc = _scene([[x, y, z]], [[1, 0, 0, 0]], [[math.log(s)] * 3], [0.0], np.zeros((1, 1, 3)))
+    cam = synth.Camera(64, 40, np.eye(4, dtype=np.float32), fx, fy, cx, cy)
+    p = oracle.project(sc, cam)
+    np.testing.assert_allclose(p["means2d"][0], [fx * x / z + cx, fy * y / z + cy], rtol=1e-14)
+    z4 = z ** 4
+    expect = [s * s * fx * fx * (z * z + x * x) / z4 + 0.3, s * s * fx * fy * x * y / z4,
+              s * s * fy * fy * (z * z + y * y) / z4 + 0.3]
+    np.testing.assert_allclose(p["cov2d"][0], expect, rtol=1e-12)
+
+
 def test_anisotropic_axis_aligned_and_rotated_90():
     # scales (sx, sy, sz) with identity rotation: Sigma' = diag(f^2 sx^2/z^2, f^2 sy^2/z^2) + 0.3
     # rotating the Gaussian by 90 degrees about the optical axis swaps the two entries
@@ -354,6 +371,53 @@ def test_alpha_below_threshold_is_skipped():
     assert np.all(r["color"] == 0.0) and np.all(r["T"] == 1.0) and np.all(r["ncontrib"] == 0)
 
 
+def test_skipped_gaussian_leaves_the_ones_behind_it():
+    # a faint Gaussian in front (alpha < 1/255 everywhere) is passed over, not a stop: the
+    # pixel is exactly what the back Gaussian renders alone, c alpha with alpha = o e^-sigma
+    W = H = 8
+    v, o = 4.0, 0.7
+    sp = _splats_isotropic([(4.0, 4.0), (4.0, 4.0)], [v, v], [0.5 / 255, o], [1.0, 2.0], W, H)
+    c = np.array([[1.0, 1.0, 1.0], [0.2, 0.6, 0.4]])
+    r = oracle.render_splats(sp, c, W, H, pixels=[3 * W + 3])
+    a = o * math.exp(-0.5 * (0.25 + 0.25) / v)
+    np.testing.assert_allclose(r["color"][0], c[1] * a, atol=1e-15)
+    np.testing.assert_allclose(r["T"][0], 1 - a, atol=1e-15)
+    assert r["ncontrib"][0] == 1 and r["blends"][0] == 2
+
+
+def test_clamped_alpha_passes_no_gradient():
+    # at the centre pixel o e^-sigma > 0.99, so C = 0.99 c (+ 0.01 bg) there: C does not move with
+    # the opacity, the mean or the conic (a small change keeps alpha on the clamp), only with c
+    W = H = 8
+    sp = _splats_isotropic([(4.0, 4.0)], [100.0], [0.999], [1.0], W, H)
+    c = np.array([[0.3, 0.5, 0.7]])
+    g = np.array([[0.4, -1.1, 0.9]])
+    f = oracle.render_splats(sp, c, W, H, pixels=[3 * W + 3])
+    np.testing.assert_allclose(f["color"][0], 0.99 * c[0], atol=1e-15)
+    b = oracle.render_splats_bwd(sp, c, W, H, g, pixels=[3 * W + 3])
+    assert np.all(b["d_opacities"] == 0.0) and np.all(b["d_means2d"] == 0.0) and np.all(b["d_conics"] == 0.0)
+    np.testing.assert_allclose(b["d_colors"][0], 0.99 * g[0], atol=1e-15)
+
+
+def test_absgrad_sums_per_pixel_magnitudes():
+    # absgrad (App. A) adds |dL_p/dmu'| pixel by pixel.  One Gaussian (conic I/v), two pixels
+    # mirrored about its centre in x: L = sum_p <g, c> alpha_p, dL_p/dmu'_x = <g, c> alpha_p dx_p / v,
+    # so the signed x gradients cancel while absgrad keeps 2 <g, c> alpha |dx| / v; in y both
+    # pixels pull the same way and the two agree
+    W = H = 8
+    v, o = 3.0, 0.6
+    sp = _splats_isotropic([(4.0, 4.0)], [v], [o], [1.0], W, H)
+    c = np.array([[0.3, 0.5, 0.7]])
+    g = np.array([[0.4, 1.1, 0.9], [0.4, 1.1, 0.9]])
+    b = oracle.render_splats_bwd(sp, c, W, H, g, pixels=[3 * W + 3, 3 * W + 4], want_absgrad=True)
+    a = o * math.exp(-0.5 * (0.25 + 0.25) / v)
+    gc = float(g[0] @ c[0])
+    np.testing.assert_allclose(b["d_means2d"][0, 0], 0.0, atol=1e-15)
+    np.testing.assert_allclose(b["absgrad"][0, 0], 2 * gc * a * 0.5 / v, rtol=1e-13)
+    np.testing.assert_allclose(b["d_means2d"][0, 1], -2 * gc * a * 0.5 / v, rtol=1e-13)
+    np.testing.assert_allclose(b["absgrad"][0, 1], 2 * gc * a * 0.5 / v, rtol=1e-13)
+
+
 def test_partition_of_unity_and_trace_invariants():
     sc, cam = synth.random_small_scene(40, seed=2, width=24, height=20, log_scale_mu=-1.6)
     sp = oracle.project(sc, cam)
@@ -450,6 +514,24 @@ def test_bin_sort_matches_brute_force(tile):
             assert (ranges[t, 0], ranges[t, 1]) == (idx[0], idx[-1] + 1)
         else:
             assert (ranges[t, 0], ranges[t, 1]) == (0, 0)
+
+
+def test_bin_sort_equal_depths_share_tiles_in_index_order():
+    # Gaussians at one spot with one depth fall in the same tiles with the same key; the order
+    # within a tile is then by c N + n ascending (stable emission in index order), against brute force
+    C, N, tile = 1, 12, 8
+    means2d = np.zeros((C, N, 2), np.float32)
+    means2d[0, :] = [13.5, 9.5]
+    means2d[0, ::3] = [30.0, 20.0]
+    depths = np.full((C, N), 1.25, np.float32)
+    depths[0, 7] = 0.75
+    radii = np.full((C, N), 6, np.int32)
+    keys, values, ranges = oracle.bin_sort(means2d, depths, radii, [40], [28], tile)
+    ref, _ = _brute_bins(means2d, depths, radii, np.array([40]), np.array([28]), tile)
+    assert [int(k) for k in keys] == [k for k, _ in ref]
+    assert [int(v) for v in values] == [v for _, v in ref]
+    lo, hi = ranges[(9 // tile) * 5 + 13 // tile]
+    assert [int(v) for v in values[lo:hi]] == [7, 1, 2, 4, 5, 8, 10, 11]
 
 
 def test_render_agrees_with_bins():
