@@ -367,6 +367,32 @@ def test_backward_multi_camera_sums_over_views():
     assert_grad_parity(g_gpu, g_ref)
 
 
+def test_unequal_focal_lengths_and_principal_point():
+    """fx != fy and cx != cy (App. E intrinsics): x must use only fx, cx and y only fy, cy, in
+    the projection, the compositing and the backward."""
+    sc = synth.clustered_scene(8000, 41, sh_degree=3, log_scale_mu=-3.2)
+    base = synth.sphere_cameras(41, [(203, 157)])[0]
+    f32 = lambda v: float(np.float32(v))
+    cam = synth.Camera(base.width, base.height, base.viewmat, f32(base.fx * 1.25), f32(base.fy * 0.8),
+                       f32(base.cx + 9.0), f32(base.cy - 6.0))
+    bg = np.array([0.3, 0.2, 0.1])
+    settings = raster.RasterSettings(background=(0.3, 0.2, 0.1))
+    out, _, _ = gpu_render(sc, [cam], settings=settings)
+    ref_p = oracle.project(sc, cam)
+    both = (out["radii"][0].cpu().numpy() > 0) & (ref_p["radii"] > 0)
+    assert both.sum() > 0.5 * (ref_p["radii"] > 0).sum()
+    np.testing.assert_allclose(out["means2d"][0].cpu().numpy()[both], ref_p["means2d"][both], atol=2e-3, rtol=0)
+    P = cam.width * cam.height
+    ref_f = oracle.render(sc, cam, bg=bg)
+    assert_image_parity(out["image"].cpu().numpy(), ref_f["image"].reshape(P, 3))
+    rng = np.random.default_rng(5)
+    d_img, d_alpha, _ = _masked_upstream(sc, (ref_f["image"].reshape(P, 3), ref_f["alpha"].reshape(P)),
+                                         out["image"].cpu().numpy(), (1 - out["final_T"]).cpu().numpy(), rng, P)
+    g_gpu, _, _ = gpu_grads(sc, [cam], d_img, d_alpha, settings=settings)
+    g_ref = oracle.render_grads(sc, cam, d_img, d_alpha=d_alpha, bg=bg)
+    assert_grad_parity(g_gpu, g_ref)
+
+
 def test_nd_features_forward_and_backward():
     """N-dimensional features instead of SH colour (App. C: c may be any N-vector)."""
     sc, cam = _mid_scene(n=4000, seed=41, deg=0)
