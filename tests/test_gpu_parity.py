@@ -393,6 +393,59 @@ def test_unequal_focal_lengths_and_principal_point():
     assert_grad_parity(g_gpu, g_ref)
 
 
+def _clamp_scene():
+    """A 4 x 4 grid of Gaussians facing an identity camera, boxes disjoint (one layer per pixel).
+    Even ones have o~ = sigmoid(9) ~ 0.9999, so at the pixel 0.1 px from their mean
+    o~ e^-sigma > 0.99 and alpha sits on the clamp; odd ones never reach it.  Every pair stays
+    0.87 % away from the clamp, 1.2e-4 (relative) from the 1/255 skip and 0.1 px from a box edge,
+    far beyond float32 rounding, so the GPU and the oracle take the same decisions."""
+    W = H = 132
+    f, c, z = 80.0, 66.0, 4.0
+    cam = synth.Camera(W, H, np.eye(4, dtype=np.float32), f, f, c, c)
+    gx, gy = np.meshgrid([18.4, 50.4, 82.4, 114.4], [18.4, 50.4, 82.4, 114.4])
+    n = gx.size
+    means = np.stack([(gx.ravel() - c) * z / f, (gy.ravel() - c) * z / f, np.full(n, z)], 1)
+    rng = np.random.default_rng(23)
+    quats = rng.normal(0, 1, (n, 4))
+    quats[:, 0] += 3.0
+    log_scales = np.log(0.15) + rng.normal(0, 0.05, (n, 3))
+    logits = np.where(np.arange(n) % 2 == 0, 9.0, 0.5)
+    sh = rng.normal(0, 0.4, (n, 4, 3))
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    return synth.Scene(f32(means), f32(quats), f32(log_scales), f32(logits), f32(sh), 1), cam
+
+
+def test_clamped_alpha_passes_no_gradient_on_the_gpu():
+    """App. C.2 cap alpha = min(0.99, o~ e^-sigma): where it is active the pixel does not move with
+    the opacity, mean or covariance, so the backward must send nothing through alpha there."""
+    sc, cam = _clamp_scene()
+    bg = np.array([0.3, 0.2, 0.1])
+    settings = raster.RasterSettings(background=(0.3, 0.2, 0.1))
+    ref_f = oracle.render(sc, cam, bg=bg)
+    sp = ref_f["splats"]
+    clamped = 0
+    for n in range(0, sc.n, 2):
+        x, y = (int(v) for v in sp["means2d"][n])
+        _, al, _ = oracle.render_trace(sp, ref_f["colors"], x, y, bg=bg)
+        clamped += int(np.sum(al == 0.99))
+    assert clamped == sc.n // 2
+    P = cam.width * cam.height
+    out, _, _ = gpu_render(sc, [cam], settings=settings)
+    assert_image_parity(out["image"].cpu().numpy(), ref_f["image"].reshape(P, 3))
+    # upstream gradient on the 3 x 3 pixels around each mean, where the clamped pairs weigh most: a
+    # backward that let gradient through the cap would miss the bar by 29x on d_means
+    mask = np.zeros(P, bool)
+    for mx, my in sp["means2d"]:
+        for y in range(int(my) - 1, int(my) + 2):
+            mask[y * cam.width + int(mx) - 1:y * cam.width + int(mx) + 2] = True
+    rng = np.random.default_rng(9)
+    d_img = rng.uniform(-1, 1, (P, 3)) * mask[:, None]
+    d_alpha = rng.uniform(-1, 1, P) * mask
+    g_gpu, _, _ = gpu_grads(sc, [cam], d_img, d_alpha, settings=settings)
+    g_ref = oracle.render_grads(sc, cam, d_img, d_alpha=d_alpha, bg=bg)
+    assert_grad_parity(g_gpu, g_ref)
+
+
 def test_nd_features_forward_and_backward():
     """N-dimensional features instead of SH colour (App. C: c may be any N-vector)."""
     sc, cam = _mid_scene(n=4000, seed=41, deg=0)
