@@ -121,11 +121,29 @@ C_MUTANTS = [
     ("pose_mean_outer_transposed", "double v = dRw[3 * i + j] + dt[i] * means[3 * n + j];",
      "double v = dRw[3 * i + j] + dt[j] * means[3 * n + i];"),
     ("pose_translation_dropped", "d_viewmat[4 * i + 3] += dt[i];", "d_viewmat[4 * i + 3] += 0.0;"),
+    ("camera_translation_dropped",
+     "sp->t[i] = Wr[i * 3 + 0] * mean[0] + Wr[i * 3 + 1] * mean[1] + Wr[i * 3 + 2] * mean[2] + tw[i];",
+     "sp->t[i] = Wr[i * 3 + 0] * mean[0] + Wr[i * 3 + 1] * mean[1] + Wr[i * 3 + 2] * mean[2];"),
+    ("antialias_not_applied", "sp->opac = g->o * sp->comp;", "sp->opac = g->o;"),
+    ("bwd_antialias_half_dropped", "double k = dcomp / (2.0 * sp.comp) / (det1 * det1);",
+     "double k = dcomp / sp.comp / (det1 * det1);"),
+    ("bwd_antialias_wrong_entry", "double ga = k * (c * det1 - det0 * sp.cov[2]);",
+     "double ga = k * (c * det1 - det0 * sp.cov[0]);"),
+    ("pose_sh_rotation_transposed",
+     "double r = viewmat[4 * i] * dv[0] + viewmat[4 * i + 1] * dv[1] + viewmat[4 * i + 2] * dv[2];",
+     "double r = viewmat[i] * dv[0] + viewmat[4 + i] * dv[1] + viewmat[8 + i] * dv[2];"),
+    ("pose_jacobian_transposed", "matmul(Jt, dT, dRw, 3, 2, 3);", "matmul(Jt, dT, dRw, 3, 2, 3);\n"
+     "            for (int i = 0; i < 3; i++) for (int j = 0; j < i; j++) { double u = dRw[3 * i + j]; "
+     "dRw[3 * i + j] = dRw[3 * j + i]; dRw[3 * j + i] = u; }"),
     # binning and sorting (App. C.2)
     ("bins_last_row_dropped", "for (int ty = box[2] / tile; ty <= box[3] / tile; ty++)",
      "for (int ty = box[2] / tile; ty < box[3] / tile; ty++)"),
     ("bins_ties_descending", "return (x->value > y->value) - (x->value < y->value);",
      "return (x->value < y->value) - (x->value > y->value);"),
+    ("ranges_start_off_by_one", "if (j == 0 || (buf[j - 1].key >> 32) != (uint64_t)t) ranges[2 * t] = (int32_t)j;",
+     "if (j == 0 || (buf[j - 1].key >> 32) != (uint64_t)t) ranges[2 * t] = (int32_t)(j + 1);"),
+    ("bins_tile_row_stride", "uint64_t gt = (uint64_t)(offs[c] + ty * tiles_x + tx);",
+     "uint64_t gt = (uint64_t)(offs[c] + ty * (tiles_x - 1) + tx);"),
     ("bins_depth_as_integer", "buf[k].key = (gt << 32) | (uint64_t)f32_bits(depths[i]);",
      "buf[k].key = (gt << 32) | (uint64_t)(uint32_t)depths[i];"),
 ]
