@@ -198,7 +198,7 @@ def outcomes():
         fname = ORACLE_FILES[kind]
         assert original[fname].count(old) == 1, f"{name}: the mutated text must occur exactly once in {fname}"
         jobs[name] = dict(original, **{fname: original[fname].replace(old, new)})
-    with tempfile.TemporaryDirectory() as tmp, ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as pool:
+    with tempfile.TemporaryDirectory() as tmp, ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as pool:
         futs = {name: pool.submit(_run_pins, files, os.path.join(tmp, name)) for name, files in jobs.items()}
         return {name: fut.result() for name, fut in futs.items()}
 
