@@ -79,6 +79,8 @@ C_MUTANTS = [
      "if (T < T_min) break;"),
     ("weight_uses_next_T", "out_col[c] += colors[(size_t)n * ch + c] * a * T;",
      "out_col[c] += colors[(size_t)n * ch + c] * a * Tn;"),
+    ("channels_stride_three", "for (int c = 0; c < ch; c++) out_col[c] += colors[(size_t)n * ch + c] * a * T;",
+     "for (int c = 0; c < ch; c++) out_col[c] += colors[(size_t)n * 3 + c] * a * T;"),
     ("background_not_weighted", "out_col[c] += T * (bg ? bg[c] : 0.0);", "out_col[c] += (bg ? bg[c] : 0.0);"),
     # compositing backward (App. D.2)
     ("bwd_suffix_dropped", "da += g[c] * (cn[c] * T - S[c] / (1.0 - a));", "da += g[c] * (cn[c] * T);"),
