@@ -12,7 +12,7 @@ __all__ = ["synth", "raster", "_lib"]
 
 
 def __getattr__(name):
-    if name in ("raster", "_lib", "batch", "serve", "autotune"):
+    if name in ("raster", "_lib", "pipeline", "serve", "autotune", "scene_io"):
         import importlib
         return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)
