@@ -154,3 +154,21 @@ def test_two_stage_stable_sort_equals_single_key_sort():
     o2 = np.argsort(em_t, kind="stable")
     np.testing.assert_array_equal(em_v[o2], values)
     np.testing.assert_array_equal(em_t[o2], (keys >> np.uint64(32)).astype(np.int64))
+
+
+def test_more_cameras_than_the_maximum_are_rejected():
+    cams = [synth.make_camera(24 + i, 20 + i, (0, 0, 4)) for i in range(_lib.GS_MAX_CAMERAS + 1)]
+    with pytest.raises(ValueError, match="cameras per call"):
+        _lib.CameraArray(cams)
+    _lib.CameraArray(cams[:_lib.GS_MAX_CAMERAS])  # the maximum itself is accepted
+    lib = _lib.load()
+    arr = (_lib.GsCamera * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i].width, arr[i].height, arr[i].fx, arr[i].fy = cam.width, cam.height, cam.fx, cam.fy
+    ptr = ctypes.cast(arr, ctypes.POINTER(_lib.GsCamera))
+    p = _lib.make_params()
+    fake, null = ctypes.c_void_p(256), ctypes.c_void_p(None)
+    assert lib.gs_num_tiles(ptr, len(cams), 16) == -1
+    assert lib.gs_tile_bin_sort_workspace(ptr, len(cams), 10, ctypes.byref(p), 100) == -1
+    assert lib.gs_project(ptr, len(cams), 10, *[fake] * 4, ctypes.byref(p), *[fake] * 6, null) == _lib.GS_ERR_ARG
+    assert b"GS_MAX_CAMERAS" in lib.gs_last_error()
