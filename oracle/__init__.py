@@ -28,11 +28,19 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALPHA_MIN = 1.0 / 255.0
-ALPHA_MAX = 0.99
-T_MIN = 1.0e-4
-EPS2D = 0.3
-NEAR = 0.01
+# Render parameters.  The paper states none of their values (they follow Kerbl et al.: the
+# alpha cap and skip, the transmittance floor, the near plane; App. A gives the 0.3 low-pass).
+# They are inputs of the rasterizer like the Gaussians and cameras, and like those the oracle
+# takes them as the float32 values a caller passes (promoted to float64 unchanged).  The
+# decisions they enter -- culling at the near plane, skipping, clamping, stopping -- then
+# compare against the same thresholds as any float32 implementation: Fig. 1's Gaussian at
+# z = 0.01 renders, and two capped alphas stacked, (1 - alpha_max)^2 < T_min, stop the pixel.
+_f32 = lambda v: float(np.float32(v))
+ALPHA_MIN = _f32(1.0 / 255.0)
+ALPHA_MAX = _f32(0.99)
+T_MIN = _f32(1.0e-4)
+EPS2D = _f32(0.3)
+NEAR = _f32(0.01)
 
 
 def build(force: bool = False) -> str:

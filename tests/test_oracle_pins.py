@@ -96,7 +96,7 @@ def test_isotropic_on_axis_closed_form():
     s, d, f = math.exp(-3.0), 4.0, 64.0
     sc = _scene([[0, 0, 0]], [[1, 0, 0, 0]], [[-3.0] * 3], [0.3], np.zeros((1, 1, 3)))
     p = oracle.project(sc, _axis_cam(d=d, f=f))
-    v = (f * s / d) ** 2 + 0.3
+    v = (f * s / d) ** 2 + oracle.EPS2D
     np.testing.assert_allclose(p["means2d"][0], [32.0, 32.0], atol=1e-12)
     np.testing.assert_allclose(p["depths"][0], d, atol=1e-12)
     np.testing.assert_allclose(p["cov2d"][0], [v, 0.0, v], atol=1e-12)
@@ -114,7 +114,8 @@ def test_off_axis_isotropic_closed_form():
     p = oracle.project(sc, cam)
     np.testing.assert_allclose(p["means2d"][0], [f * x / z + 30.0, f * y / z + 20.0], atol=1e-12)
     k = s * s * f * f / (z * z)
-    expect = [k * (1 + x * x / (z * z)) + 0.3, k * x * y / (z * z), k * (1 + y * y / (z * z)) + 0.3]
+    e = oracle.EPS2D  # the low-pass s (0.3, as the float32 value the rasterizer takes)
+    expect = [k * (1 + x * x / (z * z)) + e, k * x * y / (z * z), k * (1 + y * y / (z * z)) + e]
     np.testing.assert_allclose(p["cov2d"][0], expect, rtol=1e-12)
 
 
@@ -130,8 +131,8 @@ def test_unequal_focal_lengths_and_principal_point_closed_form():
     p = oracle.project(sc, cam)
     np.testing.assert_allclose(p["means2d"][0], [fx * x / z + cx, fy * y / z + cy], rtol=1e-14)
     z4 = z ** 4
-    expect = [s * s * fx * fx * (z * z + x * x) / z4 + 0.3, s * s * fx * fy * x * y / z4,
-              s * s * fy * fy * (z * z + y * y) / z4 + 0.3]
+    expect = [s * s * fx * fx * (z * z + x * x) / z4 + oracle.EPS2D, s * s * fx * fy * x * y / z4,
+              s * s * fy * fy * (z * z + y * y) / z4 + oracle.EPS2D]
     np.testing.assert_allclose(p["cov2d"][0], expect, rtol=1e-12)
 
 
@@ -143,7 +144,7 @@ def test_anisotropic_axis_aligned_and_rotated_90():
     q90 = [math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)]
     sc = _scene([[0, 0, z], [0, 0, z]], [[1, 0, 0, 0], q90], [ls, ls], [0.0, 0.0], np.zeros((2, 1, 3)))
     p = oracle.project(sc, _identity_cam(32, 32, f, 16.0, 16.0))
-    a, b = (f * sx / z) ** 2 + 0.3, (f * sy / z) ** 2 + 0.3
+    a, b = (f * sx / z) ** 2 + oracle.EPS2D, (f * sy / z) ** 2 + oracle.EPS2D
     np.testing.assert_allclose(p["cov2d"][0], [a, 0.0, b], atol=1e-12)
     np.testing.assert_allclose(p["cov2d"][1], [b, 0.0, a], atol=1e-12)
     lam = max(a, b)
@@ -182,7 +183,7 @@ def test_antialiased_compensation_closed_form():
     sc = _scene([[0, 0, 0]], [[1, 0, 0, 0]], [[-3.0] * 3], [1.0], np.zeros((1, 1, 3)))
     p = oracle.project(sc, _axis_cam(d=d, f=f), antialiased=True)
     v0 = (f * s / d) ** 2
-    comp = math.sqrt(v0 * v0 / ((v0 + 0.3) ** 2))  # sqrt(|S|/|S+sI|) for S = v0 I
+    comp = math.sqrt(v0 * v0 / ((v0 + oracle.EPS2D) ** 2))  # sqrt(|S|/|S+sI|) for S = v0 I
     np.testing.assert_allclose(p["opacities"][0], comp / (1 + math.exp(-1.0)), rtol=1e-13)
 
 
@@ -311,9 +312,9 @@ def test_single_gaussian_closed_form():
     for y in range(H):
         for x in range(W):
             dx, dy = x + 0.5 - mx, y + 0.5 - my
-            a = min(0.99, o * math.exp(-0.5 * (dx * dx + dy * dy) / v))
+            a = min(oracle.ALPHA_MAX, o * math.exp(-0.5 * (dx * dx + dy * dy) / v))
             inside = abs(dx) <= rad and abs(dy) <= rad
-            expect = col[0] * a if (inside and a >= 1 / 255) else np.zeros(3)
+            expect = col[0] * a if (inside and a >= oracle.ALPHA_MIN) else np.zeros(3)
             np.testing.assert_allclose(img[y, x], expect, atol=1e-15)
 
 
@@ -341,8 +342,18 @@ def test_background_and_opaque_front():
     c = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     bg = np.array([0.0, 0.0, 1.0])
     r = oracle.render_splats(sp, c, W, H, pixels=[3 * W + 3], bg=bg)
-    a = 0.99  # both clamped: exp(-sigma) ~ 0.9975 > 0.99
-    np.testing.assert_allclose(r["color"][0], [a, a * (1 - a), (1 - a) ** 2], atol=1e-15)
+    # both capped: e^-sigma ~ 0.9975 > alpha_max.  Behind the first, T = 1 - alpha_max; the second
+    # would leave (1 - alpha_max)^2, which is below T_min for the float32 parameters (1 - 0.99 in
+    # float32 is 0.0099999905, squared 9.99998e-5 < 1e-4): it is excluded and the pixel stops
+    a, tmin = oracle.ALPHA_MAX, oracle.T_MIN
+    assert (1 - a) ** 2 < tmin <= 1 - a
+    np.testing.assert_allclose(r["color"][0], [a, 0.0, 1 - a], atol=1e-15)
+    assert r["ncontrib"][0] == 1 and r["blends"][0] == 2
+    # a back Gaussian below the cap is blended behind the capped front one, weight alpha (1 - alpha_max)
+    sp["opacities"] = np.array([1.0, 0.5])
+    r = oracle.render_splats(sp, c, W, H, pixels=[3 * W + 3], bg=bg)
+    a2 = 0.5 * math.exp(-0.5 * (0.25 + 0.25) / 100.0)
+    np.testing.assert_allclose(r["color"][0], [a, a2 * (1 - a), (1 - a) * (1 - a2)], atol=1e-15)
 
 
 def test_transmittance_cutoff_excludes_and_stops():
@@ -393,10 +404,10 @@ def test_clamped_alpha_passes_no_gradient():
     c = np.array([[0.3, 0.5, 0.7]])
     g = np.array([[0.4, -1.1, 0.9]])
     f = oracle.render_splats(sp, c, W, H, pixels=[3 * W + 3])
-    np.testing.assert_allclose(f["color"][0], 0.99 * c[0], atol=1e-15)
+    np.testing.assert_allclose(f["color"][0], oracle.ALPHA_MAX * c[0], atol=1e-15)
     b = oracle.render_splats_bwd(sp, c, W, H, g, pixels=[3 * W + 3])
     assert np.all(b["d_opacities"] == 0.0) and np.all(b["d_means2d"] == 0.0) and np.all(b["d_conics"] == 0.0)
-    np.testing.assert_allclose(b["d_colors"][0], 0.99 * g[0], atol=1e-15)
+    np.testing.assert_allclose(b["d_colors"][0], oracle.ALPHA_MAX * g[0], atol=1e-15)
 
 
 def test_absgrad_sums_per_pixel_magnitudes():
@@ -425,7 +436,7 @@ def test_partition_of_unity_and_trace_invariants():
     r = oracle.render_splats(sp, ones, cam.width, cam.height)
     # sum_n alpha_n T_n + T_final = 1 (telescoping product)
     np.testing.assert_allclose(r["color"][:, 0] + r["T"], 1.0, atol=1e-13)
-    assert np.all(r["T"] >= 1e-4)
+    assert np.all(r["T"] >= oracle.T_MIN)
     checked = 0
     for y in range(0, cam.height, 3):
         for x in range(0, cam.width, 3):
@@ -433,7 +444,7 @@ def test_partition_of_unity_and_trace_invariants():
             if len(ids) == 0:
                 continue
             checked += 1
-            assert np.all(al >= 1 / 255) and np.all(al <= 0.99)
+            assert np.all(al >= oracle.ALPHA_MIN) and np.all(al <= oracle.ALPHA_MAX)
             np.testing.assert_allclose(Ts[1:], Ts[:-1] * (1 - al[:-1]), rtol=1e-13)
             assert np.all(np.diff(sp["depths"][ids]) >= 0)
     assert checked > 10
@@ -459,7 +470,7 @@ def test_fig1_single_gaussian_example():
                                atol=1e-9)
     np.testing.assert_allclose(img, img[::-1, ::-1], atol=1e-14)
     # sigma' = 100 * scale (f=1, z=0.01) plus the 0.3 low-pass
-    v = (scale / 0.01) ** 2 + 0.3
+    v = (scale / 0.01) ** 2 + oracle.EPS2D
     np.testing.assert_allclose(r["splats"]["cov2d"][0], [v, 0.0, v], rtol=1e-12)
 
 
