@@ -1,5 +1,9 @@
-"""Calls at the C ABI's limits, against the oracle: the maximum number of cameras in one call
-(32, uneven and ragged sizes) and the maximum number of feature channels (64)."""
+"""Special cases against the oracle: the paper's Fig. 1 example, and calls at the C ABI's limits
+(the maximum number of cameras in one call, 32 of uneven and ragged sizes, and the maximum number
+of feature channels, 64)."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -11,6 +15,39 @@ from gpu_helpers import assert_grad_parity, assert_image_parity, dev_scene, flip
     rel_l2
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_fig1_example_matches_the_oracle():
+    """Fig. 1: one Gaussian at (0, 0, 0.01), identity pose, f = 1, principal point (120, 120),
+    240 x 240.  Its depth equals the near plane (0.01 in float32 on both sides), which does not
+    cull it; the image is a blob centred on the principal point, the same as the oracle's."""
+    with open(os.path.join(GOLDEN, "fig1_single_gaussian.json")) as fh:
+        g = json.load(fh)
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    scale = g["scale_for_test"]
+    sc = synth.Scene(f32([g["mean"]]), f32([g["quat"]]), f32([[np.log(scale)] * 3]),
+                     f32([g["opacity_logit_for_test"]]), f32(np.ones((1, 1, 3))), 0)
+    K = g["K"]
+    cam = synth.Camera(g["width"], g["height"], np.eye(4, dtype=np.float32), K[0][0], K[1][1], K[0][2], K[1][2])
+    out, _, _ = gpu_render(sc, [cam])
+    ref = oracle.render(sc, cam)
+    P = cam.width * cam.height
+    img = out["image"].cpu().numpy()
+    assert out["radii"][0, 0].item() > 0 and ref["splats"]["radii"][0] > 0
+    assert_image_parity(img, ref["image"].reshape(P, 3))
+    assert_image_parity((1 - out["final_T"]).cpu().numpy()[:, None], ref["alpha"].reshape(P, 1), "alpha")
+    lum = img[:, 0].reshape(cam.height, cam.width)
+    assert lum.max() > 0.5 and lum[119, 119] == lum.max() == lum[120, 120]
+    # backward of a random upstream gradient on the whole image
+    rng = np.random.default_rng(12)
+    d_img = rng.uniform(-1, 1, (P, 3)) / P
+    g_gpu, _, _ = gpu_grads(sc, [cam], d_img)
+    g_ref = oracle.render_grads(sc, cam, d_img)
+    assert_grad_parity(g_gpu, g_ref, keys=("d_means", "d_log_scales", "d_opacity_logits", "d_sh"))
+    # the scale is isotropic, so rotating the Gaussian changes nothing: d_quats is zero up to rounding
+    assert np.abs(g_gpu["d_quats"]).max() <= 1e-3 * np.abs(g_gpu["d_log_scales"]).max()
 
 
 def _sizes32():
