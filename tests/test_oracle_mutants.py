@@ -160,6 +160,8 @@ PY_MUTANTS = [
      "expected = acc"),
     ("expected_depth_grad_alpha_sign", 'gA += -dE * f["expected_depth"] * inv', 'gA += dE * f["expected_depth"] * inv'),
     ("expected_depth_grad_not_scaled", "g4[:, 3] += dE * inv", "g4[:, 3] += dE"),
+    ("near_plane_float64_literal", "NEAR = _f32(0.01)", "NEAR = 0.01"),
+    ("alpha_cap_float64_literal", "ALPHA_MAX = _f32(0.99)", "ALPHA_MAX = 0.99"),
     ("depth_grad_sign", 'd_depths=g2["d_colors"][:, 3]', 'd_depths=-g2["d_colors"][:, 3]'),
 ]
 

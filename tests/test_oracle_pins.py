@@ -472,6 +472,13 @@ def test_fig1_single_gaussian_example():
     # sigma' = 100 * scale (f=1, z=0.01) plus the 0.3 low-pass
     v = (scale / 0.01) ** 2 + oracle.EPS2D
     np.testing.assert_allclose(r["splats"]["cov2d"][0], [v, 0.0, v], rtol=1e-12)
+    # the same example as a caller passes it, in float32: its depth is float32(0.01), the near plane
+    # too, so it is not culled and renders the same blob
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    sc32 = synth.Scene(f32(sc.means), f32(sc.quats), f32(sc.log_scales), f32(sc.opacity_logits), f32(sc.sh), 0)
+    r32 = oracle.render(sc32, cam)
+    assert r32["splats"]["radii"][0] == r["splats"]["radii"][0] > 0
+    np.testing.assert_allclose(r32["image"], r["image"], atol=1e-5)
 
 
 # --------------------------------------------------------------------------- #
