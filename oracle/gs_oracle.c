@@ -178,7 +178,7 @@ static void splat_eval(const gauss3d *g, const double *mean, const double *vm, c
     double disc = m * m - det;
     double lam = m + sqrt(disc > 0.0 ? disc : 0.0);
     double rr = ceil(3.0 * sqrt(lam));
-    if (!(rr > 0.0) || rr > 1.0e9) return;
+    if (!(rr > 0.0) || rr > 1.0e7) return; /* a splat wider than 1e7 pixels is culled */
     sp->radius = (int)rr;
     if (!pixel_box(sp->mu2[0], sp->mu2[1], sp->radius, W, H, sp->box)) {
         sp->radius = 0;

@@ -45,6 +45,7 @@ C_MUTANTS = [
     ("lambda_min_for_max", "double lam = m + sqrt(disc > 0.0 ? disc : 0.0);",
      "double lam = m - sqrt(disc > 0.0 ? disc : 0.0);"),
     ("radius_two_sigma", "double rr = ceil(3.0 * sqrt(lam));", "double rr = ceil(2.0 * sqrt(lam));"),
+    ("radius_cap_raised", "if (!(rr > 0.0) || rr > 1.0e7) return;", "if (!(rr > 0.0) || rr > 1.0e9) return;"),
     ("pixel_box_centre", "double x0 = ceil(mx - (double)r - 0.5), x1 = floor(mx + (double)r - 0.5);",
      "double x0 = ceil(mx - (double)r), x1 = floor(mx + (double)r);"),
     ("near_plane_ignored", "if (!(tz >= near_plane)) return; /* culled */", "if (!(tz > 0.0)) return;"),

@@ -204,6 +204,21 @@ def test_culling_and_pixel_centre_convention():
     assert img[31, 31] == img.max()
 
 
+def test_radius_cap_culls_splats_wider_than_1e7_pixels():
+    # on the optical axis of an identity camera an isotropic Gaussian of scale s at depth z has
+    # Sigma' = ((f s / z)^2 + eps) I, so r = ceil(3 sqrt((f s / z)^2 + eps)).  A splat whose radius
+    # exceeds 1e7 pixels is culled (reading P23); one of about 5e6 pixels is kept, its box clipped
+    f, z = 100.0, 0.02
+    scales = [1333.0, 333.0]
+    sc = _scene([[0, 0, z]] * 2, [[1, 0, 0, 0]] * 2, [[math.log(v)] * 3 for v in scales], [0.0] * 2,
+                np.zeros((2, 1, 3)))
+    p = oracle.project(sc, _identity_cam(64, 64, f, 32.0, 32.0))
+    r = [math.ceil(3 * math.sqrt((f * v / z) ** 2 + oracle.EPS2D)) for v in scales]
+    assert r[0] > 1e7 > r[1] > 1e6
+    assert p["radii"][0] == 0 and p["radii"][1] == r[1]
+    np.testing.assert_array_equal(p["boxes"][1], [0, 63, 0, 63])
+
+
 # --------------------------------------------------------------------------- #
 # spherical harmonics (App. C.1)                                               #
 # --------------------------------------------------------------------------- #
