@@ -127,7 +127,9 @@ def test_projection_gradients_wrt_leaves():
     rng = np.random.default_rng(32)
     N = sc.n
     wm, wc, wo, wd = rng.normal(size=(N, 2)), rng.normal(size=(N, 3)), rng.normal(size=N), rng.normal(size=N)
-    for aa in (False, True):
+    # also a camera with fx != fy and cx != cy, so that every x and y term has its own intrinsics
+    cam2 = synth.Camera(cam.width, cam.height, cam.viewmat, cam.fx * 1.3, cam.fy * 0.8, cam.cx + 2.0, cam.cy - 1.5)
+    for aa, cam in [(False, cam), (True, cam), (False, cam2), (True, cam2)]:
         ana = oracle.project_bwd(sc, cam, wm, wc, wo, d_depths=wd, antialiased=aa)
 
         def L():

@@ -68,6 +68,22 @@ C_MUTANTS = [
      "dY[3 * 11 + 1] = -k3c * (4.0 * z * z - x * x - y * y);"),
     ("sh_bwd_clamp_mask_dropped", "g[ch] = s > 0.0 ? d_colors[3 * n + ch] : 0.0;", "g[ch] = d_colors[3 * n + ch];"),
     ("sh_bwd_direction_projection_dropped", "dv[i] = (ddir[i] - dir[i] * dd) / len;", "dv[i] = ddir[i] / len;"),
+    ("sh_deg2_xy_sign", "Y[4] = k2a * x * y;", "Y[4] = -k2a * x * y;"),
+    ("sh_deg2_m0_term", "Y[6] = k2b * (2.0 * z * z - x * x - y * y);", "Y[6] = k2b * (2.0 * z * z - x * x + y * y);"),
+    ("sh_deg2_xz_index", "Y[7] = -k2a * x * z;", "Y[7] = -k2a * y * z;"),
+    ("sh_deg2_m2_sign", "Y[8] = k2c * (x * x - y * y);", "Y[8] = k2c * (y * y - x * x);"),
+    ("sh_deg3_m_minus3_term", "Y[9] = -k3a * y * (3.0 * x * x - y * y);", "Y[9] = -k3a * y * (x * x - y * y);"),
+    ("sh_deg3_xyz_constant", "Y[10] = k3b * x * y * z;", "Y[10] = k3e * x * y * z;"),
+    ("sh_deg3_m_minus1_index", "Y[11] = -k3c * y * (4.0 * z * z - x * x - y * y);",
+     "Y[11] = -k3c * x * (4.0 * z * z - x * x - y * y);"),
+    ("sh_deg3_m2_index", "Y[14] = k3e * z * (x * x - y * y);", "Y[14] = k3e * y * (x * x - y * y);"),
+    ("sh_deg3_m3_term", "Y[15] = -k3a * x * (x * x - 3.0 * y * y);", "Y[15] = -k3a * x * (x * x - y * y);"),
+    ("sh_grad_deg2_index", "dY[3 * 4 + 0] = k2a * y;", "dY[3 * 4 + 0] = k2a * x;"),
+    ("sh_grad_deg3_factor", "dY[3 * 9 + 0] = -k3a * 6.0 * x * y;", "dY[3 * 9 + 0] = -k3a * 3.0 * x * y;"),
+    ("sh_grad_deg3_last", "dY[3 * 15 + 1] = -k3a * (-6.0 * x * y);", "dY[3 * 15 + 1] = -k3a * (-3.0 * x * y);"),
+    ("sh_grad_deg3_m2_z", "dY[3 * 14 + 2] = k3e * (x * x - y * y);", "dY[3 * 14 + 2] = k3e * (x * x + y * y);"),
+    ("sh_bwd_projection_sign", "double dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];",
+     "double dd = -(dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2]);"),
     # compositing (App. C.2)
     ("depth_order_reversed", "if (da < db) return -1;\n    if (da > db) return 1;",
      "if (da > db) return -1;\n    if (da < db) return 1;"),
@@ -83,6 +99,7 @@ C_MUTANTS = [
     ("channels_stride_three", "for (int c = 0; c < ch; c++) out_col[c] += colors[(size_t)n * ch + c] * a * T;",
      "for (int c = 0; c < ch; c++) out_col[c] += colors[(size_t)n * 3 + c] * a * T;"),
     ("background_not_weighted", "out_col[c] += T * (bg ? bg[c] : 0.0);", "out_col[c] += (bg ? bg[c] : 0.0);"),
+    ("depth_ties_descending_in_compositing", "return (ia > ib) - (ia < ib);", "return (ia < ib) - (ia > ib);"),
     # compositing backward (App. D.2)
     ("bwd_suffix_dropped", "da += g[c] * (cn[c] * T - S[c] / (1.0 - a));", "da += g[c] * (cn[c] * T);"),
     ("bwd_suffix_not_updated", "for (int c = 0; c < ch; c++) S[c] += cn[c] * a * T;", ";"),
@@ -96,6 +113,8 @@ C_MUTANTS = [
     ("bwd_color_weight", "atomic_add(&d_colors[(size_t)n * ch + c], a * T * g[c]);",
      "atomic_add(&d_colors[(size_t)n * ch + c], a * g[c]);"),
     ("bwd_absgrad_signed", "atomic_add(&absgrad[2 * n], fabs(gx));", "atomic_add(&absgrad[2 * n], gx);"),
+    ("bwd_opacity_factor", "double d_o = e->G * da;", "double d_o = da;"),
+    ("bwd_sigma_opacity_dropped", "double d_sigma = -opac[n] * e->G * da;", "double d_sigma = -e->G * da;"),
     # projection backward (App. D.3, D.4)
     ("bwd_inverse_sign", "for (int i = 0; i < 4; i++) G2[i] = -G2[i];", ";"),
     ("bwd_conic_offdiag_not_split", "double dYm[4] = {d_conics[3 * n], 0.5 * d_conics[3 * n + 1], 0.5 * d_conics[3 * n + 1],",
@@ -118,6 +137,15 @@ C_MUTANTS = [
     ("bwd_antialias_term_sign", "double gb = k * (-2.0 * b * det1 + 2.0 * b * det0);",
      "double gb = k * (-2.0 * b * det1 - 2.0 * b * det0);"),
     ("bwd_antialias_compensation_dropped", "double d_o = d_oeff * sp.comp;", "double d_o = d_oeff;"),
+    ("antialias_det_sign", "double det0 = sp->cov0[0] * sp->cov0[2] - sp->cov0[1] * sp->cov0[1];",
+     "double det0 = sp->cov0[0] * sp->cov0[2] + sp->cov0[1] * sp->cov0[1];"),
+    ("bwd_antialias_c_entry", "double gc = k * (a * det1 - det0 * sp.cov[0]);",
+     "double gc = k * (a * det1 - det0 * sp.cov[2]);"),
+    ("bwd_mean2d_y_focal", "dt[1] += gmy * fy / tz;", "dt[1] += gmy * fx / tz;"),
+    ("bwd_jacobian_x_term_sign", "dt[0] += dJ[2] * (-fx / tz2);", "dt[0] += dJ[2] * (fx / tz2);"),
+    ("bwd_dM_transposed", "matmul(dSig, g.M, dM, 3, 3, 3);", "matmul(g.M, dSig, dM, 3, 3, 3);"),
+    ("bwd_scale_rotation_transposed", "for (int i = 0; i < 3; i++) dsj += g.R[i * 3 + j] * dM[i * 3 + j];",
+     "for (int i = 0; i < 3; i++) dsj += g.R[j * 3 + i] * dM[i * 3 + j];"),
     # pose gradients (App. A)
     ("pose_sh_centre_index", "d_viewmat[4 * i + j] += viewmat[4 * i + 3] * dv[j];",
      "d_viewmat[4 * i + j] += viewmat[4 * j + 3] * dv[i];"),
