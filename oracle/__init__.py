@@ -138,6 +138,7 @@ def cov3d(quat, log_scale) -> np.ndarray:
 
 
 def num_threads() -> int:
+    """OpenMP threads the oracle's loops use (reported beside its timings)."""
     return int(_load().orc_num_threads())
 
 
@@ -181,6 +182,8 @@ def project(scene, cam, eps2d=EPS2D, near=NEAR, antialiased=False):
 # --------------------------------------------------------------------------- #
 
 def sh_basis(degree: int, dirs) -> np.ndarray:
+    """Real orthonormal SH basis Y_k(dir), k < (degree+1)^2, at unit directions [P, 3] (App. C.1;
+    the basis and its sign convention are reading P7)."""
     dirs = _d64(dirs).reshape(-1, 3)
     K = (degree + 1) ** 2
     Y = np.zeros((dirs.shape[0], K))
@@ -189,6 +192,7 @@ def sh_basis(degree: int, dirs) -> np.ndarray:
 
 
 def sh_basis_grad(degree: int, dirs) -> np.ndarray:
+    """dY_k/d(x, y, z) of the basis polynomials at unit directions [P, 3] (App. C.1 differentiated)."""
     dirs = _d64(dirs).reshape(-1, 3)
     K = (degree + 1) ** 2
     dY = np.zeros((dirs.shape[0], K, 3))
