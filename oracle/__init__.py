@@ -182,8 +182,8 @@ def project(scene, cam, eps2d=EPS2D, near=NEAR, antialiased=False):
 # --------------------------------------------------------------------------- #
 
 def sh_basis(degree: int, dirs) -> np.ndarray:
-    """Real orthonormal SH basis Y_k(dir), k < (degree+1)^2, at unit directions [P, 3] (App. C.1;
-    the basis and its sign convention are reading P7)."""
+    """Real orthonormal SH basis Y_k(dir), k < (degree+1)^2, at unit directions [P, 3] (App. C.1,
+    which names SH but not the basis: the real harmonics with the Condon-Shortley phase)."""
     dirs = _d64(dirs).reshape(-1, 3)
     K = (degree + 1) ** 2
     Y = np.zeros((dirs.shape[0], K))

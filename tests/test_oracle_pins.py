@@ -207,7 +207,7 @@ def test_culling_and_pixel_centre_convention():
 def test_radius_cap_culls_splats_wider_than_1e7_pixels():
     # on the optical axis of an identity camera an isotropic Gaussian of scale s at depth z has
     # Sigma' = ((f s / z)^2 + eps) I, so r = ceil(3 sqrt((f s / z)^2 + eps)).  A splat whose radius
-    # exceeds 1e7 pixels is culled (reading P23); one of about 5e6 pixels is kept, its box clipped
+    # exceeds 1e7 pixels is culled like an empty one; one of about 5e6 pixels is kept, its box clipped
     f, z = 100.0, 0.02
     scales = [1333.0, 333.0]
     sc = _scene([[0, 0, z]] * 2, [[1, 0, 0, 0]] * 2, [[math.log(v)] * 3 for v in scales], [0.0] * 2,
