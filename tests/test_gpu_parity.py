@@ -7,6 +7,7 @@ import torch
 import oracle
 from paper_2409_06765_gb300 import _lib, raster, synth
 
+import special_scenes
 from gpu_helpers import (IMG_MEANABS, assert_grad_parity, assert_image_parity, dev_scene, flipped_pixels, gpu_grads,
                          gpu_render, image_stats, rel_l2)
 
@@ -393,42 +394,17 @@ def test_unequal_focal_lengths_and_principal_point():
     assert_grad_parity(g_gpu, g_ref)
 
 
-def _clamp_scene():
-    """A 4 x 4 grid of Gaussians facing an identity camera, boxes disjoint (one layer per pixel).
-    Even ones have o~ = sigmoid(9) ~ 0.9999, so at the pixel 0.1 px from their mean
-    o~ e^-sigma > 0.99 and alpha sits on the clamp; odd ones never reach it.  Every pair stays
-    0.87 % away from the clamp, 1.2e-4 (relative) from the 1/255 skip and 0.1 px from a box edge,
-    far beyond float32 rounding, so the GPU and the oracle take the same decisions."""
-    W = H = 132
-    f, c, z = 80.0, 66.0, 4.0
-    cam = synth.Camera(W, H, np.eye(4, dtype=np.float32), f, f, c, c)
-    gx, gy = np.meshgrid([18.4, 50.4, 82.4, 114.4], [18.4, 50.4, 82.4, 114.4])
-    n = gx.size
-    means = np.stack([(gx.ravel() - c) * z / f, (gy.ravel() - c) * z / f, np.full(n, z)], 1)
-    rng = np.random.default_rng(23)
-    quats = rng.normal(0, 1, (n, 4))
-    quats[:, 0] += 3.0
-    log_scales = np.log(0.15) + rng.normal(0, 0.05, (n, 3))
-    logits = np.where(np.arange(n) % 2 == 0, 9.0, 0.5)
-    sh = rng.normal(0, 0.4, (n, 4, 3))
-    f32 = lambda a: np.ascontiguousarray(a, np.float32)
-    return synth.Scene(f32(means), f32(quats), f32(log_scales), f32(logits), f32(sh), 1), cam
-
-
 def test_clamped_alpha_passes_no_gradient_on_the_gpu():
-    """App. C.2 cap alpha = min(0.99, o~ e^-sigma): where it is active the pixel does not move with
+    """App. C.2 cap alpha = min(alpha_max, o~ e^-sigma): where it is active the pixel does not move with
     the opacity, mean or covariance, so the backward must send nothing through alpha there."""
-    sc, cam = _clamp_scene()
+    sc, cam = special_scenes.clamp_scene()
     bg = np.array([0.3, 0.2, 0.1])
     settings = raster.RasterSettings(background=(0.3, 0.2, 0.1))
-    ref_f = oracle.render(sc, cam, bg=bg)
-    sp = ref_f["splats"]
-    clamped = 0
-    for n in range(0, sc.n, 2):
-        x, y = (int(v) for v in sp["means2d"][n])
-        _, al, _ = oracle.render_trace(sp, ref_f["colors"], x, y, bg=bg)
-        clamped += int(np.sum(al == 0.99))
+    # the scene's premise (half of the Gaussians capped at their centre pixel) is a property of
+    # the oracle alone, also checked on the CPU
+    clamped, ref_f = special_scenes.clamped_pairs(oracle, sc, cam, bg)
     assert clamped == sc.n // 2
+    sp = ref_f["splats"]
     P = cam.width * cam.height
     out, _, _ = gpu_render(sc, [cam], settings=settings)
     assert_image_parity(out["image"].cpu().numpy(), ref_f["image"].reshape(P, 3))

@@ -1,9 +1,6 @@
 """Special cases against the oracle: the paper's Fig. 1 example, and calls at the C ABI's limits
 (the maximum number of cameras in one call, 32 of uneven and ragged sizes, and the maximum number
 of feature channels, 64)."""
-import json
-import os
-
 import numpy as np
 import pytest
 import torch
@@ -11,26 +8,18 @@ import torch
 import oracle
 from paper_2409_06765_gb300 import _lib, raster, synth
 
+import special_scenes
 from gpu_helpers import assert_grad_parity, assert_image_parity, dev_scene, flipped_pixels, gpu_grads, gpu_render, \
     rel_l2
 
 pytestmark = pytest.mark.gpu
-
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def test_fig1_example_matches_the_oracle():
     """Fig. 1: one Gaussian at (0, 0, 0.01), identity pose, f = 1, principal point (120, 120),
     240 x 240.  Its depth equals the near plane (0.01 in float32 on both sides), which does not
     cull it; the image is a blob centred on the principal point, the same as the oracle's."""
-    with open(os.path.join(GOLDEN, "fig1_single_gaussian.json")) as fh:
-        g = json.load(fh)
-    f32 = lambda a: np.ascontiguousarray(a, np.float32)
-    scale = g["scale_for_test"]
-    sc = synth.Scene(f32([g["mean"]]), f32([g["quat"]]), f32([[np.log(scale)] * 3]),
-                     f32([g["opacity_logit_for_test"]]), f32(np.ones((1, 1, 3))), 0)
-    K = g["K"]
-    cam = synth.Camera(g["width"], g["height"], np.eye(4, dtype=np.float32), K[0][0], K[1][1], K[0][2], K[1][2])
+    sc, cam = special_scenes.fig1_scene()
     out, _, _ = gpu_render(sc, [cam])
     ref = oracle.render(sc, cam)
     P = cam.width * cam.height
@@ -50,14 +39,9 @@ def test_fig1_example_matches_the_oracle():
     assert np.abs(g_gpu["d_quats"]).max() <= 1e-3 * np.abs(g_gpu["d_log_scales"]).max()
 
 
-def _sizes32():
-    # ragged sizes (none a multiple of the tile) from 23 x 19 to 83 x 65
-    return [(23 + (17 * i) % 61, 19 + (13 * i) % 47) for i in range(_lib.GS_MAX_CAMERAS)]
-
-
 def test_maximum_cameras_in_one_call():
     sc = synth.clustered_scene(3000, 63, sh_degree=1, log_scale_mu=-3.0)
-    cams = synth.sphere_cameras(63, _sizes32())
+    cams = synth.sphere_cameras(63, special_scenes.ragged_sizes(_lib.GS_MAX_CAMERAS))
     out, _, ca = gpu_render(sc, cams)
     img = out["image"].cpu().numpy()
     alpha = 1.0 - out["final_T"].cpu().numpy()
