@@ -820,7 +820,7 @@ def cpu_baseline(scene, cam, target_np, pixels, gauss_sample=100_000, setup=None
             "sample": f"per-Gaussian stages on {G} of {N} Gaussians (x{N / G:.1f}); per-pixel fwd+bwd on {len(pix)} "
                       f"of {P} pixels (seed {seed}), {per_pixel * 1e3:.3f} ms/pixel after a {t_fixed * 1e3:.0f} ms "
                       f"per-call fixed cost, extrapolated linearly",
-            "sample_short": f"{G}/{N} Gaussians, {len(pix)}/{P} px (fwd+bwd), extrapolated",
+            "sample_short": f"{G}/{N} Gaussians, {len(pix)}/{P} px, extrapolated",
             "sample_blends": sample_blends}
 
 
