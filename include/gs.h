@@ -52,6 +52,8 @@ typedef int32_t gs_status;
 
 #define GS_MAX_CAMERAS 32     /* cameras per call */
 #define GS_MAX_CHANNELS 64    /* feature channels per Gaussian */
+#define GS_MAX_INTERSECTIONS 2147483647ll /* (tile, Gaussian) pairs of one gs_tile_bin_sort call: list
+                                             positions (values, tile_ranges) are int32 */
 
 /* Pinhole camera [App. C.1, App. E].  viewmat maps world to camera coordinates
  * (x right, y down, z forward), row-major 4x4; its last row is ignored.  A camera
@@ -121,7 +123,11 @@ GS_API gs_status gs_probe_peak(int32_t kind, int32_t blocks, int32_t iters, floa
 /* R_cw^T J^T + eps2d I, conic = Sigma'^-1, radius r = ceil(3 sqrt(lambda_max)),*/
 /* and the pixel box [ceil(mu'x - r - 0.5), floor(mu'x + r - 0.5)] x (same in */
 /* y) clipped to the image.  A Gaussian is invisible (radius 0, no tiles) if  */
-/* culled or if the box is empty.                                            */
+/* culled or if the box is empty.  Input limit of this library (not a rule   */
+/* of the paper, whose 3-sigma radius has no bound): a splat whose radius    */
+/* would exceed 1e7 pixels is culled too, which keeps the integer box        */
+/* arithmetic (2r) inside int32; such a splat is 4 orders of magnitude wider */
+/* than any image the ABI accepts.                                           */
 /*                                                                          */
 /* in : means [N,3], quats [N,4] (w,x,y,z, any norm > 0), log_scales [N,3],  */
 /*      opacity_logits [N]                                                   */
@@ -192,12 +198,17 @@ GS_API gs_status gs_expected_depth_bwd(int64_t P, const float *image, int32_t ch
 /*      [T,2] int32                                                          */
 /*      ([start, end) into values; (0,0) for an empty tile; T = gs_num_tiles),*/
 /*      keys [K] uint64 (optional, NULL to skip), K_out [1] int64 on the      */
-/*      device = the number of pairs K (-1 if an internal bounded wait timed   */
-/*      out, in which case the lists are invalid; not expected to happen).  When K > K_capacity only the first   */
+/*      device = the number of pairs K.  When K > K_capacity only the first   */
 /*      K_capacity slots are written, the lists are incomplete, and the       */
 /*      caller must reallocate (K_out tells by how much) and call again.      */
+/*      K_capacity above GS_MAX_INTERSECTIONS returns GS_ERR_CAPACITY: such   */
+/*      a list does not fit the int32 positions; split the cameras over       */
+/*      several calls or use a larger tile.                                   */
 /* workspace: device scratch of at least gs_tile_bin_sort_workspace() bytes,  */
-/*      256-byte aligned; its content on entry is ignored.                    */
+/*      256-byte aligned; its content on entry is ignored.  With at most 2048 */
+/*      tiles (one 1080p view at 32x32 tiles) the workspace holds nothing of  */
+/*      size K: about 44 bytes per (camera, Gaussian) pair plus 1.2 bytes per */
+/*      slot of K_capacity.                                                  */
 /* ------------------------------------------------------------------------ */
 GS_API int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                                    int64_t K_capacity);
@@ -224,6 +235,9 @@ GS_API gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, c
 /* capture.  All calls share the array: calls that overlap on the GPU (other */
 /* streams, other host threads) race on it and must be serialised.  Nothing  */
 /* in it needs clearing between calls.  Nothing is allocated by this call.   */
+/* The looked-up address is cached per device ordinal for the life of the    */
+/* process: it is not valid after cudaDeviceReset or in a context other than */
+/* the device's primary context, so do not call this entry point there.     */
 /* ------------------------------------------------------------------------ */
 #define GS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,

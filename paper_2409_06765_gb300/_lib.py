@@ -23,6 +23,7 @@ GS_ERR_CAPACITY = -3
 GS_ERR_UNSUPPORTED = -5
 GS_MAX_CAMERAS = 32
 GS_MAX_CHANNELS = 64
+GS_MAX_INTERSECTIONS = 2**31 - 1  # (tile, Gaussian) pairs of one gs_tile_bin_sort call (int32 positions)
 
 EXPORTED = (
     "gs_default_params", "gs_status_string", "gs_last_error", "gs_num_tiles", "gs_num_pixels", "gs_project",
@@ -269,6 +270,9 @@ def gs_sh_eval(cams: CameraArray, sh_degree: int, sh, means, radii, colors, stre
 
 
 def gs_tile_bin_sort_workspace(cams: CameraArray, N: int, params: GsParams, K_capacity: int) -> int:
+    if int(K_capacity) > GS_MAX_INTERSECTIONS:
+        raise GsError(GS_ERR_CAPACITY, "gs_tile_bin_sort_workspace",
+                      f"{int(K_capacity)} intersections exceed GS_MAX_INTERSECTIONS (int32 list positions)")
     n = int(load().gs_tile_bin_sort_workspace(cams.ptr, cams.C, N, ctypes.byref(params), int(K_capacity)))
     if n < 0:
         raise GsError(GS_ERR_ARG, "gs_tile_bin_sort_workspace", "invalid sizes")

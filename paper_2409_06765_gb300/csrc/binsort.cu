@@ -3,56 +3,71 @@
 // The canonical result is the list of (tile, Gaussian) pairs ordered by the 64-bit key
 // (global_tile << 32) | float_bits(depth), ties by flat index c*N + n.  Instead of one
 // radix sort over K 64-bit keys, the same order is reached in two stable stages:
-//   1. a 32-bit LSD radix sort of the C*N (camera, Gaussian) pairs by depth bits
-//      (invisible pairs get key 0xFFFFFFFF, sort last and emit nothing);
-//   2. emission of every pair's tiles in that depth order, followed by a stable LSD
-//      radix sort of the K intersections by tile id alone (ceil(log2 T) bits, in passes
-//      of at most 7 bits so each digit's run of a sorted block is long).
+//   1. a stable LSD radix sort of the C*N (camera, Gaussian) pairs by the 32 depth bits, in
+//      three passes of at most 11 bits.  The first pass also drops the pairs that touch no
+//      pixel (key 0xFFFFFFFF), so the later passes and stage 2 see only the visible ones;
+//   2. the K intersections in that depth order, sorted stably by tile id alone.  A pair's
+//      intersections are the tiles of its tile rectangle, so the list of "slots" in depth
+//      order is defined by the pairs' tile counts and rectangles; it is never written out.
+//      When the tile ids fit one digit of at most 11 bits (up to 2048 tiles: one 1080p view
+//      at 32x32 tiles), a single counting pass regenerates every slot from the pair table,
+//      once to count and once to place, and writes only the final values: no K-sized
+//      intermediate key or value array exists.  More tiles take further LSD passes over
+//      materialised (tile, value) arrays.
 // Stability carries the depth order (and the index tie-break) into each tile's list.
 //
-// Each LSD pass is a reduce-then-scan over blocks of 4096 items: a histogram kernel
-// writes every block's digit counts into a digit-major matrix, two small kernels turn the
-// matrix into each (digit, block) pair's global start, and a persistent scatter kernel
-// ranks each block stably in shared memory (atomic-OR peer masks within a warp, warp
-// prefixes across the CTA), reorders it by digit in place and stores each digit's run
-// contiguously.  The scatter streams its blocks into shared memory with 1-D bulk copies
-// (TMA) double-buffered behind an mbarrier, so the next block is in flight while the
-// current one is ranked.  No CTA waits on another CTA; the only waits are on the CTA's
-// own bulk copies, and they are bounded (a timeout raises an error flag that the call
-// reports as K_out = -1).
+// Every pass is reduce-then-scan over blocks of items (4096 for the depth passes, 16384
+// for the tile passes): a histogram kernel writes each block's digit counts into a
+// digit-major matrix (and adds the digit totals), a scan kernel turns the matrix into each
+// (digit, block)'s global start, and a rank kernel places the block.  The rank kernel
+// gives each of its 16 warps a contiguous segment of the block: the warps first count
+// their digits into per-warp 16-bit counters (shared atomics), the CTA turns the counters
+// into per-warp prefixes, and each warp then walks its segment in order, ranking 32 items
+// at a time with match.any (the lanes holding the same digit), so equal digits keep their
+// input order.  No CTA waits on another CTA and nothing waits on the device.
 //
-// Emission is balanced by output slot, not by pair: the output is cut into chunks of
-// 1024 slots, a pass over the pairs records which pair starts each chunk, and a CTA
-// fills a chunk with every thread writing 4 consecutive slots (staged through shared
-// memory so the global stores are contiguous).  Pairs that cover thousands of tiles (big
-// Gaussians close to the camera, all at the front of the depth order) therefore cost
-// no more than many small ones.
-//
-// Every kernel reads the data-dependent counts (K) from device memory, so the host never
-// synchronises and the whole call can be captured in a CUDA graph.
+// Every kernel reads the data-dependent counts (visible pairs, K) from device memory, so
+// the host never synchronises and the whole call can be captured in a CUDA graph.
 #include <stdlib.h>
 
 #include "gs_internal.cuh"
 
 namespace gs {
 
-constexpr int kRadix = 256;
-constexpr int kSortThreads = 256;        // histogram CTA (== kRadix)
-constexpr int kSortIPT = 16;             // items per histogram thread
-constexpr int kSortBlock = kSortThreads * kSortIPT;  // items per block of a pass
-constexpr int kChunk = 1024;             // emission chunk (output slots)
-constexpr int kEmitThreads = 256;
-constexpr int kSlotsPerThread = kChunk / kEmitThreads;
-static_assert(kSlotsPerThread == 4, "emission stores a thread's slots as one 16-byte store");
-constexpr long long kWaitSpins = 1ll << 22;  // bound on a wait for a bulk copy
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxDigits = 1 << kMaxDigitBits;
+constexpr int kDepthWarps = 16;                         // warps of a depth-pass CTA
+constexpr int kDepthSeg = 256;                          // items per warp segment, depth passes
+constexpr int kDepthBlock = kDepthWarps * kDepthSeg;    // 4096
+#ifndef GS_TILE_WARPS
+#define GS_TILE_WARPS 16
+#endif
+#ifndef GS_TILE_STAGE
+#define GS_TILE_STAGE 0
+#endif
+#ifndef GS_DEPTH_STAGE
+#define GS_DEPTH_STAGE 0
+#endif
+constexpr int kTileWarps = GS_TILE_WARPS;               // warps of a tile-pass CTA
+constexpr int kTileSeg = 1024;                          // slots per warp segment, tile passes
+constexpr int kTileBlock = kTileWarps * kTileSeg;
+constexpr bool kTileStage = GS_TILE_STAGE;              // tile passes keep their items in shared memory
+constexpr bool kDepthStage = GS_DEPTH_STAGE;            // depth passes keep their items in shared memory
+#ifndef GS_DEPTH_DIGIT_BITS
+#define GS_DEPTH_DIGIT_BITS 8
+#endif
+constexpr int kDepthDigitBits = GS_DEPTH_DIGIT_BITS;    // digit width of the depth passes
+constexpr int kDepthPasses = (32 + kDepthDigitBits - 1) / kDepthDigitBits;
+constexpr int kMaxTilePasses = 3;                       // up to 2^28 tiles (the ABI's limit)
+constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
+constexpr int kPeerDigits = 256;  // digits up to which the rank kernel ranks by peer masks
 
 // misc region layout (ints)
-constexpr int kMiscNeff = 0;
-constexpr int kMiscErr = 1;
-constexpr int kMiscRowsum = 64;                // [kMaxPasses][kRadix] digit totals of every pass
-constexpr int kMaxPasses = 8;                  // 4 depth passes + up to 4 tile passes
-constexpr int kFusedRowsumCols = 1024;         // passes of up to this many blocks sum digits by atomics
-constexpr int kMiscInts = kMiscRowsum + kMaxPasses * kRadix;
+constexpr int kMiscNeff = 0;   // slots actually emitted: min(K, capacity)
+constexpr int kMiscNvis = 2;   // visible pairs (depth keys other than 0xFFFFFFFF)
+constexpr int kMiscRowsum = 64;                         // [kMaxPasses][kMaxDigits] digit totals
+constexpr int kMiscInts = kMiscRowsum + kMaxPasses * kMaxDigits;
+constexpr unsigned kInvisible = 0xffffffffu;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -85,37 +100,32 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int &total, int *s_tm
     return wpre + inc - x;
 }
 
-// ---------------------------------------------------------------------------
-// small helpers
-// ---------------------------------------------------------------------------
-
 __global__ void zero_ints_kernel(int n, int *__restrict__ p) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) p[t] = 0;
 }
 
-__global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restrict__ n_eff) {
+__global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restrict__ misc) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *K_out = 0;
-        *n_eff = 0;
+        misc[kMiscNeff] = 0;
+        misc[kMiscNvis] = 0;
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // stage 1 keys
 // ---------------------------------------------------------------------------
 
 // Depth key of every (camera, Gaussian) pair.  A pair that touches no pixel (radius 0, or
-// a pixel box that is empty after clipping to the image) gets 0xFFFFFFFF and so sorts
-// after every pair with tiles: in depth order, every pair before the first such key has at
-// least one tile, which the emission relies on.
+// a pixel box that is empty after clipping to the image) gets 0xFFFFFFFF; the first depth
+// pass drops those, so every pair that reaches stage 2 has at least one tile.
 __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __grid_constant__ CamSet cs,
                                                          const float2 *__restrict__ means2d,
                                                          const float *__restrict__ depths,
                                                          const int *__restrict__ radii, uint32_t *__restrict__ keys,
                                                          int *__restrict__ vals, int *__restrict__ misc) {
-    if (blockIdx.x == 0)  // the sort's counters, digit totals and error flag start at zero
-        for (int i = threadIdx.x; i < kMiscInts; i += blockDim.x) misc[i] = 0;
+    // the sort's counters and digit totals start at zero (spread over the grid)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMiscInts; i += gridDim.x * blockDim.x) misc[i] = 0;
     // four consecutive pairs per thread: 16-byte loads of radii, depths and means, 16-byte stores
     const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= CN) return;
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
                 int x0, x1, y0, y1;
                 ok = pixel_box(mm[u].x, mm[u].y, rr[u], cam.W, cam.H, x0, x1, y0, y1);
             }
-            k[u] = ok ? __float_as_uint(dd[u]) : 0xffffffffu;
+            k[u] = ok ? __float_as_uint(dd[u]) : kInvisible;
         }
         *reinterpret_cast<uint4 *>(keys + i0) = make_uint4(k[0], k[1], k[2], k[3]);
         *reinterpret_cast<int4 *>(vals + i0) = make_int4(i0, i0 + 1, i0 + 2, i0 + 3);
@@ -154,378 +164,429 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
             int x0, x1, y0, y1;
             ok = pixel_box(m.x, m.y, r, cam.W, cam.H, x0, x1, y0, y1);
         }
-        keys[i] = ok ? __float_as_uint(depths[i]) : 0xffffffffu;
+        keys[i] = ok ? __float_as_uint(depths[i]) : kInvisible;
         vals[i] = i;
     }
 }
 
 // ---------------------------------------------------------------------------
-// one stable LSD pass as reduce-then-scan: no CTA waits on another
+// item sources of a pass: an array of (key, value), or the slots of the pair table
 // ---------------------------------------------------------------------------
 
-// Digit counts of every kSortBlock-item block: hist[d * cols + b] (digit-major), and, when
-// rowsum is given, the pass's digit totals rowsum[d] by atomic adds (zeroed before the sort;
-// used for passes of few blocks, where the adds to one counter do not queue up).
-__global__ void __launch_bounds__(kSortThreads) block_hist_kernel(const uint32_t *__restrict__ keys,
-                                                                const int *__restrict__ n_dev, int n_host, int shift,
-                                                                int bits, int cols, int *__restrict__ hist,
-                                                                int *__restrict__ rowsum) {
-    constexpr int W = kSortThreads / 32;
-    __shared__ int s_h[W][kRadix];
-    const int warp = threadIdx.x >> 5;
-    const int n = n_dev ? *n_dev : n_host;
-    const int b = blockIdx.x;
-    const int t0 = b * kSortBlock;
-    if (t0 >= n) return;  // uniform
-    for (int i = threadIdx.x; i < W * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    const unsigned mask = (1u << bits) - 1u;
-    const int end = min(n, t0 + kSortBlock);
-    uint4 q[kSortIPT / 4];  // all loads in flight before the first atomic
+// A source hands out its items in windows of 32 (one per lane).  The loads of a group of G
+// windows are issued together (load_group) before any of them is decoded (decode), so each
+// warp keeps several windows' memory requests in flight instead of waiting for one at a time.
+// Item indices are below 2^31 (C*N < 2^31 and K_capacity <= GS_MAX_INTERSECTIONS).
+
+// Items [w0, w0 + 32) of a (key, value) array; `want_val` skips the value loads.
+struct ArraySrc {
+    static constexpr int G = 8;
+    static constexpr bool kPairRank = false;
+    const uint32_t *keys;
+    const int *vals;
+    struct Raw {
+        uint32_t key;
+        int val;
+    };
+    __device__ __forceinline__ void load_group(int w0, int n, int lane, bool want_val, Raw (&r)[G]) const {
 #pragma unroll
-    for (int r = 0; r < kSortIPT / 4; ++r) {
-        const int i0 = t0 + (r * kSortThreads + threadIdx.x) * 4;  // 16-byte aligned: keys are 256-byte aligned
-        if (i0 + 3 < end) {
-            q[r] = *reinterpret_cast<const uint4 *>(keys + i0);
-        } else {
-            q[r].x = i0 + 0 < end ? keys[i0 + 0] : 0u;
-            q[r].y = i0 + 1 < end ? keys[i0 + 1] : 0u;
-            q[r].z = i0 + 2 < end ? keys[i0 + 2] : 0u;
-            q[r].w = i0 + 3 < end ? keys[i0 + 3] : 0u;
+        for (int g = 0; g < G; ++g) {
+            const int q = w0 + 32 * g + lane;
+            r[g].key = q < n ? keys[q] : kInvisible;
+            r[g].val = (q < n && want_val) ? vals[q] : 0;
         }
     }
+    // (every lane is its own pair: the ranking by pairs is not used with this source)
+    __device__ __forceinline__ void decode(const Raw &r, int w0, int n, int lane, bool &valid, uint32_t &key,
+                                           int &val, int &pair) const {
+        valid = w0 + lane < n;
+        key = r.key;
+        val = r.val;
+        pair = lane;
+    }
+};
+
+// Slots [w0, w0 + 32) of the intersection list in depth order (w0 a multiple of 32).  Pair j
+// (in depth order, j < npairs) owns slots [off_j, off_j + count_j) and covers a rectangle of
+// tiles; slot k of the pair is the rectangle's tile k in row-major order.  The pair table
+// holds one 16-byte record per pair: (off_j, global id of the first tile, rectangle width |
+// tiles per camera row << 16, flat index c*N + n).  Per window w: win_start[w] is the pair
+// holding slot 32 w, and bit b of win_bits[w] is set when a pair starts at slot 32 w + b
+// (b >= 1).  The lane of slot 32 w + l belongs to pair win_start[w] + `pair`, with `pair` the
+// number of bits set in 1..l; it loads that pair's record itself.  `pair` numbers the pairs of
+// the window in slot order; a pair's slots are distinct tiles, so when the digit is the whole
+// tile id, lanes of one pair never share a digit.
+struct EmitSrc {
+    static constexpr int G = 4;
+    static constexpr bool kPairRank = true;
+    const int4 *pairs;
+    const int *win_start;
+    const unsigned *win_bits;
+    struct Raw {
+        int4 rec;
+        unsigned bits;
+    };
+    __device__ __forceinline__ void load_group(int w0, int n, int lane, bool want_val, Raw (&r)[G]) const {
+        (void)want_val;
+        int pc[G];
 #pragma unroll
-    for (int r = 0; r < kSortIPT / 4; ++r) {
-        const int i0 = t0 + (r * kSortThreads + threadIdx.x) * 4;
-        if (i0 + 0 < end) atomicAdd(&s_h[warp][(q[r].x >> shift) & mask], 1);
-        if (i0 + 1 < end) atomicAdd(&s_h[warp][(q[r].y >> shift) & mask], 1);
-        if (i0 + 2 < end) atomicAdd(&s_h[warp][(q[r].z >> shift) & mask], 1);
-        if (i0 + 3 < end) atomicAdd(&s_h[warp][(q[r].w >> shift) & mask], 1);
+        for (int g = 0; g < G; ++g) {
+            const int wg = w0 + 32 * g;
+            const bool in = wg < n;
+            pc[g] = in ? win_start[wg >> 5] : 0;
+            r[g].bits = in ? win_bits[wg >> 5] : 0u;
+        }
+        const unsigned le = 0xffffffffu >> (31 - lane);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const bool in = w0 + 32 * g + lane < n;
+            r[g].rec = in ? pairs[pc[g] + __popc(r[g].bits & le)] : make_int4(0, 0, 1, 0);
+        }
+    }
+    __device__ __forceinline__ void decode(const Raw &r, int w0, int n, int lane, bool &valid, uint32_t &key,
+                                           int &val, int &pair) const {
+        pair = __popc(r.bits & (0xffffffffu >> (31 - lane)));
+        val = r.rec.w;
+        valid = w0 + lane < n;
+        const int k = valid ? w0 + lane - r.rec.x : 0;  // slot of the pair: row-major in its rectangle
+        const int w = max(r.rec.z & 0xffff, 1), tx = r.rec.z >> 16;
+        // k / w from an approximate reciprocal, made exact by integer steps (a few at most)
+        int ky = __float2int_rz(((float)k + 0.5f) * rcp_approx((float)w));
+        int kx = k - ky * w;
+        while (kx < 0) {
+            --ky;
+            kx += w;
+        }
+        while (kx >= w) {
+            ++ky;
+            kx -= w;
+        }
+        key = valid ? (uint32_t)(r.rec.y + ky * tx + kx) : kInvisible;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// one stable LSD pass: histogram, scan, rank + place (no CTA waits on another)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int pass_items(const int *n_dev, int n_host) { return n_dev ? *n_dev : n_host; }
+
+// Digit counts of every block of WARPS * SEG items: hist[d * cols + b] (digit-major), and the
+// pass's digit totals rowsum[d] by atomic adds (zeroed before the sort).  With `drop`, items
+// whose key is 0xFFFFFFFF are left out, and the number of items kept is added to *n_kept
+// (zeroed before the sort).
+template <class Src, int WARPS, int SEG>
+__global__ void __launch_bounds__(32 * WARPS) rank_hist_kernel(const Src src, const int *__restrict__ n_dev,
+                                                             int n_host, int shift, int bits, int cols,
+                                                             int *__restrict__ hist, int *__restrict__ rowsum,
+                                                             int drop, int *__restrict__ n_kept) {
+    constexpr int NT = 32 * WARPS;
+    __shared__ int s_h[kMaxDigits];
+    __shared__ int s_kept;
+    const int n = pass_items(n_dev, n_host);
+    const int b = blockIdx.x;
+    const int t0 = b * (WARPS * SEG);
+    if (t0 >= n) return;  // uniform
+    const int nd = 1 << bits;
+    const unsigned mask = (unsigned)nd - 1u;
+    for (int d = threadIdx.x; d < nd; d += NT) s_h[d] = 0;
+    if (threadIdx.x == 0) s_kept = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = t0 + warp * SEG;
+    const int s1 = min(s0 + SEG, n);
+    int kept = 0;
+    for (int w0 = s0; w0 < s1; w0 += 32 * Src::G) {
+        typename Src::Raw raw[Src::G];
+        src.load_group(w0, s1, lane, false, raw);
+#pragma unroll
+        for (int g = 0; g < Src::G; ++g) {
+            const int wg = w0 + 32 * g;
+            if (wg >= s1) break;  // uniform over the warp
+            bool valid;
+            uint32_t key;
+            int val, pair;
+            src.decode(raw[g], wg, s1, lane, valid, key, val, pair);
+            if (drop && key == kInvisible) valid = false;
+            if (valid) {
+                atomicAdd(&s_h[(key >> shift) & mask], 1);
+                ++kept;
+            }
+        }
+    }
+    if (drop) {
+        kept = __reduce_add_sync(0xffffffffu, kept);
+        if (lane == 0 && kept) atomicAdd(&s_kept, kept);
     }
     __syncthreads();
-    const int d = threadIdx.x;  // kSortThreads == kRadix
-    int c = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) c += s_h[w][d];
-    hist[(size_t)d * cols + b] = c;
-    if (rowsum && c) atomicAdd(&rowsum[d], c);
-}
-
-// Row sums of the digit-major count matrix over its first nb = ceil(n / kSortBlock) columns.
-__global__ void __launch_bounds__(kSortThreads) hist_rowsum_kernel(const int *__restrict__ n_dev, int n_host, int cols,
-                                                                 const int *__restrict__ hist, int *__restrict__ rowsum) {
-    __shared__ int s_tmp[8];
-    const int n = n_dev ? *n_dev : n_host;
-    const int nb = (n + kSortBlock - 1) / kSortBlock;
-    const int *row = hist + (size_t)blockIdx.x * cols;
-    int s = 0;
-    for (int b = threadIdx.x; b < nb; b += kSortThreads) s += row[b];
-    int tot;
-    block_exclusive_scan(s, tot, s_tmp);
-    if (threadIdx.x == 0) rowsum[blockIdx.x] = tot;
+    for (int d = threadIdx.x; d < nd; d += NT) {
+        const int c = s_h[d];
+        hist[(size_t)d * cols + b] = c;
+        if (c) atomicAdd(&rowsum[d], c);
+    }
+    if (drop && threadIdx.x == 0 && s_kept) atomicAdd(n_kept, s_kept);
 }
 
 // hist[d * cols + b] <- global start of digit d for block b:
-// sum_{d' < d} rowsum[d'] + sum_{b' < b} hist[d * cols + b'].
-// Rows of up to 256 * MAXSEG blocks: every thread loads its whole segment into registers (all
-// loads in flight at once) and rewrites it from there.
+// sum_{d' < d} rowsum[d'] + sum_{b' < b} hist[d * cols + b'].  One CTA per digit; rows of up
+// to 256 * MAXSEG blocks are loaded into registers (all loads in flight at once).  With
+// `ranges` (a single tile pass, where digits are tiles), digit d < T also gets its tile range
+// (start, end), or (0, 0) when empty.
 template <int MAXSEG>
-__global__ void __launch_bounds__(kSortThreads) hist_scan_reg_kernel(const int *__restrict__ n_dev, int n_host,
-                                                                   int cols, const int *__restrict__ rowsum,
-                                                                   int *__restrict__ hist) {
+__global__ void __launch_bounds__(256) rank_scan_kernel(const int *__restrict__ n_dev, int n_host,
+                                                        int block_items, int cols, const int *__restrict__ rowsum,
+                                                        int *__restrict__ hist, int2 *__restrict__ ranges, int T) {
     __shared__ int s_tmp[8];
-    const int n = n_dev ? *n_dev : n_host;
-    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int n = pass_items(n_dev, n_host);
+    const int nb = (int)(((long long)n + block_items - 1) / block_items);
     const int d = blockIdx.x;
-    int *row = hist + (size_t)d * cols;
-    const int seg = (nb + kSortThreads - 1) / kSortThreads;  // <= MAXSEG (checked by the host)
-    const int b0 = threadIdx.x * seg, b1 = min(nb, b0 + seg);
-    int v[MAXSEG];
+    // start of digit d: the digit totals below d (kMaxDigits / 256 = 8 per thread)
+    int pre = 0;
 #pragma unroll
-    for (int k = 0; k < MAXSEG; ++k) v[k] = b0 + k < b1 ? row[b0 + k] : 0;
-    const int pre = threadIdx.x < d ? rowsum[threadIdx.x] : 0;
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < MAXSEG; ++k) s += v[k];
-    int base, tot;
-    block_exclusive_scan(pre, base, s_tmp);
-    int run = base + block_exclusive_scan(s, tot, s_tmp);
-#pragma unroll
-    for (int k = 0; k < MAXSEG; ++k) {
-        if (b0 + k < b1) row[b0 + k] = run;
-        run += v[k];
+    for (int k = 0; k < kMaxDigits / 256; ++k) {
+        const int e = threadIdx.x * (kMaxDigits / 256) + k;
+        pre += e < d ? rowsum[e] : 0;
     }
-}
-
-__global__ void __launch_bounds__(kSortThreads) hist_scan_kernel(const int *__restrict__ n_dev, int n_host, int cols,
-                                                               const int *__restrict__ rowsum, int *__restrict__ hist) {
-    __shared__ int s_tmp[8];
-    const int n = n_dev ? *n_dev : n_host;
-    const int nb = (n + kSortBlock - 1) / kSortBlock;
-    const int d = blockIdx.x;
     int base;
-    block_exclusive_scan(threadIdx.x < d ? rowsum[threadIdx.x] : 0, base, s_tmp);
+    block_exclusive_scan(pre, base, s_tmp);
+    if (ranges && d < T && threadIdx.x == 0) {
+        const int c = rowsum[d];
+        ranges[d] = c ? make_int2(base, base + c) : make_int2(0, 0);
+    }
     int *row = hist + (size_t)d * cols;
-    // each thread scans a contiguous segment of the row
-    const int seg = (nb + kSortThreads - 1) / kSortThreads;
+    const int seg = (nb + 255) / 256;
     const int b0 = threadIdx.x * seg, b1 = min(nb, b0 + seg);
-    int s = 0;
-    for (int b = b0; b < b1; ++b) s += row[b];
-    int tot;
-    int run = base + block_exclusive_scan(s, tot, s_tmp);
-    for (int b = b0; b < b1; ++b) {
-        const int v = row[b];
-        row[b] = run;
-        run += v;
+    if (seg <= MAXSEG) {
+        int v[MAXSEG > 0 ? MAXSEG : 1];
+#pragma unroll
+        for (int k = 0; k < MAXSEG; ++k) v[k] = b0 + k < b1 ? row[b0 + k] : 0;
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < MAXSEG; ++k) s += v[k];
+        int tot;
+        int run = base + block_exclusive_scan(s, tot, s_tmp);
+#pragma unroll
+        for (int k = 0; k < MAXSEG; ++k) {
+            if (b0 + k < b1) row[b0 + k] = run;
+            run += v[k];
+        }
+    } else {
+        int s = 0;
+        for (int bb = b0; bb < b1; ++bb) s += row[bb];
+        int tot;
+        int run = base + block_exclusive_scan(s, tot, s_tmp);
+        for (int bb = b0; bb < b1; ++bb) {
+            const int v = row[bb];
+            row[bb] = run;
+            run += v;
+        }
     }
 }
 
-// --- bulk copies (TMA, 1-D) into shared memory with mbarrier completion -------------
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+// Shared memory of the rank kernel for a block of `block` items and nd digits: the staged
+// keys and values, per-warp 16-bit digit counters, the block's digit starts, and (for digits
+// up to kPeerDigits, when not ranking by pairs) per-warp peer masks.
+__host__ __device__ constexpr size_t rank_smem_bytes(int block, int warps, int nd, bool peers, bool stage) {
+    return (stage ? (size_t)block * 8 : 0) + (size_t)warps * nd * 2 + (size_t)nd * 4 +
+           (peers ? (size_t)warps * kPeerDigits * 4 : 0);
 }
 
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for a bulk copy; false (and the error flag raised) when the copy never lands.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, int *err) {
-    for (long long it = 0; it < kWaitSpins; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-    }
-    atomicExch(err, 1);
-    return false;
-}
-
-constexpr int kTmaThreads = 512;
-constexpr int kTmaWarps = kTmaThreads / 32;
-constexpr int kTmaIPT = kSortBlock / kTmaThreads;  // items per scatter thread
-constexpr size_t kTmaSmem = 2ull * kSortBlock * 8          // double-buffered keys + values (reordered in place)
-                            + 2ull * kTmaWarps * kRadix * 4  // per-warp digit counts, per-warp peer masks
-                            + 2ull * kRadix * 4              // local starts, shifts
-                            + 128;                           // barriers, scratch
-
-// Stable scatter of one pass by persistent CTAs (two per SM): the next block's keys and
-// values are bulk-copied into the other shared-memory buffer while the current block is
-// ranked and stored, so DRAM latency hides behind the ranking instead of stalling it.
-// The ranked block is reordered by digit into its own input buffer (the items are held in
-// registers across the barrier), so each CTA needs no separate reorder buffer.
-__global__ void __launch_bounds__(kTmaThreads, 2) scatter_tma_kernel(const uint32_t *__restrict__ keys_in,
-                                                                     const int *__restrict__ vals_in,
-                                                                     uint32_t *__restrict__ keys_out,
-                                                                     int *__restrict__ vals_out,
-                                                                     const int *__restrict__ n_dev, int n_host,
-                                                                     int shift, int bits, int cols,
-                                                                     const int *__restrict__ hist,
-                                                                     int *__restrict__ err) {
-    constexpr int W = kTmaWarps;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint32_t *s_in_k = reinterpret_cast<uint32_t *>(smem);              // [2][kSortBlock]
-    int *s_in_v = reinterpret_cast<int *>(s_in_k + 2 * kSortBlock);      // [2][kSortBlock]
-    int(*s_warp)[kRadix] = reinterpret_cast<int(*)[kRadix]>(s_in_v + 2 * kSortBlock);
-    unsigned(*s_peer)[kRadix] = reinterpret_cast<unsigned(*)[kRadix]>(&s_warp[W][0]);
-    int *s_local = reinterpret_cast<int *>(&s_peer[W][0]);
-    int *s_shift = s_local + kRadix;
-    unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(s_shift + kRadix);  // [2]
-    int *s_tmp = reinterpret_cast<int *>(s_bar + 2);                                       // [W]
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = n_dev ? *n_dev : n_host;
-    const int nb = (n + kSortBlock - 1) / kSortBlock;
-    const unsigned mask = (1u << bits) - 1u;
-    if (blockIdx.x >= nb) return;  // uniform
-    if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// Stable placement of one block.  (i) every warp counts its segment's digits into its own
+// 16-bit counters (with STAGE it also keeps the items, loaded or generated once, in shared
+// memory; without, it loads or generates them again in (iii), which keeps more CTAs resident);
+// (ii) the counters become per-warp prefixes; (iii) every warp walks its segment in order and
+// ranks 32 items at a time among equal digits -- by the window's pairs (whole tile ids as
+// digits), by peer masks (up to kPeerDigits digits) or by match.any -- and writes each item to
+// its final position.
+template <class Src, int WARPS, int SEG, bool STAGE>
+__global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src, const int *__restrict__ n_dev,
+                                                                int n_host, int shift, int bits, int cols,
+                                                                const int *__restrict__ hist,
+                                                                uint32_t *__restrict__ keys_out,
+                                                                int *__restrict__ vals_out, int drop,
+                                                                int pair_rank) {
+    constexpr int NT = 32 * WARPS;
+    constexpr int BLOCK = WARPS * SEG;
+    static_assert(SEG % (32 * 8) == 0 && WARPS % 8 == 0 && BLOCK <= 65535,
+                  "per-warp 16-bit counters, cleared 16 bytes at a time; groups of up to 8 windows");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = pass_items(n_dev, n_host);
+    const int b = blockIdx.x;
+    const int t0 = b * BLOCK;
+    if (t0 >= n) return;  // uniform
+    const int nd = 1 << bits;
+    const unsigned mask = (unsigned)nd - 1u;
+    const bool by_pairs = Src::kPairRank && pair_rank;
+    const bool by_peers = !by_pairs && nd <= kPeerDigits;
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(smem);                     // [BLOCK] (STAGE)
+    int *s_val = reinterpret_cast<int *>(s_key + (STAGE ? BLOCK : 0));        // [BLOCK] (STAGE)
+    unsigned short *s_c16 = reinterpret_cast<unsigned short *>(s_val + (STAGE ? BLOCK : 0));  // [WARPS][nd]
+    unsigned *s_c32 = reinterpret_cast<unsigned *>(s_c16);
+    int *s_start = reinterpret_cast<int *>(s_c16 + WARPS * nd);                // [nd]
+    unsigned *s_peer = reinterpret_cast<unsigned *>(s_start + nd);             // [WARPS][kPeerDigits]
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(s_c16);
+        for (int i = threadIdx.x; i < WARPS * nd / 8; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int d = threadIdx.x; d < nd; d += NT) s_start[d] = hist[(size_t)d * cols + b];
+        if (by_peers)
+            for (int i = threadIdx.x; i < WARPS * kPeerDigits; i += NT) s_peer[i] = 0u;
     }
     __syncthreads();
-    // issue the bulk copies of block `blk` into buffer `buf` (thread 0); the ragged tail of
-    // the last block (fewer than 4 items past a 16-byte boundary) is loaded after the wait
-    auto issue = [&](int blk, int buf) {
-        const int t0 = blk * kSortBlock;
-        const int items = min(kSortBlock, n - t0);
-        const unsigned bytes = (unsigned)(items & ~3) * 4u;
-        mbar_expect_tx(&s_bar[buf], 2u * bytes);
-        if (bytes) {
-            bulk_g2s(s_in_k + buf * kSortBlock, keys_in + t0, bytes, &s_bar[buf]);
-            bulk_g2s(s_in_v + buf * kSortBlock, vals_in + t0, bytes, &s_bar[buf]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = t0 + warp * SEG;
+    const int s1 = min(s0 + SEG, n);
+    unsigned short *my = s_c16 + warp * nd;
+    // (i) stage the segment and count its digits per warp (staged key: the key, or with
+    // by_pairs the tile id | window pair << 16; 0xFFFFFFFF for an item that is not kept)
+    for (int w0 = s0; w0 < s1; w0 += 32 * Src::G) {
+        typename Src::Raw raw[Src::G];
+        src.load_group(w0, s1, lane, STAGE, raw);
+#pragma unroll
+        for (int g = 0; g < Src::G; ++g) {
+            const int wg = w0 + 32 * g;
+            if (wg >= s1) break;  // uniform over the warp
+            bool valid;
+            uint32_t key;
+            int val, pair;
+            src.decode(raw[g], wg, s1, lane, valid, key, val, pair);
+            if (drop && key == kInvisible) valid = false;
+            const int li = wg - t0 + lane;
+            if (STAGE && wg + lane < s1) {
+                s_key[li] = !valid ? kInvisible : (by_pairs ? (key | ((uint32_t)pair << 16)) : key);
+                s_val[li] = val;
+            }
+            if (valid) {
+                const int c = warp * nd + (int)((key >> shift) & mask);
+                atomicAdd(&s_c32[c >> 1], 1u << ((c & 1) * 16));
+            }
         }
-    };
-    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    }
+    __syncthreads();
+    // (ii) counters -> exclusive prefixes over the warps (warp w's items of digit d come after
+    // those of warps < w)
+    for (int d = threadIdx.x; d < nd; d += NT) {
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const int c = s_c16[w * nd + d];
+            s_c16[w * nd + d] = (unsigned short)run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // (iii) each warp walks its segment in order
     const unsigned lt = lanemask_lt();
-    int it = 0;
-    for (int blk = blockIdx.x; blk < nb; blk += gridDim.x, ++it) {
-        const int buf = it & 1;
-        const int t0 = blk * kSortBlock;
-        const int items = min(kSortBlock, n - t0);
-        // prefetch the next block into the other buffer: the previous iteration ended with a
-        // proxy fence by every thread and a CTA barrier after its last access to that buffer
-        const int next = blk + gridDim.x;
-        if (threadIdx.x == 0 && next < nb) issue(next, buf ^ 1);
-        for (int i = threadIdx.x; i < W * kRadix; i += kTmaThreads) {
-            (&s_warp[0][0])[i] = 0;
-            if (it == 0) (&s_peer[0][0])[i] = 0u;  // the ranking leaves every peer mask at zero again
-        }
-        const bool landed = mbar_wait_bounded(&s_bar[buf], (unsigned)(it >> 1) & 1u, err);
-        uint32_t *ik = s_in_k + buf * kSortBlock;
-        int *iv = s_in_v + buf * kSortBlock;
-        // ragged tail (< 4 items) with plain loads
-        const int body = items & ~3;
-        if (threadIdx.x < items - body) {
-            ik[body + threadIdx.x] = keys_in[t0 + body + threadIdx.x];
-            iv[body + threadIdx.x] = vals_in[t0 + body + threadIdx.x];
-        }
-        if (!__syncthreads_and(landed)) {
-            // a copy never arrived: give up on this CTA's remaining blocks (the error flag is set);
-            // wait, bounded, for the copy still in flight before shared memory is released
-            if (threadIdx.x == 0 && next < nb) mbar_wait_bounded(&s_bar[buf ^ 1], (unsigned)((it + 1) >> 1) & 1u, err);
-            return;
-        }
-        // stable rank inside each warp (warp w owns items [w*32*kTmaIPT, (w+1)*32*kTmaIPT))
-        uint32_t kk[kTmaIPT];
-        int vv[kTmaIPT], rank[kTmaIPT];
+    for (int w0 = s0; w0 < s1; w0 += 32 * Src::G) {
+      typename Src::Raw raw[Src::G];
+      if (!STAGE) src.load_group(w0, s1, lane, true, raw);
 #pragma unroll
-        for (int j = 0; j < kTmaIPT; ++j) {
-            const int li = warp * 32 * kTmaIPT + j * 32 + lane;
-            const bool ok = li < items;
-            kk[j] = ok ? ik[li] : 0u;
-            vv[j] = ok ? iv[li] : 0;
-            const unsigned d = ok ? ((kk[j] >> shift) & mask) : 0u;
-            if (ok) atomicOr(&s_peer[warp][d], 1u << lane);
-            __syncwarp();
-            const unsigned peers = ok ? s_peer[warp][d] : 0u;
-            const int before = ok ? s_warp[warp][d] : 0;
-            __syncwarp();
-            if (ok && (__ffs(peers) - 1) == lane) {
-                s_warp[warp][d] = before + __popc(peers);
-                s_peer[warp][d] = 0u;
-            }
-            rank[j] = before + __popc(peers & lt);
-            __syncwarp();
+      for (int g = 0; g < Src::G; ++g) {
+        const int wg = w0 + 32 * g;
+        if (wg >= s1) break;  // uniform over the warp
+        uint32_t sk;
+        int val;
+        if (STAGE) {
+            const int li = wg - t0 + lane;
+            const bool inside = wg + lane < s1;
+            sk = inside ? s_key[li] : kInvisible;
+            val = inside ? s_val[li] : 0;
+        } else {
+            bool v;
+            uint32_t k;
+            int pair;
+            src.decode(raw[g], wg, s1, lane, v, k, val, pair);
+            if (drop && k == kInvisible) v = false;
+            sk = !v ? kInvisible : (by_pairs ? (k | ((uint32_t)pair << 16)) : k);
         }
-        __syncthreads();
-        {
-            const int d = threadIdx.x;
-            int run = 0;
-            if (d < kRadix) {
-                int c[W];  // all W counts in flight before the prefix is written back
-#pragma unroll
-                for (int w = 0; w < W; ++w) c[w] = s_warp[w][d];
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    s_warp[w][d] = run;
-                    run += c[w];
+        const bool valid = sk != kInvisible;
+        uint32_t key;
+        unsigned d;
+        int rank;
+        if (by_pairs) {
+            // the window's pairs one after the other: lanes of one pair hold distinct tiles
+            key = sk & 0xffffu;
+            d = key & mask;
+            const int pair = valid ? (int)(sk >> 16) : 0;
+            const int npair = __reduce_max_sync(0xffffffffu, pair) + 1;
+            rank = 0;
+            for (int p = 0; p < npair; ++p) {
+                if (valid && pair == p) {
+                    rank = my[d];
+                    my[d] = (unsigned short)(rank + 1);
                 }
+                __syncwarp();
             }
-            int tot;
-            const int local = block_exclusive_scan<kTmaThreads>(run, tot, s_tmp);
-            if (d < kRadix) {
-                s_local[d] = local;
-                s_shift[d] = hist[(size_t)d * cols + blk] - local;
+        } else if (by_peers) {
+            key = sk;
+            d = (key >> shift) & mask;
+            unsigned *pm = s_peer + warp * kPeerDigits + d;
+            if (valid) atomicOr(pm, 1u << lane);
+            __syncwarp();
+            const unsigned peers = valid ? *pm : 0u;
+            const int before = valid ? (int)my[d] : 0;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) {
+                my[d] = (unsigned short)(before + __popc(peers));
+                *pm = 0u;  // left at zero for the next window
+            }
+            __syncwarp();
+            rank = before + __popc(peers & lt);
+        } else {
+            key = sk;
+            d = valid ? ((key >> shift) & mask) : (0x10000u + lane);  // invalid lanes match no one
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int before = valid ? (int)my[d] : 0;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) my[d] = (unsigned short)(before + __popc(peers));
+            __syncwarp();
+            rank = before + __popc(peers & lt);
+        }
+        if (valid) {
+            const int pos = s_start[d] + rank;
+            if ((unsigned)pos < (unsigned)n) {  // holds by construction
+                if (keys_out) keys_out[pos] = key;
+                vals_out[pos] = val;
             }
         }
-        __syncthreads();
-        // every item of the block is in registers: reorder by digit into the input buffer
-#pragma unroll
-        for (int j = 0; j < kTmaIPT; ++j) {
-            const int li = warp * 32 * kTmaIPT + j * 32 + lane;
-            if (li < items) {
-                const unsigned d = (kk[j] >> shift) & mask;
-                const int lp = s_local[d] + s_warp[warp][d] + rank[j];
-                if ((unsigned)lp < (unsigned)kSortBlock) {  // holds by construction
-                    ik[lp] = kk[j];
-                    iv[lp] = vv[j];
-                }
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < items; i += kTmaThreads) {
-            const uint32_t k = ik[i];
-            const int pos = i + s_shift[(k >> shift) & mask];
-            if ((unsigned)pos < (unsigned)n) {  // holds by construction; guards the scatter
-                keys_out[pos] = k;
-                vals_out[pos] = iv[i];
-            }
-        }
-        // order this iteration's generic-proxy accesses to the buffer before the bulk copy
-        // that refills it two iterations on
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+      }
     }
 }
 
 // ---------------------------------------------------------------------------
-// stage 2: tile counts, offsets, chunk starts, balanced emission
+// stage 2: tile counts, offsets and window starts of the visible pairs in depth order
 // ---------------------------------------------------------------------------
-
-// Tile rectangle of pair i from its radius r and 2D mean m (false when it touches no tile).
-__device__ __forceinline__ bool tile_rect_of(const CamSet &cs, int N, int i, int r, float2 m, int &c, int &tx0,
-                                             int &tx1, int &ty0, int &ty1) {
-    if ((unsigned)i >= (unsigned)(cs.C * N) || r <= 0) return false;
-    c = i / N;
-    const CamDev &cam = cs.cam[c];
-    int x0, x1, y0, y1;
-    if (!pixel_box(m.x, m.y, r, cam.W, cam.H, x0, x1, y0, y1)) return false;
-    const int t = cs.tile;
-    tx0 = x0 / t;
-    tx1 = x1 / t;
-    ty0 = y0 / t;
-    ty1 = y1 / t;
-    return true;
-}
 
 constexpr int kPairsPerThread = 4;                            // consecutive pairs per thread
 constexpr int kPairsPerCta = 256 * kPairsPerThread;           // pairs per CTA of the count/offset kernels
 
-// Tiles touched by each pair, in depth order, their sum per CTA, and each pair's tile
-// rectangle packed as (tx0 | ty0 << 16, width | camera << 16) for the emission.  A thread
-// owns kPairsPerThread consecutive pairs: all their indices, then all their radii and means
-// are requested before any is used, so the two dependent gathers overlap.
+// Tiles touched by each visible pair, in depth order, their sum per CTA, and each pair's tile
+// rectangle packed as (global id of its first tile, width | tiles per camera row << 16).  A
+// thread owns kPairsPerThread consecutive pairs: all their indices, then all their radii and
+// means are requested before any is used, so the two dependent gathers overlap.  Also zeroes
+// the tile ranges when a later pass fills only the non-empty ones.
 __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, int *__restrict__ tile_ranges,
+                                                          int nwin, unsigned *__restrict__ win_bits,
                                                           const __grid_constant__ CamSet cs,
-                                                          const int *__restrict__ order,
+                                                          const int *__restrict__ order, const int *__restrict__ nvis,
                                                           const float2 *__restrict__ means2d,
                                                           const int *__restrict__ radii, int *__restrict__ counts,
                                                           int2 *__restrict__ rects, long long *__restrict__ partials) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * T; i += gridDim.x * blockDim.x)
-        tile_ranges[i] = 0;  // empty tiles read (0, 0); the ranges kernel fills the others later
+    if (tile_ranges)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * T; i += gridDim.x * blockDim.x)
+            tile_ranges[i] = 0;  // empty tiles read (0, 0); the ranges kernel fills the others later
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nwin; i += gridDim.x * blockDim.x)
+        win_bits[i] = 0u;  // the offsets kernel ORs in the pair starts
     __shared__ long long s_w[8];
+    const int nv = *nvis;
     const int j0 = blockIdx.x * kPairsPerCta + threadIdx.x * kPairsPerThread;
     int id[kPairsPerThread], r[kPairsPerThread];
     float2 m[kPairsPerThread];
-    if (j0 + kPairsPerThread <= CN) {  // j0 is a multiple of 4 and order 16-byte aligned
+    if (j0 + kPairsPerThread <= nv) {  // j0 is a multiple of 4 and order 16-byte aligned
         const int4 v = *reinterpret_cast<const int4 *>(order + j0);
         id[0] = v.x, id[1] = v.y, id[2] = v.z, id[3] = v.w;
     } else {
 #pragma unroll
-        for (int u = 0; u < kPairsPerThread; ++u) id[u] = j0 + u < CN ? order[j0 + u] : -1;
+        for (int u = 0; u < kPairsPerThread; ++u) id[u] = j0 + u < nv ? order[j0 + u] : -1;
     }
 #pragma unroll
     for (int u = 0; u < kPairsPerThread; ++u) {
@@ -537,10 +598,19 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, 
     int2 rc[kPairsPerThread];
 #pragma unroll
     for (int u = 0; u < kPairsPerThread; ++u) {
-        int c = 0, tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
-        const bool ok = tile_rect_of(cs, N, id[u], r[u], m[u], c, tx0, tx1, ty0, ty1);
-        cnt[u] = ok ? (tx1 - tx0 + 1) * (ty1 - ty0 + 1) : 0;
-        rc[u] = make_int2(tx0 | (ty0 << 16), (ok ? tx1 - tx0 + 1 : 1) | (c << 16));
+        cnt[u] = 0;
+        rc[u] = make_int2(0, 1);
+        if ((unsigned)id[u] < (unsigned)CN && r[u] > 0) {
+            const int c = id[u] / N;
+            const CamDev &cam = cs.cam[c];
+            int x0, x1, y0, y1;
+            if (pixel_box(m[u].x, m[u].y, r[u], cam.W, cam.H, x0, x1, y0, y1)) {
+                const int t = cs.tile;
+                const int tx0 = x0 / t, tx1 = x1 / t, ty0 = y0 / t, ty1 = y1 / t;
+                cnt[u] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+                rc[u] = make_int2(cam.tile_offset + ty0 * cam.tiles_x + tx0, (tx1 - tx0 + 1) | (cam.tiles_x << 16));
+            }
+        }
     }
     if (j0 + kPairsPerThread <= CN) {
         *reinterpret_cast<int4 *>(counts + j0) = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -571,7 +641,7 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, 
 // thread rewrites its segment from its exclusive start (one pass, no per-round barriers).
 __global__ void __launch_bounds__(1024) partial_scan_kernel(int G, long long *__restrict__ partials,
                                                             long long capacity, long long *__restrict__ K_out,
-                                                            int *__restrict__ n_eff) {
+                                                            int *__restrict__ misc) {
     __shared__ long long s_w[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = (G + 1023) / 1024;
@@ -599,19 +669,23 @@ __global__ void __launch_bounds__(1024) partial_scan_kernel(int G, long long *__
     }
     if (threadIdx.x == 0) {
         *K_out = tot;
-        *n_eff = (int)(tot < capacity ? tot : capacity);
+        misc[kMiscNeff] = (int)(tot < capacity ? tot : capacity);
     }
 }
 
-// Exclusive offsets of every pair, and for each emission chunk the pair holding its first
-// slot (chunk_start[c] = j when c * kChunk falls in [offsets[j], offsets[j] + counts[j])).
+// Exclusive slot offsets of every visible pair, written with the pair's tile rectangle and
+// flat index as one 16-byte record (offsets clamped to n_eff, below 2^31), and for each window
+// of 32 slots the pair holding its first slot (win_start[w] = j when 32 w falls in
+// [off_j, off_j + count_j)).
 __global__ void __launch_bounds__(256) offsets_kernel(int CN, const int *__restrict__ counts,
+                                                      const int2 *__restrict__ rects, const int *__restrict__ order,
                                                       const long long *__restrict__ partials,
-                                                      const int *__restrict__ n_eff, long long *__restrict__ offsets,
-                                                      int *__restrict__ chunk_start) {
+                                                      const int *__restrict__ misc, int4 *__restrict__ pairs,
+                                                      int *__restrict__ win_start, unsigned *__restrict__ win_bits) {
     __shared__ long long s_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j0 = blockIdx.x * kPairsPerCta + threadIdx.x * kPairsPerThread;
+    const int nv = misc[kMiscNvis];
     int cnt[kPairsPerThread];
     if (j0 + kPairsPerThread <= CN) {
         const int4 v = *reinterpret_cast<const int4 *>(counts + j0);
@@ -632,124 +706,41 @@ __global__ void __launch_bounds__(256) offsets_kernel(int CN, const int *__restr
     long long wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_w[w];
     long long off = partials[blockIdx.x] + wpre + x - mine;
-    const long long limit = *n_eff;
+    const long long limit = misc[kMiscNeff];
 #pragma unroll
     for (int u = 0; u < kPairsPerThread; ++u) {
         const int j = j0 + u;
-        if (j >= CN) break;
-        offsets[j] = off;
+        if (j >= nv) break;
+        const int2 rc = rects[j];
+        pairs[j] = make_int4((int)min(off, limit), rc.x, rc.y, order[j]);
         if (cnt[u] > 0 && off < limit) {
             const long long end = min(off + cnt[u], limit);
-            for (long long c = (off + kChunk - 1) / kChunk; c * kChunk < end; ++c) chunk_start[c] = j;
+            for (long long w = (off + 31) >> 5; (w << 5) < end; ++w) win_start[w] = j;
+            if (off & 31) atomicOr(&win_bits[off >> 5], 1u << (off & 31));  // starts inside a window
         }
         off += cnt[u];
     }
 }
 
-// Balanced emission of (tile id, pair index) in depth order into [0, n_eff).
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(
-    int CN, const __grid_constant__ CamSet cs, const int *__restrict__ order, const int2 *__restrict__ rects,
-    const long long *__restrict__ offsets, const int *__restrict__ chunk_start, const int *__restrict__ n_eff,
-    uint32_t *__restrict__ tkeys, int *__restrict__ tvals) {
-    // at most one pair per slot: every pair before the first tile-less one has >= 1 tile, and
-    // tile-less pairs (offset n_eff or beyond) are never inside a chunk
-    constexpr int P = kChunk;
-    __shared__ int s_off[P + 1];  // first slot of each pair, relative to the chunk
-    __shared__ int s_base[P];     // global tile id of the rectangle's first tile
-    __shared__ int s_wt[P];       // rectangle width | the camera's tiles per row << 16
-    __shared__ int s_id[P];
-    const int n = *n_eff;
-    const int nchunks = (n + kChunk - 1) / kChunk;
-    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {  // normally one chunk per CTA
-        const long long k0 = (long long)ch * kChunk;
-        const int len = (int)min((long long)kChunk, n - k0);
-        const int j0 = chunk_start[ch];
-        // the pairs of this chunk: j0, j0 + 1, ... while their first slot is inside the chunk
-        // (offsets are non-decreasing, so they form a prefix and a count gives their number);
-        // they end at the pair holding the next chunk's first slot, so only those are read
-        const int j_end = (ch + 1 < nchunks) ? chunk_start[ch + 1] : CN - 1;
-        const int cand = min(P, j_end - j0 + 1);
-        int np = 0;
-        for (int s0 = 0; s0 < cand; s0 += kEmitThreads) {
-            const int s = s0 + threadIdx.x;
-            const int j = j0 + s;
-            const long long off = (j < CN) ? offsets[j] : (1ll << 62);
-            const bool in = off < k0 + len;
-            if (in) {
-                const int2 rc = rects[j];
-                const CamDev &cam = cs.cam[rc.y >> 16];
-                s_off[s] = (int)(off - k0);  // negative for the pair that straddles into the chunk
-                s_base[s] = cam.tile_offset + (rc.x >> 16) * cam.tiles_x + (rc.x & 0xffff);
-                s_wt[s] = (rc.y & 0xffff) | (cam.tiles_x << 16);
-                s_id[s] = order[j];
-            }
-            np += __syncthreads_count(in);
-        }
-        if (threadIdx.x == 0) s_off[np] = 1 << 30;
-        __syncthreads();
-        // each thread fills kSlotsPerThread consecutive slots and stores them as one 16-byte
-        // store per array (consecutive threads, consecutive 16-byte pieces)
-        const int q0 = threadIdx.x * kSlotsPerThread;
-        if (q0 < len) {
-            int lo = 0, hi = np - 1;  // last pair whose first slot is <= q0
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= q0) lo = mid;
-                else hi = mid - 1;
-            }
-            int p = lo;
-            // position (kx, ky) of slot q0 in its pair's tile rectangle: one division, then the
-            // following slots step through the rectangle (a new pair starts at its corner)
-            int w = s_wt[p] & 0xffff, tx = s_wt[p] >> 16;
-            const int kk = q0 - s_off[p];
-            const int ky = kk / w;
-            int kx = kk - ky * w;
-            int tile = s_base[p] + ky * tx + kx;
-            uint32_t key[kSlotsPerThread];
-            int val[kSlotsPerThread];
-#pragma unroll
-            for (int u = 0; u < kSlotsPerThread; ++u) {
-                const int q = q0 + u;
-                if (u > 0 && q < len) {
-                    if (q >= s_off[p + 1]) {
-                        while (q >= s_off[p + 1]) ++p;
-                        w = s_wt[p] & 0xffff;
-                        tx = s_wt[p] >> 16;
-                        kx = 0;
-                        tile = s_base[p];
-                    } else if (++kx == w) {
-                        kx = 0;
-                        tile += tx - w + 1;  // first tile of the next row of the rectangle
-                    } else {
-                        ++tile;
-                    }
-                }
-                key[u] = (uint32_t)tile;
-                val[u] = s_id[p];
-            }
-            if (q0 + kSlotsPerThread <= len) {  // k0 and q0 are multiples of 4: 16-byte aligned
-                *reinterpret_cast<uint4 *>(tkeys + k0 + q0) = make_uint4(key[0], key[1], key[2], key[3]);
-                *reinterpret_cast<int4 *>(tvals + k0 + q0) = make_int4(val[0], val[1], val[2], val[3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < kSlotsPerThread; ++u)
-                    if (q0 + u < len) {
-                        tkeys[k0 + q0 + u] = key[u];
-                        tvals[k0 + q0 + u] = val[u];
-                    }
-            }
-        }
-        __syncthreads();  // the next chunk reuses the shared arrays
+// 64-bit keys (tile << 32 | depth bits) of the sorted list, from the tile ranges and values:
+// one warp per tile (only when the caller asks for the keys).
+__global__ void __launch_bounds__(256) keys64_kernel(int T, int CN, const int2 *__restrict__ ranges,
+                                                     const int *__restrict__ vals, const float *__restrict__ depths,
+                                                     unsigned long long *__restrict__ keys64) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= T) return;
+    const int2 r = ranges[t];
+    for (int p = r.x + (threadIdx.x & 31); p < r.y; p += 32) {
+        const int v = vals[p];
+        keys64[p] = ((unsigned long long)t << 32) | ((unsigned)v < (unsigned)CN ? __float_as_uint(depths[v]) : 0u);
     }
 }
 
-// Tile boundaries of the sorted list; each thread looks at 4 consecutive entries.
+// Tile boundaries of a list sorted by materialised tile keys (the passes of more than 2048
+// tiles); each thread looks at 4 consecutive entries.
 __global__ void ranges_kernel(const int *__restrict__ n_dev, int T, int CN, const uint32_t *__restrict__ tkeys,
                               const int *__restrict__ vals, const float *__restrict__ depths,
-                              int2 *__restrict__ ranges, unsigned long long *__restrict__ keys64,
-                              const int *__restrict__ err, long long *__restrict__ K_out) {
-    // a timed-out bulk-copy wait in any pass (never expected) is reported through K_out
-    if (blockIdx.x == 0 && threadIdx.x == 0 && *err) *K_out = -1;
+                              int2 *__restrict__ ranges, unsigned long long *__restrict__ keys64) {
     const int n = *n_dev;
     const int nq = (n + 3) / 4;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -835,16 +826,15 @@ cudaError_t launch_tile_order(int T, const int *tile_ranges, int *order, cudaStr
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int sort_grid_blocks();  // defined in gs_abi.cu (4 CTAs per SM of the current device)
-
 static int tile_bits(long long T) {
     int b = 1;
     while ((1ll << b) < T) ++b;
     return b;
 }
 
-BinSortLayout binsort_layout(long long CN, long long Kcap, int G) {
-    (void)G;
+static int tile_passes(long long T) { return (tile_bits(T) + kMaxDigitBits - 1) / kMaxDigitBits; }
+
+BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
     BinSortLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -852,54 +842,59 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, int G) {
         o += align256(bytes);
         return at;
     };
-    const long long cnb = (CN + 255) / 256;
-    const long long max_items = CN > Kcap ? CN : Kcap;
-    const long long cols = (max_items + kSortBlock - 1) / kSortBlock;
+    const long long cnb = (CN + kPairsPerCta - 1) / kPairsPerCta;
+    const long long cols_d = (CN + kDepthBlock - 1) / kDepthBlock;
+    const long long cols_t = (Kcap + kTileBlock - 1) / kTileBlock;
+    const long long cols = cols_d > cols_t ? cols_d : cols_t;
     L.dk0 = take(CN * 4);
     L.dk1 = take(CN * 4);
     L.dv0 = take(CN * 4);
     L.dv1 = take(CN * 4);
     L.counts = take(CN * 4);
     L.rects = take(CN * 8);
-    L.offsets = take(CN * 8);
-    L.chunk_start = take(((Kcap + kChunk - 1) / kChunk + 1) * 4);
+    L.offsets = take(CN * 16);  // one 16-byte record per visible pair
+    L.win_start = take(((Kcap + 31) / 32 + 1) * 4);
+    L.win_bits = take(((Kcap + 31) / 32 + 1) * 4);
     L.partials = take((size_t)(cnb + 1) * 8);
     L.misc = take((size_t)kMiscInts * 4);
-    L.matrix = take((size_t)(cols > 0 ? cols : 1) * kRadix * 4);
-    L.tk0 = take(Kcap * 4);
-    L.tk1 = take(Kcap * 4);
-    L.tvB = take(Kcap * 4);
+    L.matrix = take((size_t)(cols > 0 ? cols : 1) * kMaxDigits * 4);
+    // (tile, value) arrays of the list exist only when the tile ids need more than one pass
+    const bool multi = tile_passes(T) > 1;
+    L.tk0 = multi ? take(Kcap * 4) : 0;
+    L.tk1 = multi ? take(Kcap * 4) : 0;
+    L.tvB = multi ? take(Kcap * 4) : 0;
     L.total = o;
     return L;
 }
 
-// One stable LSD pass by reduce-then-scan over blocks of kSortBlock items.
-static cudaError_t rts_pass(const uint32_t *kin, const int *vin, uint32_t *kout, int *vout, const int *n_dev,
-                            int n_host, long long max_items, int shift, int bits, int *matrix, int *rowsum, int *err,
-                            cudaStream_t st) {
-    const int cols = (int)((max_items + kSortBlock - 1) / kSortBlock);
+// One stable LSD pass (histogram, scan, rank + place) over blocks of WARPS * SEG items.
+template <class Src, int WARPS, int SEG, bool STAGE>
+static cudaError_t rank_pass(const Src &src, const int *n_dev, int n_host, long long max_items, int shift, int bits,
+                             int *matrix, int *rowsum, int drop, int *n_kept, uint32_t *kout, int *vout,
+                             int2 *ranges, int T, cudaStream_t st) {
+    constexpr int block = WARPS * SEG;
+    const int cols = (int)((max_items + block - 1) / block);
     if (cols <= 0) return cudaSuccess;
-    const bool fused = cols <= kFusedRowsumCols;
-    block_hist_kernel<<<cols, kSortThreads, 0, st>>>(kin, n_dev, n_host, shift, bits, cols, matrix,
-                                                     fused ? rowsum : nullptr);
+    rank_hist_kernel<Src, WARPS, SEG><<<cols, 32 * WARPS, 0, st>>>(src, n_dev, n_host, shift, bits, cols, matrix,
+                                                                  rowsum, drop, n_kept);
     note_launch();
-    if (!fused) {
-        hist_rowsum_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, matrix, rowsum);
-        note_launch();
-    }
-    if (cols <= kSortThreads * 4)
-        hist_scan_reg_kernel<4><<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
-    else if (cols <= kSortThreads * 32)
-        hist_scan_reg_kernel<32><<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+    const int nd = 1 << bits;
+    if (cols <= 256 * 4)
+        rank_scan_kernel<4><<<nd, 256, 0, st>>>(n_dev, n_host, block, cols, rowsum, matrix, ranges, T);
+    else if (cols <= 256 * 32)
+        rank_scan_kernel<32><<<nd, 256, 0, st>>>(n_dev, n_host, block, cols, rowsum, matrix, ranges, T);
     else
-        hist_scan_kernel<<<kRadix, kSortThreads, 0, st>>>(n_dev, n_host, cols, rowsum, matrix);
+        rank_scan_kernel<0><<<nd, 256, 0, st>>>(n_dev, n_host, block, cols, rowsum, matrix, ranges, T);
     note_launch();
-    cudaError_t e =
-        ensure_smem((const void *)scatter_tma_kernel, (int)kTmaSmem);
+    // ranking by pairs needs every digit to be a whole tile id: one pass over all tile bits
+    const int pair_rank = (shift == 0 && ranges != nullptr) ? 1 : 0;
+    const bool peers = !(Src::kPairRank && pair_rank) && nd <= kPeerDigits;
+    const int smem = (int)rank_smem_bytes(block, WARPS, nd, peers, STAGE);
+    cudaError_t e = ensure_smem((const void *)rank_scatter_kernel<Src, WARPS, SEG, STAGE>,
+                                (int)rank_smem_bytes(block, WARPS, kMaxDigits, true, STAGE));
     if (e != cudaSuccess) return e;
-    const int persistent = 2 * sort_grid_blocks() / 4;  // two CTAs per SM
-    scatter_tma_kernel<<<cols < persistent ? cols : persistent, kTmaThreads, kTmaSmem, st>>>(
-        kin, vin, kout, vout, n_dev, n_host, shift, bits, cols, matrix, err);
+    rank_scatter_kernel<Src, WARPS, SEG, STAGE><<<cols, 32 * WARPS, smem, st>>>(
+        src, n_dev, n_host, shift, bits, cols, matrix, kout, vout, drop, pair_rank);
     note_launch();
     return cudaGetLastError();
 }
@@ -909,87 +904,120 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
                            long long *K_out, void *ws, cudaStream_t st) {
     const int C = cs.C;
     const long long CN = (long long)C * N;
-    const int G = sort_grid_blocks();
-    BinSortLayout L = binsort_layout(CN, Kcap, G);
+    const int T = cs.total_tiles;
+    BinSortLayout L = binsort_layout(CN, Kcap, T);
     char *w = (char *)ws;
     uint32_t *dk0 = (uint32_t *)(w + L.dk0), *dk1 = (uint32_t *)(w + L.dk1);
     int *dv0 = (int *)(w + L.dv0), *dv1 = (int *)(w + L.dv1);
     int *counts = (int *)(w + L.counts);
     int2 *rects = (int2 *)(w + L.rects);
-    long long *offsets = (long long *)(w + L.offsets);
-    int *chunk_start = (int *)(w + L.chunk_start);
+    int4 *pairs = (int4 *)(w + L.offsets);
+    int *win_start = (int *)(w + L.win_start);
+    unsigned *win_bits = (unsigned *)(w + L.win_bits);
+    const int nwin = (int)((Kcap + 31) / 32 + 1);
     long long *partials = (long long *)(w + L.partials);
     int *misc = (int *)(w + L.misc);
     int *n_eff = misc + kMiscNeff;
-    int *err = misc + kMiscErr;
+    int *n_vis = misc + kMiscNvis;
     int *matrix = (int *)(w + L.matrix);
     int *rowsum = misc + kMiscRowsum;
-    uint32_t *tk0 = (uint32_t *)(w + L.tk0), *tk1 = (uint32_t *)(w + L.tk1);
-    int *tvB = (int *)(w + L.tvB);
 
     const int cn = (int)CN;
-    const int T = cs.total_tiles;
     if (cn == 0) {
-        empty_result_kernel<<<1, 32, 0, st>>>(K_out, n_eff);
+        empty_result_kernel<<<1, 32, 0, st>>>(K_out, misc);
         note_launch();
         zero_ints_kernel<<<(2 * T + 255) / 256, 256, 0, st>>>(2 * T, tile_ranges);
         note_launch();
         return cudaGetLastError();
     }
-    const int bits = tile_bits(T);
-    const int tpasses = (bits + 6) / 7;                // passes of at most 7 bits
-    const int tdigit = (bits + tpasses - 1) / tpasses;  // equal digit widths
-    // stage 1: depth order of all (camera, Gaussian) pairs
+    // stage 1: depth order of the visible (camera, Gaussian) pairs
     const int eb = (cn + 1023) / 1024;  // four pairs per thread
     depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0, misc);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < 4; ++pass) {
-        const bool even = (pass % 2) == 0;
-        e = rts_pass(even ? dk0 : dk1, even ? dv0 : dv1, even ? dk1 : dk0, even ? dv1 : dv0, nullptr, cn, cn, 8 * pass,
-                     8, matrix, rowsum + pass * kRadix, err, st);
-        if (e != cudaSuccess) return e;
+    {
+        // passes of kDepthDigitBits bits (the last takes the rest); the first drops the pairs
+        // without tiles
+        uint32_t *kin = dk0, *kout = dk1;
+        int *vin = dv0, *vout = dv1;
+        int shift = 0;
+        for (int pass = 0; pass < kDepthPasses; ++pass) {
+            const ArraySrc src{kin, vin};
+            const int width = min(kDepthDigitBits, 32 - shift);
+            e = rank_pass<ArraySrc, kDepthWarps, kDepthSeg, kDepthStage>(src, pass ? n_vis : nullptr, cn, cn, shift, width, matrix,
+                                               rowsum + pass * kMaxDigits, pass == 0, n_vis, kout, vout, nullptr, 0,
+                                               st);
+            if (e != cudaSuccess) return e;
+            shift += width;
+            uint32_t *tk = kin;
+            kin = kout;
+            kout = tk;
+            int *tv = vin;
+            vin = vout;
+            vout = tv;
+        }
     }
-    const int *order = dv0;  // after 4 passes the sorted pairs are back in (dk0, dv0)
-    // stage 2: tile counts, offsets, balanced emission, stable sort by tile id
+    const int *order = (kDepthPasses % 2) ? dv1 : dv0;  // where the last depth pass wrote
+    // stage 2: tile counts, offsets, then the tile passes over the slots in depth order
+    const int passes = tile_passes(T);
+    const int bits = tile_bits(T);
     const int pb = (cn + kPairsPerCta - 1) / kPairsPerCta;  // CTAs of the count and offset kernels
-    count_tiles_kernel<<<pb, 256, 0, st>>>(cn, N, T, tile_ranges, cs, order, (const float2 *)means2d, radii, counts,
-                                           rects, partials);
+    count_tiles_kernel<<<pb, 256, 0, st>>>(cn, N, T, passes > 1 ? tile_ranges : nullptr, nwin, win_bits, cs, order,
+                                           n_vis,
+                                           (const float2 *)means2d, radii, counts, rects, partials);
     note_launch();
-    partial_scan_kernel<<<1, 1024, 0, st>>>(pb, partials, Kcap, K_out, n_eff);
+    partial_scan_kernel<<<1, 1024, 0, st>>>(pb, partials, Kcap, K_out, misc);
     note_launch();
-    offsets_kernel<<<pb, 256, 0, st>>>(cn, counts, partials, n_eff, offsets, chunk_start);
+    offsets_kernel<<<pb, 256, 0, st>>>(cn, counts, rects, order, partials, misc, pairs, win_start, win_bits);
     note_launch();
-    // choose buffers so that the last pass writes into the caller's `values`
-    uint32_t *kA = tk0, *kB = tk1;
-    int *vA = (tpasses % 2 == 0) ? values : tvB;
-    int *vB = (tpasses % 2 == 0) ? tvB : values;
-    if (Kcap > 0) {
-        const long long chunks = (Kcap + kChunk - 1) / kChunk;
-        const long long emit_blocks = chunks < 2ll * G ? chunks : 2ll * G;  // persistent: 8 CTAs per SM
-        emit_kernel<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(cn, cs, order, rects, offsets, chunk_start, n_eff,
-                                                                    kA, vA);
-        note_launch();
-    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < tpasses; ++pass) {
-        e = rts_pass(kA, vA, kB, vB, n_eff, 0, Kcap, tdigit * pass, tdigit, matrix, rowsum + (4 + pass) * kRadix, err,
-                     st);
-        if (e != cudaSuccess) return e;
-        uint32_t *tk = kA;
-        kA = kB;
-        kB = tk;
-        int *tv = vA;
-        vA = vB;
-        vB = tv;
+    if (Kcap <= 0) {  // nothing can be written: ranges stay zero
+        if (passes == 1) {
+            zero_ints_kernel<<<(2 * T + 255) / 256, 256, 0, st>>>(2 * T, tile_ranges);
+            note_launch();
+        }
+        return cudaGetLastError();
     }
-    // (kA, vA) now hold the sorted list; vA == values
-    // one thread per 4 entries of the largest possible list (threads past the real count exit)
+    const EmitSrc emit{pairs, win_start, win_bits};
+    int2 *ranges = (int2 *)tile_ranges;
+    if (passes == 1) {
+        // one counting pass: slots -> values, tile ranges from the digit totals
+        e = rank_pass<EmitSrc, kTileWarps, kTileSeg, kTileStage>(emit, n_eff, 0, Kcap, 0, bits, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
+                                         nullptr, nullptr, values, ranges, T, st);
+        if (e != cudaSuccess) return e;
+        if (keys64) {
+            keys64_kernel<<<(T + 7) / 8, 256, 0, st>>>(T, cn, ranges, values, depths, keys64);
+            note_launch();
+        }
+        return cudaGetLastError();
+    }
+    // several passes over materialised (tile, value) arrays; the last one writes `values`
+    uint32_t *tk0 = (uint32_t *)(w + L.tk0), *tk1 = (uint32_t *)(w + L.tk1);
+    int *tvB = (int *)(w + L.tvB);
+    const int dw = (bits + passes - 1) / passes;
+    uint32_t *kout = tk0;
+    int *vout = ((passes - 1) % 2 == 0) ? values : tvB;
+    e = rank_pass<EmitSrc, kTileWarps, kTileSeg, kTileStage>(emit, n_eff, 0, Kcap, 0, dw, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
+                                     nullptr, kout, vout, nullptr, 0, st);
+    if (e != cudaSuccess) return e;
+    for (int pass = 1; pass < passes; ++pass) {
+        const int width = min(dw, bits - pass * dw);
+        const ArraySrc src{kout, vout};
+        uint32_t *k2 = (kout == tk0) ? tk1 : tk0;
+        int *v2 = (vout == values) ? tvB : values;
+        e = rank_pass<ArraySrc, kTileWarps, kTileSeg, kTileStage>(src, n_eff, 0, Kcap, pass * dw, width, matrix,
+                                          rowsum + (kDepthPasses + pass) * kMaxDigits, 0, nullptr, k2, v2, nullptr, 0,
+                                          st);
+        if (e != cudaSuccess) return e;
+        kout = k2;
+        vout = v2;
+    }
+    // (kout, vout) hold the sorted list; vout == values
     const long long rq = (Kcap + 3) / 4;
     ranges_kernel<<<(unsigned)((rq + 255) / 256 > 0 ? (rq + 255) / 256 : 1), 256, 0, st>>>(
-        n_eff, T, cn, kA, vA, depths, (int2 *)tile_ranges, keys64, err, K_out);
+        n_eff, T, cn, kout, vout, depths, ranges, keys64);
     note_launch();
     return cudaGetLastError();
 }

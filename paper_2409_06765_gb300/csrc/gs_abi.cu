@@ -26,7 +26,7 @@ cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *
 cudaError_t launch_expected_depth(long long, const float *, int, int, const float *, float *, cudaStream_t);
 cudaError_t launch_expected_depth_bwd(long long, const float *, int, int, const float *, const float *, float *,
                                       float *, cudaStream_t);
-BinSortLayout binsort_layout(long long CN, long long Kcap, int G);
+BinSortLayout binsort_layout(long long CN, long long Kcap, long long T);
 cudaError_t launch_binsort(const CamSet &, int, const float *, const float *, const int *, long long,
                            unsigned long long *, int *, int *, long long *, void *, cudaStream_t);
 cudaError_t launch_raster_fwd(const CamSet &, const RasterConsts &, int, int, int, const int *, const int *, const int *,
@@ -100,21 +100,6 @@ cudaError_t ensure_smem(const void *kernel, int bytes) {
         }
     if (used < 256) table[used++] = Entry{dev, kernel, bytes};
     return cudaSuccess;
-}
-
-// CTAs of the sort kernels: 4 per SM of the current device (cached per device).
-int sort_grid_blocks() {
-    static std::mutex mu;
-    static int cache[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4 * 148;
-    std::lock_guard<std::mutex> lock(mu);
-    if (cache[dev] == 0) {
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-        cache[dev] = 4 * sms;
-    }
-    return cache[dev];
 }
 
 }  // namespace gs
@@ -341,8 +326,8 @@ int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, 
                                    int64_t K_capacity) {
     CamSet cs;
     if (!params || make_camset(cams, C, params->tile, cs) != GS_OK) return -1;
-    if (N < 0 || K_capacity < 0 || K_capacity >= (1ll << 31) || (long long)C * N >= (1ll << 31)) return -1;
-    return (int64_t)binsort_layout((long long)C * N, K_capacity, sort_grid_blocks()).total;
+    if (N < 0 || K_capacity < 0 || K_capacity > GS_MAX_INTERSECTIONS || (long long)C * N >= (1ll << 31)) return -1;
+    return (int64_t)binsort_layout((long long)C * N, K_capacity, cs.total_tiles).total;
 }
 
 gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
@@ -355,7 +340,14 @@ gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs
     GS_TRY(make_camset(cams, C, params->tile, cs));
     GS_TRY(check_cn(C, N));
     cs.N = N;
-    if (K_capacity < 0 || K_capacity >= (1ll << 31)) return fail_arg("K_capacity must be in [0, 2^31)");
+    if (K_capacity < 0) return fail_arg("K_capacity must be >= 0");
+    if (K_capacity > GS_MAX_INTERSECTIONS) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "K_capacity %lld exceeds GS_MAX_INTERSECTIONS (2^31 - 1): list positions are int32; "
+                 "render fewer cameras per call or use a larger tile",
+                 (long long)K_capacity);
+        return GS_ERR_CAPACITY;
+    }
     if (cs.total_tiles >= (1 << 28)) return fail_arg("more than 2^28 tiles in one call");
     GS_NONNULL(tile_ranges); GS_NONNULL(K_out); GS_NONNULL(workspace);
     if (N > 0) {
@@ -367,7 +359,7 @@ gs_status gs_tile_bin_sort(const gs_camera *cams, int32_t C, int32_t N, const gs
     if (N > 0 && !aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
     if (!aligned(tile_ranges, 8)) return fail_arg("tile_ranges must be 8-byte aligned");
     if (keys && !aligned(keys, 8)) return fail_arg("keys must be 8-byte aligned");
-    size_t need = binsort_layout((long long)C * N, K_capacity, sort_grid_blocks()).total;
+    size_t need = binsort_layout((long long)C * N, K_capacity, cs.total_tiles).total;
     if (workspace_bytes < need) {
         snprintf(g_last_error, sizeof(g_last_error), "workspace too small: %zu < %zu bytes", workspace_bytes, need);
         return GS_ERR_CAPACITY;

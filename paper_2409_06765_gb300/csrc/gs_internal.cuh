@@ -47,7 +47,7 @@ struct CamSet {
 
 // Byte offsets of the tile_bin_sort workspace regions (see binsort.cu).
 struct BinSortLayout {
-    size_t dk0, dk1, dv0, dv1, counts, rects, offsets, chunk_start, partials, misc, matrix, tk0, tk1, tvB, total;
+    size_t dk0, dk1, dv0, dv1, counts, rects, offsets, win_start, win_bits, partials, misc, matrix, tk0, tk1, tvB, total;
 };
 
 struct RasterConsts {

@@ -56,7 +56,8 @@ extern "C" GS_API gs_status gs_tile_bin_sort_noalloc(const gs_camera *cams, int3
                                                      int64_t *K_out, void *stream) {
     if (!params || !cams || !tile_ranges || !K_out) return GS_ERR_ARG;
     if (C < 1 || C > GS_MAX_CAMERAS || N < 0 || (long long)C * N >= (1ll << 31)) return GS_ERR_ARG;
-    if (K_capacity < 0 || K_capacity >= (1ll << 31)) return GS_ERR_ARG;
+    if (K_capacity < 0) return GS_ERR_ARG;
+    if (K_capacity > GS_MAX_INTERSECTIONS) return GS_ERR_CAPACITY;
     // the scratch this call would need, checked before anything is launched
     const int64_t need = gs_tile_bin_sort_workspace(cams, C, N, params, K_capacity);
     if (need < 0) return GS_ERR_ARG;

@@ -136,12 +136,14 @@ class FramePipeline:
             self._pre()
             torch.cuda.synchronize(self.device)
             K = int(self.K_out.item())
-            if K < 0:
-                raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1)")
             if K <= self.capacity:
                 self.K = K
                 return K
-            self.capacity = int(K * self.margin) + 1024
+            if K > _lib.GS_MAX_INTERSECTIONS:
+                raise _lib.GsError(_lib.GS_ERR_CAPACITY, "FramePipeline",
+                                   f"{K} intersections exceed GS_MAX_INTERSECTIONS (int32 list positions): "
+                                   "use a larger tile or fewer cameras per call")
+            self.capacity = min(int(K * self.margin) + 1024, _lib.GS_MAX_INTERSECTIONS)
             self._alloc_sort()
         raise RuntimeError("intersection count did not settle")
 
@@ -149,7 +151,7 @@ class FramePipeline:
         """After a synchronise: did the last frame need more intersections than the buffers hold?"""
         K = int(self.K_out.item())
         self.K = K
-        return K < 0 or K > self.capacity
+        return K > self.capacity
 
     @property
     def device_bytes(self) -> int:

@@ -92,8 +92,6 @@ class RasterState:
         self.pending = None
         ev.synchronize()
         K = int(K_host.item())
-        if K < 0:
-            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
         if K <= self.capacity:
             return True
         self.ensure(cams, N, params, K, dev)
@@ -101,8 +99,12 @@ class RasterState:
         return False
 
     def ensure(self, cams, N, params, K, device):
+        if K > _lib.GS_MAX_INTERSECTIONS:
+            raise _lib.GsError(_lib.GS_ERR_CAPACITY, "RasterState",
+                               f"{K} intersections exceed GS_MAX_INTERSECTIONS (int32 list positions): "
+                               "use a larger tile or fewer cameras per call")
         if K > self.capacity or self.values is None:
-            self.capacity = max(int(K * 1.25) + 1024, 1 << 16)
+            self.capacity = min(max(int(K * 1.25) + 1024, 1 << 16), _lib.GS_MAX_INTERSECTIONS)
             self.values = torch.empty(self.capacity, dtype=torch.int32, device=device)
             self.ws_key = ()
         key = (cams.C, N, self.capacity, params.tile)
@@ -159,8 +161,6 @@ def bin_sort(cams, N, params, means2d, depths, radii, state: RasterState | None 
         _lib.gs_tile_bin_sort(cams, N, params, means2d, depths, radii, state.capacity, keys, state.values, ranges,
                               K_out, state.workspace)
         K = int(K_out.item())
-        if K < 0:
-            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
         if K <= state.capacity:
             break
         state.ensure(cams, N, params, K, dev)
@@ -251,8 +251,6 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
             return dict(sp, colors=colors, values=state.values, ranges=bs["ranges"], K=None, image=image,
                         final_T=final_T, last_contrib=last, blends=blends, params=params, tile_order=order)
         K = int(bs["K_out"].item())
-        if K < 0:
-            raise RuntimeError("gs_tile_bin_sort reported an internal timeout (K_out = -1); lists are invalid")
         if K <= state.capacity:
             break
         state.ensure(cams, N, params, K, means.device)

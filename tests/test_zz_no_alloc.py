@@ -58,10 +58,10 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls():
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     lib = _lib.load()
     ca, p, sp, N = _inputs(3, 1000, (64, 48))
-    too_big = 4_000_000  # intersection capacity whose scratch exceeds the built-in array
-    assert _lib.gs_tile_bin_sort_workspace(ca, N, p, too_big) > _lib.GS_NOALLOC_SCRATCH_BYTES
-    fake = ctypes.c_void_p(256)
-    st = lib.gs_tile_bin_sort_noalloc(ca.ptr, 1, N, ctypes.byref(p), fake, fake, fake, too_big, None, fake, fake,
-                                      fake, None)
+    too_many = 2_000_000  # Gaussians whose per-pair scratch exceeds the built-in array
+    assert _lib.gs_tile_bin_sort_workspace(ca, too_many, p, 400_000) > _lib.GS_NOALLOC_SCRATCH_BYTES
+    fake = ctypes.c_void_p(256)  # never dereferenced: the size check comes first
+    st = lib.gs_tile_bin_sort_noalloc(ca.ptr, 1, too_many, ctypes.byref(p), fake, fake, fake, 400_000, None, fake,
+                                      fake, fake, None)
     assert st == _lib.GS_ERR_CAPACITY
     assert b"scratch" in lib.gs_last_error()
