@@ -205,10 +205,10 @@ GS_API gs_status gs_expected_depth_bwd(int64_t P, const float *image, int32_t ch
 /*      a list does not fit the int32 positions; split the cameras over       */
 /*      several calls or use a larger tile.                                   */
 /* workspace: device scratch of at least gs_tile_bin_sort_workspace() bytes,  */
-/*      256-byte aligned; its content on entry is ignored.  With at most 2048 */
-/*      tiles (one 1080p view at 32x32 tiles) the workspace holds nothing of  */
-/*      size K: about 44 bytes per (camera, Gaussian) pair plus 1.2 bytes per */
-/*      slot of K_capacity.                                                  */
+/*      256-byte aligned; its content on entry is ignored.  About 44 bytes    */
+/*      per (camera, Gaussian) pair plus, per slot of K_capacity, under one   */
+/*      byte with at most 2048 tiles (one 1080p view at 32x32 tiles: nothing  */
+/*      of size K is materialised) and about 12.8 bytes beyond.              */
 /* ------------------------------------------------------------------------ */
 GS_API int64_t gs_tile_bin_sort_workspace(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                                    int64_t K_capacity);

@@ -4,16 +4,15 @@
 // (global_tile << 32) | float_bits(depth), ties by flat index c*N + n.  Instead of one
 // radix sort over K 64-bit keys, the same order is reached in two stable stages:
 //   1. a stable LSD radix sort of the C*N (camera, Gaussian) pairs by the 32 depth bits, in
-//      three passes of at most 11 bits.  The first pass also drops the pairs that touch no
-//      pixel (key 0xFFFFFFFF), so the later passes and stage 2 see only the visible ones;
+//      four passes of 8 bits.  The first pass also drops the pairs that touch no pixel (key
+//      0xFFFFFFFF), so the later passes and stage 2 see only the visible ones;
 //   2. the K intersections in that depth order, sorted stably by tile id alone.  A pair's
 //      intersections are the tiles of its tile rectangle, so the list of "slots" in depth
-//      order is defined by the pairs' tile counts and rectangles; it is never written out.
-//      When the tile ids fit one digit of at most 11 bits (up to 2048 tiles: one 1080p view
-//      at 32x32 tiles), a single counting pass regenerates every slot from the pair table,
-//      once to count and once to place, and writes only the final values: no K-sized
-//      intermediate key or value array exists.  More tiles take further LSD passes over
-//      materialised (tile, value) arrays.
+//      order is defined by the pairs' tile counts and rectangles.  When the tile ids fit one
+//      digit of at most 11 bits (up to 2048 tiles: one 1080p view at 32x32 tiles), a single
+//      counting pass regenerates every slot from a 16-byte pair record, once to count and
+//      once to place, and writes only the final values: no K-sized key or value array
+//      exists.  More tiles take further LSD passes over materialised (tile, value) arrays.
 // Stability carries the depth order (and the index tie-break) into each tile's list.
 //
 // Every pass is reduce-then-scan over blocks of items (4096 for the depth passes, 16384
@@ -23,8 +22,13 @@
 // gives each of its 16 warps a contiguous segment of the block: the warps first count
 // their digits into per-warp 16-bit counters (shared atomics), the CTA turns the counters
 // into per-warp prefixes, and each warp then walks its segment in order, ranking 32 items
-// at a time with match.any (the lanes holding the same digit), so equal digits keep their
-// input order.  No CTA waits on another CTA and nothing waits on the device.
+// at a time among equal digits, so equal digits keep their input order.  The ranking uses
+// per-warp peer masks for the 8-bit depth digits (match.any for the last, skewed one) and,
+// in the single tile pass, the window's pairs one after another (a pair's slots are
+// distinct tiles).  The depth passes reorder each block by digit in shared memory and write
+// contiguous runs; the tile pass writes each slot straight to its place (runs of a block
+// over 2048 tiles are too short to coalesce).  No CTA waits on another CTA and nothing
+// waits on the device.
 //
 // Every kernel reads the data-dependent counts (visible pairs, K) from device memory, so
 // the host never synchronises and the whole call can be captured in a CUDA graph.
@@ -39,24 +43,10 @@ constexpr int kMaxDigits = 1 << kMaxDigitBits;
 constexpr int kDepthWarps = 16;                         // warps of a depth-pass CTA
 constexpr int kDepthSeg = 256;                          // items per warp segment, depth passes
 constexpr int kDepthBlock = kDepthWarps * kDepthSeg;    // 4096
-#ifndef GS_TILE_WARPS
-#define GS_TILE_WARPS 16
-#endif
-#ifndef GS_TILE_STAGE
-#define GS_TILE_STAGE 0
-#endif
-#ifndef GS_DEPTH_STAGE
-#define GS_DEPTH_STAGE 0
-#endif
-constexpr int kTileWarps = GS_TILE_WARPS;               // warps of a tile-pass CTA
+constexpr int kTileWarps = 16;                          // warps of a tile-pass CTA
 constexpr int kTileSeg = 1024;                          // slots per warp segment, tile passes
-constexpr int kTileBlock = kTileWarps * kTileSeg;
-constexpr bool kTileStage = GS_TILE_STAGE;              // tile passes keep their items in shared memory
-constexpr bool kDepthStage = GS_DEPTH_STAGE;            // depth passes keep their items in shared memory
-#ifndef GS_DEPTH_DIGIT_BITS
-#define GS_DEPTH_DIGIT_BITS 8
-#endif
-constexpr int kDepthDigitBits = GS_DEPTH_DIGIT_BITS;    // digit width of the depth passes
+constexpr int kTileBlock = kTileWarps * kTileSeg;       // 16384
+constexpr int kDepthDigitBits = 8;                      // digit width of the depth passes
 constexpr int kDepthPasses = (32 + kDepthDigitBits - 1) / kDepthDigitBits;
 constexpr int kMaxTilePasses = 3;                       // up to 2^28 tiles (the ABI's limit)
 constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
@@ -250,17 +240,15 @@ struct EmitSrc {
         valid = w0 + lane < n;
         const int k = valid ? w0 + lane - r.rec.x : 0;  // slot of the pair: row-major in its rectangle
         const int w = max(r.rec.z & 0xffff, 1), tx = r.rec.z >> 16;
-        // k / w from an approximate reciprocal, made exact by integer steps (a few at most)
+        // k / w from an approximate reciprocal and one branch-free correction step: the
+        // quotient is below 4096 (tile rows of a camera) and the float estimate of
+        // (k + 0.5) / w, whose fraction is at least 0.5 / w from an integer, is off by less
+        // than one, so floor() lands on the quotient or next to it
         int ky = __float2int_rz(((float)k + 0.5f) * rcp_approx((float)w));
         int kx = k - ky * w;
-        while (kx < 0) {
-            --ky;
-            kx += w;
-        }
-        while (kx >= w) {
-            ++ky;
-            kx -= w;
-        }
+        const int adj = (kx < 0) ? -1 : (kx >= w ? 1 : 0);
+        ky += adj;
+        kx -= adj * w;
         key = valid ? (uint32_t)(r.rec.y + ky * tx + kx) : kInvisible;
     }
 };
@@ -383,33 +371,38 @@ __global__ void __launch_bounds__(256) rank_scan_kernel(const int *__restrict__ 
     }
 }
 
-// Shared memory of the rank kernel for a block of `block` items and nd digits: the staged
-// keys and values, per-warp 16-bit digit counters, the block's digit starts, and (for digits
-// up to kPeerDigits, when not ranking by pairs) per-warp peer masks.
-__host__ __device__ constexpr size_t rank_smem_bytes(int block, int warps, int nd, bool peers, bool stage) {
-    return (stage ? (size_t)block * 8 : 0) + (size_t)warps * nd * 2 + (size_t)nd * 4 +
+// Shared memory of the rank kernel for a block of `block` items and nd digits: the reordered
+// block (keys and values), per-warp 16-bit digit counters, the block's digit starts in the
+// output and in the block, and (for digits up to kPeerDigits, when not ranking by pairs)
+// per-warp peer masks.
+__host__ __device__ constexpr size_t rank_smem_bytes(int block, int warps, int nd, bool peers, bool reorder) {
+    return (reorder ? (size_t)block * 8 : 0) + (size_t)warps * nd * 2 + (size_t)nd * 8 +
            (peers ? (size_t)warps * kPeerDigits * 4 : 0);
 }
 
 // Stable placement of one block.  (i) every warp counts its segment's digits into its own
-// 16-bit counters (with STAGE it also keeps the items, loaded or generated once, in shared
-// memory; without, it loads or generates them again in (iii), which keeps more CTAs resident);
-// (ii) the counters become per-warp prefixes; (iii) every warp walks its segment in order and
-// ranks 32 items at a time among equal digits -- by the window's pairs (whole tile ids as
-// digits), by peer masks (up to kPeerDigits digits) or by match.any -- and writes each item to
-// its final position.
-template <class Src, int WARPS, int SEG, bool STAGE>
+// 16-bit counters; (ii) the counters become per-warp prefixes and the block's digit totals are
+// scanned; (iii) every warp walks its segment in order (loading or generating the items again)
+// and ranks 32 items at a time among equal digits -- by the window's pairs (whole tile ids as
+// digits), by peer masks (up to kPeerDigits digits) or by match.any -- placing each item in
+// shared memory at its position within the block, so the block ends up sorted by digit;
+// (iv) the block is written out as one contiguous run per digit.  Without REORDER, (iii) writes
+// every item straight to its final position and (iv) is skipped: with many digits (2048 tiles)
+// the runs of a block are too short to coalesce, and the buffer would cost occupancy.
+template <class Src, int WARPS, int SEG, bool REORDER>
 __global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src, const int *__restrict__ n_dev,
                                                                 int n_host, int shift, int bits, int cols,
                                                                 const int *__restrict__ hist,
                                                                 uint32_t *__restrict__ keys_out,
                                                                 int *__restrict__ vals_out, int drop,
-                                                                int pair_rank) {
+                                                                int pair_rank, int no_peers) {
     constexpr int NT = 32 * WARPS;
     constexpr int BLOCK = WARPS * SEG;
     static_assert(SEG % (32 * 8) == 0 && WARPS % 8 == 0 && BLOCK <= 65535,
                   "per-warp 16-bit counters, cleared 16 bytes at a time; groups of up to 8 windows");
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tmp[WARPS];
+    __shared__ int s_kept;
     const int n = pass_items(n_dev, n_host);
     const int b = blockIdx.x;
     const int t0 = b * BLOCK;
@@ -417,13 +410,15 @@ __global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src,
     const int nd = 1 << bits;
     const unsigned mask = (unsigned)nd - 1u;
     const bool by_pairs = Src::kPairRank && pair_rank;
-    const bool by_peers = !by_pairs && nd <= kPeerDigits;
-    uint32_t *s_key = reinterpret_cast<uint32_t *>(smem);                     // [BLOCK] (STAGE)
-    int *s_val = reinterpret_cast<int *>(s_key + (STAGE ? BLOCK : 0));        // [BLOCK] (STAGE)
-    unsigned short *s_c16 = reinterpret_cast<unsigned short *>(s_val + (STAGE ? BLOCK : 0));  // [WARPS][nd]
+    const bool by_peers = !by_pairs && !no_peers && nd <= kPeerDigits;
+    constexpr int RB = REORDER ? BLOCK : 0;
+    uint32_t *s_ok = reinterpret_cast<uint32_t *>(smem);                       // [RB] reordered keys
+    int *s_ov = reinterpret_cast<int *>(s_ok + RB);                             // [RB] reordered values
+    unsigned short *s_c16 = reinterpret_cast<unsigned short *>(s_ov + RB);     // [WARPS][nd]
     unsigned *s_c32 = reinterpret_cast<unsigned *>(s_c16);
-    int *s_start = reinterpret_cast<int *>(s_c16 + WARPS * nd);                // [nd]
-    unsigned *s_peer = reinterpret_cast<unsigned *>(s_start + nd);             // [WARPS][kPeerDigits]
+    int *s_start = reinterpret_cast<int *>(s_c16 + WARPS * nd);                // [nd] start in the output
+    int *s_local = s_start + nd;                                               // [nd] start in the block
+    unsigned *s_peer = reinterpret_cast<unsigned *>(s_local + nd);             // [WARPS][kPeerDigits]
     {
         uint4 *z = reinterpret_cast<uint4 *>(s_c16);
         for (int i = threadIdx.x; i < WARPS * nd / 8; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -436,11 +431,10 @@ __global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src,
     const int s0 = t0 + warp * SEG;
     const int s1 = min(s0 + SEG, n);
     unsigned short *my = s_c16 + warp * nd;
-    // (i) stage the segment and count its digits per warp (staged key: the key, or with
-    // by_pairs the tile id | window pair << 16; 0xFFFFFFFF for an item that is not kept)
+    // (i) per-warp digit counts
     for (int w0 = s0; w0 < s1; w0 += 32 * Src::G) {
         typename Src::Raw raw[Src::G];
-        src.load_group(w0, s1, lane, STAGE, raw);
+        src.load_group(w0, s1, lane, false, raw);
 #pragma unroll
         for (int g = 0; g < Src::G; ++g) {
             const int wg = w0 + 32 * g;
@@ -450,11 +444,6 @@ __global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src,
             int val, pair;
             src.decode(raw[g], wg, s1, lane, valid, key, val, pair);
             if (drop && key == kInvisible) valid = false;
-            const int li = wg - t0 + lane;
-            if (STAGE && wg + lane < s1) {
-                s_key[li] = !valid ? kInvisible : (by_pairs ? (key | ((uint32_t)pair << 16)) : key);
-                s_val[li] = val;
-            }
             if (valid) {
                 const int c = warp * nd + (int)((key >> shift) & mask);
                 atomicAdd(&s_c32[c >> 1], 1u << ((c & 1) * 16));
@@ -462,93 +451,114 @@ __global__ void __launch_bounds__(32 * WARPS) rank_scatter_kernel(const Src src,
         }
     }
     __syncthreads();
-    // (ii) counters -> exclusive prefixes over the warps (warp w's items of digit d come after
-    // those of warps < w)
-    for (int d = threadIdx.x; d < nd; d += NT) {
-        int run = 0;
+    // (ii) counters -> per-warp prefixes (warp w's items of digit d come after those of warps < w);
+    // the block's digit totals -> their exclusive scan s_local (each thread a contiguous run of digits)
+    {
+        const int per = (nd + NT - 1) / NT;
+        const int d0 = min(nd, (int)threadIdx.x * per), d1 = min(nd, d0 + per);
+        int sum = 0;
+        for (int d = d0; d < d1; ++d) {
+            int run = 0;
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-            const int c = s_c16[w * nd + d];
-            s_c16[w * nd + d] = (unsigned short)run;
-            run += c;
+            for (int w = 0; w < WARPS; ++w) {
+                const int c = s_c16[w * nd + d];
+                s_c16[w * nd + d] = (unsigned short)run;
+                run += c;
+            }
+            s_local[d] = run;  // the digit's total for now
+            sum += run;
         }
+        int tot;
+        int pre = block_exclusive_scan<NT>(sum, tot, s_tmp);
+        for (int d = d0; d < d1; ++d) {
+            const int c = s_local[d];
+            s_local[d] = pre;
+            pre += c;
+        }
+        if (threadIdx.x == 0) s_kept = tot;
     }
     __syncthreads();
-    // (iii) each warp walks its segment in order
+    // (iii) each warp walks its segment in order and places its items in the block's digit order
     const unsigned lt = lanemask_lt();
     for (int w0 = s0; w0 < s1; w0 += 32 * Src::G) {
-      typename Src::Raw raw[Src::G];
-      if (!STAGE) src.load_group(w0, s1, lane, true, raw);
+        typename Src::Raw raw[Src::G];
+        src.load_group(w0, s1, lane, true, raw);
 #pragma unroll
-      for (int g = 0; g < Src::G; ++g) {
-        const int wg = w0 + 32 * g;
-        if (wg >= s1) break;  // uniform over the warp
-        uint32_t sk;
-        int val;
-        if (STAGE) {
-            const int li = wg - t0 + lane;
-            const bool inside = wg + lane < s1;
-            sk = inside ? s_key[li] : kInvisible;
-            val = inside ? s_val[li] : 0;
-        } else {
-            bool v;
-            uint32_t k;
-            int pair;
-            src.decode(raw[g], wg, s1, lane, v, k, val, pair);
-            if (drop && k == kInvisible) v = false;
-            sk = !v ? kInvisible : (by_pairs ? (k | ((uint32_t)pair << 16)) : k);
-        }
-        const bool valid = sk != kInvisible;
-        uint32_t key;
-        unsigned d;
-        int rank;
-        if (by_pairs) {
-            // the window's pairs one after the other: lanes of one pair hold distinct tiles
-            key = sk & 0xffffu;
-            d = key & mask;
-            const int pair = valid ? (int)(sk >> 16) : 0;
-            const int npair = __reduce_max_sync(0xffffffffu, pair) + 1;
-            rank = 0;
-            for (int p = 0; p < npair; ++p) {
-                if (valid && pair == p) {
-                    rank = my[d];
-                    my[d] = (unsigned short)(rank + 1);
+        for (int g = 0; g < Src::G; ++g) {
+            const int wg = w0 + 32 * g;
+            if (wg >= s1) break;  // uniform over the warp
+            bool valid;
+            uint32_t key;
+            int val, pair;
+            src.decode(raw[g], wg, s1, lane, valid, key, val, pair);
+            if (drop && key == kInvisible) valid = false;
+            unsigned d;
+            int rank;
+            if (by_pairs) {
+                // the window's pairs one after the other: lanes of one pair hold distinct tiles
+                d = (key >> shift) & mask;
+                const int np = __reduce_max_sync(0xffffffffu, valid ? pair : 0) + 1;
+                rank = 0;
+                for (int p = 0; p < np; ++p) {
+                    const int c = my[d];  // (every lane reads its own digit's counter)
+                    if (valid && pair == p) {
+                        rank = c;
+                        my[d] = (unsigned short)(c + 1);
+                    }
+                    __syncwarp();
+                }
+            } else if (by_peers) {
+                d = (key >> shift) & mask;
+                unsigned *pm = s_peer + warp * kPeerDigits + d;
+                if (valid) atomicOr(pm, 1u << lane);
+                __syncwarp();
+                const unsigned peers = valid ? *pm : 0u;
+                const int before = valid ? (int)my[d] : 0;
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1) {
+                    my[d] = (unsigned short)(before + __popc(peers));
+                    *pm = 0u;  // left at zero for the next window
                 }
                 __syncwarp();
+                rank = before + __popc(peers & lt);
+            } else {
+                d = valid ? ((key >> shift) & mask) : (0x10000u + lane);  // invalid lanes match no one
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int before = valid ? (int)my[d] : 0;
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1) my[d] = (unsigned short)(before + __popc(peers));
+                __syncwarp();
+                rank = before + __popc(peers & lt);
             }
-        } else if (by_peers) {
-            key = sk;
-            d = (key >> shift) & mask;
-            unsigned *pm = s_peer + warp * kPeerDigits + d;
-            if (valid) atomicOr(pm, 1u << lane);
-            __syncwarp();
-            const unsigned peers = valid ? *pm : 0u;
-            const int before = valid ? (int)my[d] : 0;
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) {
-                my[d] = (unsigned short)(before + __popc(peers));
-                *pm = 0u;  // left at zero for the next window
-            }
-            __syncwarp();
-            rank = before + __popc(peers & lt);
-        } else {
-            key = sk;
-            d = valid ? ((key >> shift) & mask) : (0x10000u + lane);  // invalid lanes match no one
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int before = valid ? (int)my[d] : 0;
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) my[d] = (unsigned short)(before + __popc(peers));
-            __syncwarp();
-            rank = before + __popc(peers & lt);
-        }
-        if (valid) {
-            const int pos = s_start[d] + rank;
-            if ((unsigned)pos < (unsigned)n) {  // holds by construction
-                if (keys_out) keys_out[pos] = key;
-                vals_out[pos] = val;
+            if (valid) {
+                if (REORDER) {
+                    const int lp = s_local[d] + rank;
+                    if ((unsigned)lp < (unsigned)BLOCK) {  // holds by construction
+                        s_ok[lp] = key;
+                        s_ov[lp] = val;
+                    }
+                } else {
+                    const int pos = s_start[d] + rank;
+                    if ((unsigned)pos < (unsigned)n) {  // holds by construction
+                        if (keys_out) keys_out[pos] = key;
+                        vals_out[pos] = val;
+                    }
+                }
             }
         }
-      }
+    }
+    if (!REORDER) return;
+    __syncthreads();
+    // (iv) the block in digit order: consecutive threads write consecutive slots of each run
+    const int kept = s_kept;
+    for (int i = threadIdx.x; i < kept; i += NT) {
+        const uint32_t key = s_ok[i];
+        const int d = (int)((key >> shift) & mask);
+        const int pos = s_start[d] + (i - s_local[d]);
+        if ((unsigned)pos < (unsigned)n) {  // holds by construction
+            if (keys_out) keys_out[pos] = key;
+            vals_out[pos] = s_ov[i];
+        }
     }
 }
 
@@ -868,10 +878,13 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
 }
 
 // One stable LSD pass (histogram, scan, rank + place) over blocks of WARPS * SEG items.
-template <class Src, int WARPS, int SEG, bool STAGE>
+// One stable LSD pass (histogram, scan, rank + place) over blocks of WARPS * SEG items.
+// `skewed`: most items share a few digits (the top bits of positive float depths), where lanes
+// OR-ing into one peer mask serialise and match.any ranks faster.
+template <class Src, int WARPS, int SEG, bool REORDER>
 static cudaError_t rank_pass(const Src &src, const int *n_dev, int n_host, long long max_items, int shift, int bits,
                              int *matrix, int *rowsum, int drop, int *n_kept, uint32_t *kout, int *vout,
-                             int2 *ranges, int T, cudaStream_t st) {
+                             int2 *ranges, int T, cudaStream_t st, bool skewed = false) {
     constexpr int block = WARPS * SEG;
     const int cols = (int)((max_items + block - 1) / block);
     if (cols <= 0) return cudaSuccess;
@@ -888,13 +901,13 @@ static cudaError_t rank_pass(const Src &src, const int *n_dev, int n_host, long 
     note_launch();
     // ranking by pairs needs every digit to be a whole tile id: one pass over all tile bits
     const int pair_rank = (shift == 0 && ranges != nullptr) ? 1 : 0;
-    const bool peers = !(Src::kPairRank && pair_rank) && nd <= kPeerDigits;
-    const int smem = (int)rank_smem_bytes(block, WARPS, nd, peers, STAGE);
-    cudaError_t e = ensure_smem((const void *)rank_scatter_kernel<Src, WARPS, SEG, STAGE>,
-                                (int)rank_smem_bytes(block, WARPS, kMaxDigits, true, STAGE));
+    const bool peers = !(Src::kPairRank && pair_rank) && !skewed && nd <= kPeerDigits;
+    const int smem = (int)rank_smem_bytes(block, WARPS, nd, peers, REORDER);
+    const int smem_max = (int)rank_smem_bytes(block, WARPS, kMaxDigits, true, REORDER);
+    cudaError_t e = ensure_smem((const void *)rank_scatter_kernel<Src, WARPS, SEG, REORDER>, smem_max);
     if (e != cudaSuccess) return e;
-    rank_scatter_kernel<Src, WARPS, SEG, STAGE><<<cols, 32 * WARPS, smem, st>>>(
-        src, n_dev, n_host, shift, bits, cols, matrix, kout, vout, drop, pair_rank);
+    rank_scatter_kernel<Src, WARPS, SEG, REORDER><<<cols, 32 * WARPS, smem, st>>>(
+        src, n_dev, n_host, shift, bits, cols, matrix, kout, vout, drop, pair_rank, skewed ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
@@ -945,9 +958,10 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
         for (int pass = 0; pass < kDepthPasses; ++pass) {
             const ArraySrc src{kin, vin};
             const int width = min(kDepthDigitBits, 32 - shift);
-            e = rank_pass<ArraySrc, kDepthWarps, kDepthSeg, kDepthStage>(src, pass ? n_vis : nullptr, cn, cn, shift, width, matrix,
-                                               rowsum + pass * kMaxDigits, pass == 0, n_vis, kout, vout, nullptr, 0,
-                                               st);
+            // (the last pass writes only the values: the sorted keys are not read again)
+            e = rank_pass<ArraySrc, kDepthWarps, kDepthSeg, true>(
+                src, pass ? n_vis : nullptr, cn, cn, shift, width, matrix, rowsum + pass * kMaxDigits, pass == 0,
+                n_vis, pass + 1 < kDepthPasses ? kout : nullptr, vout, nullptr, 0, st, pass + 1 == kDepthPasses);
             if (e != cudaSuccess) return e;
             shift += width;
             uint32_t *tk = kin;
@@ -981,11 +995,13 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
         return cudaGetLastError();
     }
     const EmitSrc emit{pairs, win_start, win_bits};
+
     int2 *ranges = (int2 *)tile_ranges;
     if (passes == 1) {
         // one counting pass: slots -> values, tile ranges from the digit totals
-        e = rank_pass<EmitSrc, kTileWarps, kTileSeg, kTileStage>(emit, n_eff, 0, Kcap, 0, bits, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
-                                         nullptr, nullptr, values, ranges, T, st);
+        e = rank_pass<EmitSrc, kTileWarps, kTileSeg, false>(emit, n_eff, 0, Kcap, 0, bits, matrix,
+                                                            rowsum + kDepthPasses * kMaxDigits, 0, nullptr, nullptr,
+                                                            values, ranges, T, st);
         if (e != cudaSuccess) return e;
         if (keys64) {
             keys64_kernel<<<(T + 7) / 8, 256, 0, st>>>(T, cn, ranges, values, depths, keys64);
@@ -999,7 +1015,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     const int dw = (bits + passes - 1) / passes;
     uint32_t *kout = tk0;
     int *vout = ((passes - 1) % 2 == 0) ? values : tvB;
-    e = rank_pass<EmitSrc, kTileWarps, kTileSeg, kTileStage>(emit, n_eff, 0, Kcap, 0, dw, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
+    e = rank_pass<EmitSrc, kTileWarps, kTileSeg, false>(emit, n_eff, 0, Kcap, 0, dw, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
                                      nullptr, kout, vout, nullptr, 0, st);
     if (e != cudaSuccess) return e;
     for (int pass = 1; pass < passes; ++pass) {
@@ -1007,7 +1023,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
         const ArraySrc src{kout, vout};
         uint32_t *k2 = (kout == tk0) ? tk1 : tk0;
         int *v2 = (vout == values) ? tvB : values;
-        e = rank_pass<ArraySrc, kTileWarps, kTileSeg, kTileStage>(src, n_eff, 0, Kcap, pass * dw, width, matrix,
+        e = rank_pass<ArraySrc, kTileWarps, kTileSeg, false>(src, n_eff, 0, Kcap, pass * dw, width, matrix,
                                           rowsum + (kDepthPasses + pass) * kMaxDigits, 0, nullptr, k2, v2, nullptr, 0,
                                           st);
         if (e != cudaSuccess) return e;

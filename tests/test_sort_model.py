@@ -52,14 +52,17 @@ def _pairs_in_depth_order(means2d, depths, radii, widths, heights, t):
     return np.array(order, np.int64), np.array(counts, np.int64), np.array(rects, np.int64).reshape(-1, 2)
 
 
-def _f32_quotient(k, w):
-    q = int(np.float32(np.float32(k) + np.float32(0.5)) * np.float32(np.float32(1.0) / np.float32(w)))
+def _f32_quotient(k, w, rcp_ulps=0):
+    """k / w as the emission computes it: a float32 estimate of (k + 0.5) / w from a reciprocal
+    (``rcp_ulps`` ulps away from the correctly rounded one, as the hardware approximation may
+    be), truncated, then one correction step of -1, 0 or +1."""
+    r32 = np.float32(np.float32(1.0) / np.float32(w))
+    for _ in range(abs(rcp_ulps)):
+        r32 = np.nextafter(r32, np.float32(np.inf if rcp_ulps > 0 else -np.inf), dtype=np.float32)
+    q = int(np.float32(np.float32(np.float32(k) + np.float32(0.5)) * r32))
     r = k - q * w
-    while r < 0:
-        q, r = q - 1, r + w
-    while r >= w:
-        q, r = q + 1, r - w
-    return q, r
+    adj = -1 if r < 0 else (1 if r >= w else 0)
+    return q + adj, r - adj * w
 
 
 def emit_window(offsets, rects, order, win_start, w0, n_slots):
@@ -190,10 +193,19 @@ def test_emission_windows_with_single_slot_pairs_and_a_capacity_cut():
         assert got == want[:n_slots]
 
 
-def test_float_quotient_with_integer_correction_is_exact():
+def test_float_quotient_with_one_correction_step_is_exact():
+    """Slot k of a rectangle of width w <= 4096 tiles and at most 4096 rows (a camera of up to
+    32768 pixels a side at 8-pixel tiles): one correction step after the float estimate gives
+    the exact row and column, also with a reciprocal off by a couple of ulps."""
     rng = np.random.default_rng(3)
-    for k, w in zip(rng.integers(0, 1 << 24, 20000), rng.integers(1, 4097, 20000)):
-        assert _f32_quotient(int(k), int(w)) == divmod(int(k), int(w))
+    w = rng.integers(1, 4097, 40000)
+    k = (rng.random(40000) * w * rng.integers(1, 4097, 40000)).astype(np.int64)
+    for kk, ww in zip(k, w):
+        for ulps in (-2, 0, 2):
+            assert _f32_quotient(int(kk), int(ww), ulps) == divmod(int(kk), int(ww))
+    for ww in (1, 3, 7, 60, 4096):  # the extremes of each width: first and last slot of 4096 rows
+        for kk in (0, ww - 1, ww, 4096 * ww - 1):
+            assert _f32_quotient(kk, ww, 2) == divmod(kk, ww)
 
 
 def rank_pass(keys, vals, shift, bits, seg, warps=16, drop=None):
@@ -281,14 +293,14 @@ def test_intersection_capacity_above_the_int32_limit_is_a_capacity_error():
 
 
 def test_single_pass_workspace_holds_nothing_of_the_list_size():
-    """Up to 2048 tiles the sort keeps no K-sized arrays: the workspace grows by about one byte
+    """Up to 2048 tiles the sort keeps no K-sized arrays: the workspace grows by under one byte
     per slot of capacity (block counts and window starts); past 2048 tiles it holds (tile,
-    value) arrays."""
+    value) arrays and a second value array, 12 bytes per slot."""
     p = _lib.make_params(tile=32)
     one = _lib.CameraArray([synth.make_camera(1920, 1080, (0, 0, 4))])  # 2040 tiles
     a = _lib.gs_tile_bin_sort_workspace(one, 1000, p, 1_000_000)
     b = _lib.gs_tile_bin_sort_workspace(one, 1000, p, 9_000_000)
-    assert 0 < (b - a) / 8_000_000 < 2.0
+    assert 0 < (b - a) / 8_000_000 < 1.0
     many = _lib.CameraArray([synth.make_camera(1920, 1080, (0, 0, 4))] * 2)  # 4080 tiles
     a = _lib.gs_tile_bin_sort_workspace(many, 1000, p, 1_000_000)
     b = _lib.gs_tile_bin_sort_workspace(many, 1000, p, 9_000_000)
