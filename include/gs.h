@@ -70,7 +70,10 @@ typedef struct gs_camera {
  * near plane 0.01, alpha in [1/255, 0.99], transmittance floor 1e-4. */
 typedef struct gs_params {
     int32_t tile;         /* tile edge in pixels: 8, 16 or 32 */
-    int32_t batch_depth;  /* Gaussians staged in shared memory per batch: 32..1024, multiple of 32 */
+    int32_t batch_depth;  /* Gaussians staged in shared memory per batch: 32..1024, multiple of 32.
+                             A staged entry takes 48 bytes plus 16 per 4 channels; a batch beyond
+                             the 227 KB of shared memory of one CTA (e.g. 1024 entries with 64
+                             channels) returns GS_ERR_UNSUPPORTED. */
     int32_t antialiased;  /* 0: classic mode; 1: opacity * sqrt(|S'| / |S' + sI|) [App. A] */
     int32_t pixels_per_thread; /* pixels one compositing thread owns, stacked along y: 0 = default
                                   (1 for 8x8 and 16x16 tiles, 4 for 32x32); also 2 for 16x16, 2 or 4

@@ -39,6 +39,9 @@ cudaError_t launch_raster_bwd(const CamSet &, const RasterConsts &, int, int, in
 cudaError_t launch_probe(int, int, int, float *, double *, cudaStream_t);
 cudaError_t launch_tile_order(int, const int *, int *, cudaStream_t);
 int raster_channel_capacity(int tile, int ppt, int ch, bool restricted);
+size_t raster_fwd_smem(int batch, int chc);
+size_t raster_bwd_smem(int batch, int chc, int threads, bool reduce_buffers);
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 int raster_pixels_per_thread(int tile, int ppt);
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -399,6 +402,16 @@ gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, const gs
                  channels, blend_count ? " and blend counting" : "");
         return GS_ERR_UNSUPPORTED;
     }
+    {
+        const size_t need = raster_fwd_smem(params->batch_depth,
+                                            raster_channel_capacity(params->tile, ppt, channels, blend_count != nullptr));
+        if (need > kMaxSmemPerCta) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "batch_depth %d with %d channels needs %zu bytes of shared memory per CTA (at most %zu)",
+                     params->batch_depth, channels, need, kMaxSmemPerCta);
+            return GS_ERR_UNSUPPORTED;
+        }
+    }
     GS_NONNULL(tile_ranges); GS_NONNULL(image); GS_NONNULL(final_T); GS_NONNULL(last_contrib);
     if (N > 0) {
         GS_NONNULL(values); GS_NONNULL(radii); GS_NONNULL(means2d); GS_NONNULL(conics); GS_NONNULL(opacities);
@@ -437,6 +450,17 @@ gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs
         snprintf(g_last_error, sizeof(g_last_error), "no backward kernel for tile %d with %d channels%s",
                  params->tile, channels, absgrad ? " and absgrad" : "");
         return GS_ERR_UNSUPPORTED;
+    }
+    {
+        const size_t need = raster_bwd_smem(params->batch_depth,
+                                            raster_channel_capacity(params->tile, ppt, channels, absgrad != nullptr),
+                                            params->tile * params->tile / ppt, ppt <= 2);
+        if (need > kMaxSmemPerCta) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "batch_depth %d with %d channels needs %zu bytes of shared memory per CTA (at most %zu)",
+                     params->batch_depth, channels, need, kMaxSmemPerCta);
+            return GS_ERR_UNSUPPORTED;
+        }
     }
     if (N == 0) return GS_OK;
     GS_NONNULL(tile_ranges); GS_NONNULL(values); GS_NONNULL(radii); GS_NONNULL(means2d); GS_NONNULL(conics);

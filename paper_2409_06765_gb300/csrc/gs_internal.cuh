@@ -209,20 +209,23 @@ __device__ __forceinline__ void warp_band(int tx0, int ty0, int warp, int lane, 
 //   box = (x0, x1 - x0, y0, y1 - y0) of the (unclipped) pixel box
 // The sigma cut is ln(opacity / alpha_min): beyond it alpha < alpha_min, so such pairs
 // never blend; it is used only to skip work that would be skipped anyway.
+__device__ __forceinline__ void make_splat(int id, float2 m, int r, float o, float ca, float cb, float cc,
+                                           float alpha_min, float4 &g, float4 &h, int4 &box) {
+    int x0, x1, y0, y1;
+    support_span(m.x, r, x0, x1);
+    support_span(m.y, r, y0, y1);
+    const float cut = !(o >= alpha_min) ? -1.f : (alpha_min > 0.f ? __logf(o / alpha_min) : 3.0e38f);
+    g = make_float4(m.x, m.y, -0.5f * kLog2e * ca, -kLog2e * cb);
+    h = make_float4(-0.5f * kLog2e * cc, o, cut, __int_as_float(id));
+    box = make_int4(x0, x1 - x0, y0, y1 - y0);
+}
+
 __device__ __forceinline__ void stage_splat(int id, const float2 *__restrict__ means2d,
                                             const float *__restrict__ conics, const float *__restrict__ opac,
                                             const int *__restrict__ radii, float alpha_min, float4 &g, float4 &h,
                                             int4 &box) {
-    const float2 m = means2d[id];
-    const int r = radii[id];
-    int x0, x1, y0, y1;
-    support_span(m.x, r, x0, x1);
-    support_span(m.y, r, y0, y1);
-    const float o = opac[id];
-    const float cut = !(o >= alpha_min) ? -1.f : (alpha_min > 0.f ? __logf(o / alpha_min) : 3.0e38f);
-    g = make_float4(m.x, m.y, -0.5f * kLog2e * conics[3 * id], -kLog2e * conics[3 * id + 1]);
-    h = make_float4(-0.5f * kLog2e * conics[3 * id + 2], o, cut, __int_as_float(id));
-    box = make_int4(x0, x1 - x0, y0, y1 - y0);
+    make_splat(id, means2d[id], radii[id], opac[id], conics[3 * id], conics[3 * id + 1], conics[3 * id + 2],
+               alpha_min, g, h, box);
 }
 
 // Can the staged Gaussian blend at any pixel of the rectangle of pixel indices

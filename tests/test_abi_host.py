@@ -74,6 +74,14 @@ def test_host_validation_rejects_bad_arguments_before_any_launch():
     assert lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(p), 0, *args, null) == _lib.GS_ERR_ARG
     p8 = _lib.make_params(tile=8)
     assert lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(p8), 7, *args, null) == _lib.GS_ERR_UNSUPPORTED
+    # a staged batch beyond one CTA's shared memory (1024 entries of 64 channels)
+    big = _lib.make_params(tile=16, batch_depth=1024, pixels_per_thread=1)
+    no_count = [fake] * 11 + [null, null]  # ... blend_count and tile_order NULL
+    assert lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(big), 64, *no_count, null) == _lib.GS_ERR_UNSUPPORTED
+    assert b"shared memory" in lib.gs_last_error()
+    ok = _lib.make_params(tile=16, batch_depth=256, pixels_per_thread=1)
+    st = lib.gs_rasterize_fwd(cams.ptr, 1, 10, ctypes.byref(ok), 64, *[null] * 12, null, null)
+    assert st == _lib.GS_ERR_ARG  # past the size checks: fails on the NULL buffers instead
     # SH degree
     assert lib.gs_sh_eval(cams.ptr, 1, 10, 4, fake, fake, fake, fake, null) == _lib.GS_ERR_ARG
     # workspace too small is a capacity error
