@@ -267,10 +267,12 @@ def summary_line(full):
         if "error" in srv:
             line["serving"] = {"error": srv["error"][:80]}
         else:
-            # per path: p50 ms, p99 ms, frames/s at saturation, mean views per batch at the trace's rate
-            line["serving"] = {name: [_r(srv[name].get(k), 3) for k in ("p50_ms", "p99_ms", "saturated_frames_per_s",
-                                                                         "mean_views_per_batch")]
-                               for name in ("batched", "single_view") if name in srv}
+            # per path (streams): p50 ms, p99 ms, frames/s at saturation, mean views per batch at the
+            # trace's rate and at saturation
+            line["serving"] = {short: [_r(srv[name].get(k), 3) for k in ("p50_ms", "p99_ms", "saturated_frames_per_s",
+                                                                          "mean_views_per_batch",
+                                                                          "saturated_mean_views_per_batch")]
+                               for name, short in (("batched", "batch"), ("single_view", "single")) if name in srv}
     line["serving_p99_ms"] = _r(full.get("serving_p99_ms"), 3)
     return line
 
@@ -468,7 +470,8 @@ def run_ours(args):
     if not args.skip_next:
         for name, fn in (("multiview", lambda: run_multiview(dscene, 5, log)),
                          ("memory", lambda: run_memory(5, sched, log)),
-                         ("serving", lambda: run_serving(args.serve_seconds, args.serve_rate, log))):
+                         ("serving", lambda: run_serving(args.serve_seconds, args.serve_rate, log,
+                                                         warm_s=args.serve_warmup, schedule=sched))):
             try:
                 log(f"{name} ...")
                 extra[name] = fn()
@@ -713,36 +716,51 @@ def run_memory(steps, sched, log):
     return out
 
 
-def run_serving(seconds, rate, log, warm_s=2.0):
-    """8 resident scenes (0.5..6M Gaussians), Poisson requests, batched vs single-view serving."""
+def run_serving(seconds, rate, log, warm_s=2.0, schedule=None):
+    """8 resident scenes (0.5..6M Gaussians), Poisson requests: continuous batching (up to 8 views
+    of any scenes per batch) against the single-view path at the same number of streams (4),
+    and the plain single-view path on one stream."""
     import gc
     import torch
     from paper_2409_06765_gb300 import serve, synth
+    from paper_2409_06765_gb300.pipeline import Schedule
+    sched = schedule or Schedule()
     sizes_m = [0.5, 1, 2, 3, 4, 5, 5, 6]
     store = serve.ResidentScenes()
     t0 = time.time()
     for sid, m in enumerate(sizes_m):
-        store.add(sid, synth.clustered_scene(int(m * 1_000_000), 50 + sid))
+        store.add(sid, synth.clustered_scene(int(m * 1_000_000), 50 + sid), schedule=sched)
     setup_s = time.time() - t0
     trace = serve.poisson_trace(rate, warm_s + seconds, len(sizes_m), seed=58)
     sat = serve.poisson_trace(10 * rate, 400 / (10 * rate), len(sizes_m), seed=59)  # 400 requests at once
     out = {"workload": f"8 resident scenes ({', '.join(str(m) for m in sizes_m)} M Gaussians, SH 3); Poisson "
                        f"{rate:.0f} req/s for {seconds:.0f} s after {warm_s:.0f} s warm-up; sizes 640x480, "
                        "1280x720, 1920x1080; forward only, image returned to pinned host memory",
+           "seconds": seconds, "rate": rate, "schedule": sched.as_dict(),
            "scene_setup_s": setup_s, "resident_scene_bytes": sum(s.nbytes for s in store.scenes.values())}
-    for name, kw in (("batched", dict(max_views=8, streams=4)), ("single_view", dict(max_views=1, streams=1))):
-        srv = serve.Server(store, **kw)
-        srv.serve(sat[:16], realtime=False)  # warm the allocator and the kernels
+    warm = serve.Server(store, schedule=sched, max_views=8, streams=4)
+    warm.serve(sat, realtime=False)  # the allocator's pools, pinned buffers and every kernel, once
+    warm.serve(serve.poisson_trace(rate, 1.0, len(sizes_m), seed=57), realtime=True)
+    del warm
+    for name, kw in (("batched", dict(max_views=8, streams=4)), ("single_view", dict(max_views=1, streams=4)),
+                     ("single_view_1_stream", dict(max_views=1, streams=1))):
+        srv = serve.Server(store, schedule=sched, **kw)
+        srv.serve(sat[:32], realtime=False)  # this server's streams and pinned buffers
         res = srv.serve(trace, realtime=True)
         summ = serve.latency_summary(res, skip_before_s=warm_s)
         t1 = time.perf_counter()
         sat_res = srv.serve(sat, realtime=False)
         sat_s = time.perf_counter() - t1
+        ssum = serve.latency_summary(sat_res)
         summ["saturated_frames_per_s"] = len(sat_res) / sat_s
+        summ["saturated_mean_views_per_batch"] = ssum["mean_views_per_batch"]
+        summ["saturated_mean_scenes_per_batch"] = ssum["mean_scenes_per_batch"]
+        summ["streams"], summ["max_views"] = kw["streams"], kw["max_views"]
         summ["batches"], summ["overflow_retries"] = srv.batches, srv.overflows
         out[name] = summ
         log(f"  serving {name}: p50 {summ['p50_ms']:.2f} ms p99 {summ['p99_ms']:.2f} ms, "
-            f"saturated {summ['saturated_frames_per_s']:.0f} frames/s")
+            f"{summ['mean_views_per_batch']:.2f} views/batch; saturated {summ['saturated_frames_per_s']:.0f} frames/s "
+            f"({summ['saturated_mean_views_per_batch']:.2f} views/batch)")
         del srv
         gc.collect()
     out["p99_ms"] = out["batched"]["p99_ms"]
@@ -892,6 +910,7 @@ def main():
     ap.add_argument("--detail-out", default=None, help="also write the full result record (JSON) to this file")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-warmup", type=float, default=2.0, help="seconds of the trace left out of the latencies")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

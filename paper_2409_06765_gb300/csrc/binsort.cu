@@ -48,7 +48,7 @@ constexpr int kTileSeg = 1024;                          // slots per warp segmen
 constexpr int kTileBlock = kTileWarps * kTileSeg;       // 16384
 constexpr int kDepthDigitBits = 8;                      // digit width of the depth passes
 constexpr int kDepthPasses = (32 + kDepthDigitBits - 1) / kDepthDigitBits;
-constexpr int kMaxTilePasses = 3;                       // up to 2^28 tiles (the ABI's limit)
+constexpr int kMaxTilePasses = 4;                       // up to 2^28 tiles (the ABI's limit) in 8-bit passes
 constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
 constexpr int kPeerDigits = 256;  // digits up to which the rank kernel ranks by peer masks
 
@@ -842,7 +842,12 @@ static int tile_bits(long long T) {
     return b;
 }
 
-static int tile_passes(long long T) { return (tile_bits(T) + kMaxDigitBits - 1) / kMaxDigitBits; }
+// One counting pass over whole tile ids up to 2048 tiles; beyond, LSD passes of at most 8 bits
+// (peer-mask ranking, blocks reordered in shared memory, like the depth passes).
+static int tile_passes(long long T) {
+    const int b = tile_bits(T);
+    return b <= kMaxDigitBits ? 1 : (b + kDepthDigitBits - 1) / kDepthDigitBits;
+}
 
 BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
     BinSortLayout L;
@@ -853,9 +858,12 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
         return at;
     };
     const long long cnb = (CN + kPairsPerCta - 1) / kPairsPerCta;
+    // digit-major count matrix: the largest (digits x blocks) of any pass
     const long long cols_d = (CN + kDepthBlock - 1) / kDepthBlock;
-    const long long cols_t = (Kcap + kTileBlock - 1) / kTileBlock;
-    const long long cols = cols_d > cols_t ? cols_d : cols_t;
+    const long long m_depth = cols_d * (1 << kDepthDigitBits);
+    const long long m_tile = tile_passes(T) == 1 ? (Kcap + kTileBlock - 1) / kTileBlock * (long long)kMaxDigits
+                                                 : (Kcap + kDepthBlock - 1) / kDepthBlock * (1ll << kDepthDigitBits);
+    const long long mat = m_depth > m_tile ? m_depth : m_tile;
     L.dk0 = take(CN * 4);
     L.dk1 = take(CN * 4);
     L.dv0 = take(CN * 4);
@@ -867,7 +875,7 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
     L.win_bits = take(((Kcap + 31) / 32 + 1) * 4);
     L.partials = take((size_t)(cnb + 1) * 8);
     L.misc = take((size_t)kMiscInts * 4);
-    L.matrix = take((size_t)(cols > 0 ? cols : 1) * kMaxDigits * 4);
+    L.matrix = take((size_t)(mat > 0 ? mat : 1) * 4);
     // (tile, value) arrays of the list exist only when the tile ids need more than one pass
     const bool multi = tile_passes(T) > 1;
     L.tk0 = multi ? take(Kcap * 4) : 0;
@@ -1012,20 +1020,21 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     // several passes over materialised (tile, value) arrays; the last one writes `values`
     uint32_t *tk0 = (uint32_t *)(w + L.tk0), *tk1 = (uint32_t *)(w + L.tk1);
     int *tvB = (int *)(w + L.tvB);
-    const int dw = (bits + passes - 1) / passes;
+    const int dw = (bits + passes - 1) / passes;  // <= 8 bits
     uint32_t *kout = tk0;
     int *vout = ((passes - 1) % 2 == 0) ? values : tvB;
-    e = rank_pass<EmitSrc, kTileWarps, kTileSeg, false>(emit, n_eff, 0, Kcap, 0, dw, matrix, rowsum + kDepthPasses * kMaxDigits, 0,
-                                     nullptr, kout, vout, nullptr, 0, st);
+    e = rank_pass<EmitSrc, kDepthWarps, kDepthSeg, true>(emit, n_eff, 0, Kcap, 0, dw, matrix,
+                                                         rowsum + kDepthPasses * kMaxDigits, 0, nullptr, kout, vout,
+                                                         nullptr, 0, st);
     if (e != cudaSuccess) return e;
     for (int pass = 1; pass < passes; ++pass) {
         const int width = min(dw, bits - pass * dw);
         const ArraySrc src{kout, vout};
         uint32_t *k2 = (kout == tk0) ? tk1 : tk0;
         int *v2 = (vout == values) ? tvB : values;
-        e = rank_pass<ArraySrc, kTileWarps, kTileSeg, false>(src, n_eff, 0, Kcap, pass * dw, width, matrix,
-                                          rowsum + (kDepthPasses + pass) * kMaxDigits, 0, nullptr, k2, v2, nullptr, 0,
-                                          st);
+        e = rank_pass<ArraySrc, kDepthWarps, kDepthSeg, true>(src, n_eff, 0, Kcap, pass * dw, width, matrix,
+                                                              rowsum + (kDepthPasses + pass) * kMaxDigits, 0, nullptr,
+                                                              k2, v2, nullptr, 0, st);
         if (e != cudaSuccess) return e;
         kout = k2;
         vout = v2;

@@ -4,20 +4,25 @@ Several scenes' Gaussians stay resident on the device.  Forward-only render requ
 (scene, camera) arrive over time; the server
 
 * admits an arrived request into its scene's queue,
-* forms a batch from whatever has arrived for one scene (up to ``max_views`` cameras of
-  any mix of sizes) -- one multi-camera call renders them together (C > 1, per-camera
-  tile lists, one launch per stage),
-* launches the batch on a free CUDA stream of a small pool, so batches of different
-  scenes overlap on the device, as long as the device memory the batch needs (its
-  buffers, sized from the request sizes) fits in the free-HBM budget left by the batches
-  in flight; otherwise the batch waits until enough in-flight work retires,
+* forms a batch from whatever has arrived: the scene whose oldest request has waited
+  longest first (up to ``max_views`` cameras of any mix of sizes, and at most 2048 tiles
+  per scene group so that its sort stays one counting pass), then, with ``max_groups`` > 1,
+  the next-oldest scenes while the batch has room.  Each scene group of the batch is one
+  multi-camera call (C > 1, per-camera tile lists, one launch per stage); the groups of a
+  batch run back to back on one stream and retire together,
+* launches the batch on a free CUDA stream of a small pool, so batches overlap on the
+  device, as long as the device memory the batch needs (its buffers, sized from the
+  request sizes) fits in the free-HBM budget left by the batches in flight; otherwise the
+  batch waits until enough in-flight work retires,
 * retires a batch when its stream's event completes: the images (already copied to
   pinned host memory on the batch's stream) are handed back and the batch's memory is
-  returned to the budget.
+  returned to the budget.  A scene group whose intersection lists outgrew their estimate
+  is rendered again with the exact size (at most ``max_retries`` times, admitted against
+  the memory budget like a new batch).
 
-The unbatched single-view path is the same loop with one stream and one view per batch.
-A camera's image does not depend on the batch it was rendered in (its tile lists hold
-only its own Gaussians, in the same order), so batching changes latency, never pixels.
+The unbatched single-view path is the same loop with one view per batch.  A camera's image
+does not depend on the batch it was rendered in (its tile lists hold only its own
+Gaussians, in the same order), so batching changes latency, never pixels.
 
 ``plan_batch`` holds the batching decision as a pure function so that it can be tested
 without a GPU.
@@ -55,6 +60,7 @@ class Result:
     launched: float
     done: float
     batch_views: int
+    batch: int = -1  # serial number of the batch that rendered it
 
     @property
     def latency(self) -> float:
@@ -65,28 +71,39 @@ class Result:
 # batching decision (pure)
 # --------------------------------------------------------------------------------------
 
-def plan_batch(queues: dict, max_views: int, budget_free: int, estimate):
-    """Pick the next batch.
+def plan_batch(queues: dict, max_views: int, budget_free: int, estimate, group_ok=None, max_groups: int = 8):
+    """Pick the next batch: a list of scene groups [(scene, requests), ...].
 
-    queues: scene id -> list of queued requests (arrival order).  The scene whose oldest
-    request has waited longest goes first; its batch takes queued requests in arrival order
-    while the batch has fewer than ``max_views`` cameras and its estimated device bytes
-    (``estimate(scene, requests)``) fit in ``budget_free``.  Returns (scene, requests) or
-    None when nothing fits (the caller waits for in-flight work to retire).
+    queues: scene id -> list of queued requests (arrival order).  Scenes are visited in the
+    order of their oldest request (longest wait first); each takes its queued requests in
+    arrival order while the batch has fewer than ``max_views`` cameras, the estimated device
+    bytes of all its groups (``estimate(scene, requests)`` per group) fit in ``budget_free``
+    and ``group_ok(scene, requests)`` (when given) accepts the group.  A request that the
+    group rule alone turns down is left for a later batch (it is taken first there).
+    Returns None when nothing fits (the caller waits for in-flight work to retire): the
+    oldest request of the oldest scene is never overtaken by younger ones.
     """
     order = sorted((q[0].arrival, sid) for sid, q in queues.items() if q)
+    groups, views, used = [], 0, 0
     for _, sid in order:
-        q = queues[sid]
+        if views >= max_views or len(groups) >= max_groups:
+            break
         take = []
-        for req in q[:max_views]:
-            if estimate(sid, take + [req]) > budget_free:
+        for req in queues[sid][:max_views - views]:
+            if take and group_ok is not None and not group_ok(sid, take + [req]):
+                break
+            if used + estimate(sid, take + [req]) > budget_free:
                 break
             take.append(req)
-        if take:
-            return sid, take
-        # the oldest request of this scene does not fit: do not let younger ones overtake it
-        return None
-    return None
+        if not take:
+            break  # the next scene's oldest request does not fit: the batch ends here
+        used += estimate(sid, take)
+        groups.append((sid, take))
+        views += len(take)
+        nxt = queues[sid][len(take)] if len(take) < len(queues[sid]) else None
+        if nxt is not None and views < max_views and (group_ok is None or group_ok(sid, take + [nxt])):
+            break  # this scene's next request did not fit the budget
+    return groups or None
 
 
 # --------------------------------------------------------------------------------------
@@ -138,25 +155,39 @@ def batch_bytes(scene: DeviceScene, cams, schedule: Schedule, capacity: int) -> 
 # --------------------------------------------------------------------------------------
 
 @dataclass
-class _Batch:
+class _Group:
     sid: int
     reqs: list
     pipe: FramePipeline
+    capacity: int
+    nbytes: int
+    host_off: int          # first float of this group's images in the batch's pinned buffer
+    k_slot: int            # index of this group's intersection count in the batch's count buffer
+    offsets: list = field(default_factory=list)
+
+
+@dataclass
+class _Batch:
+    groups: list
     stream: torch.cuda.Stream
     event: torch.cuda.Event
     host_img: torch.Tensor
     host_k: torch.Tensor
     nbytes: int
-    capacity: int
     launched: float
-    offsets: list = field(default_factory=list)
+    serial: int = -1
+
+    @property
+    def views(self) -> int:
+        return sum(len(g.reqs) for g in self.groups)
 
 
 class Server:
     """Continuous-batching render server (forward only) over ResidentScenes."""
 
     def __init__(self, store: ResidentScenes, schedule: Schedule = Schedule(), max_views: int = 8, streams: int = 4,
-                 budget_bytes: int | None = None, k_margin: float = 1.5):
+                 budget_bytes: int | None = None, k_margin: float = 1.5, max_retries: int = 3,
+                 max_group_tiles: int | None = 2048, max_groups: int = 1):
         self.store = store
         self.schedule = schedule
         self.max_views = max(1, min(int(max_views), _lib.GS_MAX_CAMERAS))
@@ -164,54 +195,78 @@ class Server:
         free, _ = torch.cuda.mem_get_info(store.device)
         self.budget = budget_bytes if budget_bytes is not None else max(0, free - store.reserve)
         self.k_margin = k_margin
+        self.max_retries = int(max_retries)
+        # a scene group's views share one sort: up to 2048 tiles it is the single counting pass
+        # over whole tile ids; more tiles take LSD passes over materialised lists, which cost
+        # more per view than rendering the views apart, so a group stays within that size
+        # (a single view above it still renders, alone)
+        self.max_group_tiles = max_group_tiles
+        # scene groups per batch: groups of different scenes share no GPU work (each is its own
+        # call), so by default a batch is one scene's views; more groups only pack the launches
+        self.max_groups = max(1, int(max_groups))
         self.overflows = 0
         self.batches = 0
+        self.groups = 0
         self.waits_for_memory = 0
         # pinned host buffers per stream (a stream carries one batch at a time): allocating
         # page-locked memory per batch costs milliseconds and stalls the loop
         self._pinned = {}
 
-    # capacity of a batch's intersection buffers from the scene's intersections per pixel
+    # capacity of a group's intersection buffers from the scene's intersections per pixel
     def _capacity(self, sid, reqs, hint=0):
         px = sum(r.camera.width * r.camera.height for r in reqs)
         est = int(px * self.store.k_rate[sid] * self.k_margin) + 65536
-        return max(est, int(hint))
+        return min(max(est, int(hint)), _lib.GS_MAX_INTERSECTIONS)
 
-    def _estimate(self, sid, reqs):
+    def _group_ok(self, sid, reqs):
+        if self.max_group_tiles is None:
+            return True
+        t = self.schedule.tile
+        tiles = sum(((r.camera.width + t - 1) // t) * ((r.camera.height + t - 1) // t) for r in reqs)
+        return tiles <= self.max_group_tiles
+
+    def _estimate(self, sid, reqs, hint=0):
         if not reqs:
             return 0
         cams = [r.camera for r in reqs]
-        return batch_bytes(self.store.scenes[sid], cams, self.schedule, self._capacity(sid, reqs))
+        return batch_bytes(self.store.scenes[sid], cams, self.schedule, self._capacity(sid, reqs, hint))
 
-    def _launch(self, sid, reqs, stream, now, hint=0):
-        scene = self.store.scenes[sid]
-        cams = [r.camera for r in reqs]
-        cap = self._capacity(sid, reqs, hint)
-        nbytes = batch_bytes(scene, cams, self.schedule, cap)
+    def _launch(self, groups, stream, now, hints=None):
+        """Render the scene groups [(scene, requests), ...] back to back on `stream`."""
+        hints = hints or [0] * len(groups)
+        pix = [sum(r.camera.width * r.camera.height for r in reqs) for _, reqs in groups]
+        host_img, host_k = self._host_buffers(stream, 3 * sum(pix), len(groups))
+        out, off, nbytes = [], 0, 0
         with torch.cuda.stream(stream):
-            pipe = FramePipeline(scene, cams, self.schedule, backward=False, capacity=cap)
-            pipe.forward()
-            host_img, host_k = self._host_buffers(stream, pipe.image.shape)
-            host_img.copy_(pipe.image, non_blocking=True)
-            host_k.copy_(pipe.K_out, non_blocking=True)
+            for k, ((sid, reqs), hint) in enumerate(zip(groups, hints)):
+                scene = self.store.scenes[sid]
+                cams = [r.camera for r in reqs]
+                cap = self._capacity(sid, reqs, hint)
+                nb = batch_bytes(scene, cams, self.schedule, cap)
+                pipe = FramePipeline(scene, cams, self.schedule, backward=False, capacity=cap)
+                pipe.forward()
+                n = pipe.image.numel()
+                host_img[off:off + n].copy_(pipe.image.view(-1), non_blocking=True)
+                host_k[k:k + 1].copy_(pipe.K_out, non_blocking=True)
+                out.append(_Group(sid, reqs, pipe, cap, nb, off, k, offsets=pipe.cams.pixel_offsets()))
+                off += n
+                nbytes += nb
             ev = torch.cuda.Event()
             ev.record(stream)
         self.batches += 1
-        return _Batch(sid, reqs, pipe, stream, ev, host_img, host_k, nbytes, cap, now,
-                      offsets=pipe.cams.pixel_offsets())
+        self.groups += len(groups)
+        return _Batch(out, stream, ev, host_img, host_k, nbytes, now, self.batches)
 
-    def _host_buffers(self, stream, shape):
-        """The stream's pinned image buffer (grown when a batch needs more) and count slot."""
-        n = 1
-        for d in shape:
-            n *= int(d)
+    def _host_buffers(self, stream, floats, groups):
+        """The stream's pinned image buffer (grown when a batch needs more) and count slots."""
         img, k = self._pinned.get(stream.cuda_stream, (None, None))
-        if img is None or img.numel() < n:  # grow geometrically: few page-locked allocations
-            img = torch.empty(max(n, 2 * (img.numel() if img is not None else 0), 1 << 20), dtype=torch.float32,
+        if img is None or img.numel() < floats:  # grow geometrically: few page-locked allocations
+            img = torch.empty(max(floats, 2 * (img.numel() if img is not None else 0), 1 << 20), dtype=torch.float32,
                               pin_memory=True)
-            k = k if k is not None else torch.empty(1, dtype=torch.int64, pin_memory=True)
-            self._pinned[stream.cuda_stream] = (img, k)
-        return img[:n].view(shape), k
+        if k is None or k.numel() < groups:
+            k = torch.empty(max(groups, _lib.GS_MAX_CAMERAS), dtype=torch.int64, pin_memory=True)
+        self._pinned[stream.cuda_stream] = (img, k)
+        return img, k
 
     def serve(self, requests, realtime=True, poll_sleep=50e-6):
         """Serve a trace; returns the results in completion order.  With realtime=False every
@@ -222,7 +277,7 @@ class Server:
         inflight: list[_Batch] = []
         reserved = 0
         results = []
-        retry: list = []  # (sid, reqs, capacity hint) of batches whose buffers overflowed
+        retry: list = []  # (scene, requests, capacity hint, attempts) of groups whose lists outgrew their buffers
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
         while pending or inflight or retry or any(queues.values()):
@@ -239,43 +294,56 @@ class Server:
                 free_streams.append(b.stream)
                 reserved -= b.nbytes
                 done = clock()
-                K = int(b.host_k.item())
-                px = sum(r.camera.width * r.camera.height for r in b.reqs)
-                if K > 0:  # learn the scene's intersections per pixel from every batch
-                    self.store.k_rate[b.sid] = max(self.store.k_rate[b.sid], K / px)
-                if K < 0 or K > b.capacity:
-                    self.overflows += 1
-                    retry.append((b.sid, b.reqs, int(max(K, b.capacity) * 1.1) + 1024))
-                else:
-                    img = b.host_img.numpy()
-                    for r, off in zip(b.reqs, b.offsets):
+                img = b.host_img.numpy()
+                for g in b.groups:
+                    K = int(b.host_k[g.k_slot].item())
+                    px = sum(r.camera.width * r.camera.height for r in g.reqs)
+                    if K > 0:  # learn the scene's intersections per pixel from every group
+                        self.store.k_rate[g.sid] = max(self.store.k_rate[g.sid], K / px)
+                    if K > g.capacity:
+                        self.overflows += 1
+                        attempts = getattr(g, "attempts", 0) + 1
+                        if attempts > self.max_retries:
+                            raise RuntimeError(f"scene {g.sid}: intersection lists still outgrew their buffers after "
+                                               f"{self.max_retries} retries")
+                        retry.append((g.sid, g.reqs, int(K * 1.1) + 1024, attempts))
+                        continue
+                    for r, off in zip(g.reqs, g.offsets):
                         P = r.camera.width * r.camera.height
-                        results.append(Result(r.rid, r.scene, img[off:off + P].reshape(r.camera.height,
+                        o = g.host_off + 3 * off
+                        results.append(Result(r.rid, r.scene, img[o:o + 3 * P].reshape(r.camera.height,
                                                                                        r.camera.width, 3).copy(),
-                                              r.arrival, b.launched, done, len(b.reqs)))
+                                              r.arrival, b.launched, done, b.views, b.serial))
                 del b
                 progressed = True
-            # launch: overflowed batches first, then new batches while streams and memory allow
+            # launch: overflowed groups first (each alone, admitted by memory), then new batches
             while free_streams and retry:
-                sid, reqs, hint = retry.pop(0)
-                st = free_streams.pop(0)
-                b = self._launch(sid, reqs, st, now, hint)
+                sid, reqs, hint, attempts = retry[0]
+                need = self._estimate(sid, reqs, hint)
+                if need > self.budget - reserved:
+                    if not inflight:
+                        raise MemoryError(f"scene {sid}: a retried group needs {need} bytes, the budget is "
+                                          f"{self.budget - reserved}")
+                    break  # wait for in-flight work to retire
+                retry.pop(0)
+                b = self._launch([(sid, reqs)], free_streams.pop(0), now, [hint])
+                b.groups[0].attempts = attempts
                 reserved += b.nbytes
                 inflight.append(b)
                 progressed = True
-            while free_streams:
-                plan = plan_batch(queues, self.max_views, self.budget - reserved, self._estimate)
+            while free_streams and not retry:
+                plan = plan_batch(queues, self.max_views, self.budget - reserved, self._estimate, self._group_ok,
+                                  self.max_groups)
                 if plan is None:
                     if any(queues.values()):
                         self.waits_for_memory += 1 if inflight else 0
                         if not inflight:
                             raise MemoryError("a single request does not fit in the memory budget")
                     break
-                sid, reqs = plan
-                for r in reqs:
-                    queues[sid].remove(r)
-                st = free_streams.pop(0)
-                b = self._launch(sid, reqs, st, now)
+                for sid, reqs in plan:
+                    for r in reqs:
+                        queues[sid].remove(r)
+                b = self._launch(plan, free_streams.pop(0), now)
                 reserved += b.nbytes
                 inflight.append(b)
                 progressed = True
@@ -325,4 +393,5 @@ def latency_summary(results, skip_before_s=0.0):
             "queue_wait_p50_ms": float(np.percentile(wait, 50)), "queue_wait_p99_ms": float(np.percentile(wait, 99)),
             "batch_time_p50_ms": float(np.percentile(service, 50)), "batch_time_p99_ms": float(np.percentile(service, 99)),
             "frames_per_s": float(lat.size / span) if span > 0 else None,
-            "mean_views_per_batch": float(np.mean([r.batch_views for r in kept]))}
+            "mean_views_per_batch": float(len(kept) / len({r.batch for r in kept})),
+            "mean_scenes_per_batch": float(len({(r.batch, r.scene) for r in kept}) / len({r.batch for r in kept}))}

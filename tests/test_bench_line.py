@@ -83,7 +83,7 @@ def test_result_line_is_short_and_carries_the_contract_fields():
         assert key in line["roofline"]
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert set(line["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
-    assert line["serving"]["batched"][1] > 0 and "multiview" in line and "memory" in line
+    assert line["serving"]["batch"][1] > 0 and "multiview" in line and "memory" in line
     # the whole record is still there, on stderr
     detail = [ln for ln in err.getvalue().splitlines() if ln.startswith("detail ")]
     assert json.loads(detail[0][len("detail "):]) == json.loads(json.dumps(full))

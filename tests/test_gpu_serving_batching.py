@@ -87,6 +87,23 @@ def test_served_images_are_the_same_alone_and_in_the_mix():
     assert_image_parity(out[req.rid].image.reshape(-1, 3), ref["image"].reshape(-1, 3))
 
 
+def test_a_batch_of_several_scenes_renders_each_view_as_alone():
+    """Requests of three scenes queued together form one batch (one multi-camera call per
+    scene group on one stream); every image equals the view rendered alone."""
+    store, _ = _store()
+    cams = synth.sphere_cameras(47, [(96, 64), (128, 96), (200, 120), (64, 48), (150, 90)])
+    trace = [serve.Request(i, i % 3, cam, 0.001 * i) for i, cam in enumerate(cams)]
+    srv = serve.Server(store, max_views=8, streams=1)
+    res = srv.serve(trace, realtime=False)
+    assert len(res) == len(trace) and srv.batches == 1 and srv.groups == 3
+    assert {r.batch for r in res} == {1} and all(r.batch_views == len(trace) for r in res)
+    s = serve.latency_summary(res)
+    assert s["mean_views_per_batch"] == len(trace) and s["mean_scenes_per_batch"] == 3
+    for r in res:
+        req = trace[r.rid]
+        np.testing.assert_array_equal(r.image, _alone(store.scenes[req.scene], req.camera))
+
+
 def test_unbatched_path_and_realtime_loop_give_the_same_images():
     store, _ = _store()
     trace = _trace(n=12, seed=45)
