@@ -88,12 +88,13 @@ def test_served_images_are_the_same_alone_and_in_the_mix():
 
 
 def test_a_batch_of_several_scenes_renders_each_view_as_alone():
-    """Requests of three scenes queued together form one batch (one multi-camera call per
-    scene group on one stream); every image equals the view rendered alone."""
+    """With cross-scene groups allowed, requests of three scenes queued together form one batch
+    (one multi-camera call per scene group on one stream); every image equals the view
+    rendered alone."""
     store, _ = _store()
     cams = synth.sphere_cameras(47, [(96, 64), (128, 96), (200, 120), (64, 48), (150, 90)])
     trace = [serve.Request(i, i % 3, cam, 0.001 * i) for i, cam in enumerate(cams)]
-    srv = serve.Server(store, max_views=8, streams=1)
+    srv = serve.Server(store, max_views=8, streams=1, max_groups=3)
     res = srv.serve(trace, realtime=False)
     assert len(res) == len(trace) and srv.batches == 1 and srv.groups == 3
     assert {r.batch for r in res} == {1} and all(r.batch_views == len(trace) for r in res)
