@@ -86,6 +86,9 @@ typedef struct gs_params {
     int32_t persistent;   /* compositing launch: 0 = one CTA per tile; 1 = as many CTAs as fit on the GPU,
                              each taking the next tile of tile_order (heaviest first) until none is left;
                              needs the tile_order of gs_tile_order.  Changes the schedule only. */
+    int32_t colors_shared; /* compositing: 0 = colors [C,N,ch], one row per (camera, Gaussian); 1 = colors
+                              [N,ch] shared by every camera (N-D features, App. C), and the backward's
+                              d_colors is [N,ch], accumulated over the cameras */
 } gs_params;
 
 GS_API void gs_default_params(gs_params *params);
@@ -274,7 +277,8 @@ GS_API gs_status gs_tile_order(const gs_camera *cams, int32_t C, const gs_params
 /* C += T * background.                                                      */
 /*                                                                          */
 /* in : tile_ranges, values (from gs_tile_bin_sort), radii [C,N],             */
-/*      means2d [C,N,2], conics [C,N,3], opacities [C,N], colors [C,N,ch],    */
+/*      means2d [C,N,2], conics [C,N,3], opacities [C,N], colors [C,N,ch]     */
+/*      ([N,ch] with params->colors_shared),                                 */
 /*      background: host array of `channels` floats or NULL (zeros)          */
 /* out: image [pixels, channels], final_T [pixels] (alpha = 1 - final_T),     */
 /*      last_contrib [pixels] int32 = number of list entries of the pixel's   */
@@ -310,7 +314,8 @@ GS_API gs_status gs_rasterize_fwd(const gs_camera *cams, int32_t C, int32_t N, c
 /* in : as gs_rasterize_fwd plus final_T, last_contrib from it, d_image       */
 /*      [pixels, channels], d_alpha [pixels] or NULL                         */
 /* out (accumulated, caller zeroes): d_means2d [C,N,2], d_conics [C,N,3],     */
-/*      d_opacities [C,N], d_colors [C,N,channels], absgrad [C,N,2] or NULL   */
+/*      d_opacities [C,N], d_colors [C,N,channels] ([N,channels], summed over */
+/*      the cameras, with params->colors_shared), absgrad [C,N,2] or NULL     */
 /* tile_order: as for gs_rasterize_fwd.                                      */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_rasterize_bwd(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,

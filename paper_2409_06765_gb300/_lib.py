@@ -50,7 +50,7 @@ class GsParams(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("batch_depth", ctypes.c_int32), ("antialiased", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32), ("eps2d", ctypes.c_float), ("near_plane", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("colors_shared", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -158,11 +158,12 @@ class CameraArray:
 
 
 def make_params(tile=16, batch_depth=256, antialiased=False, eps2d=0.3, near_plane=0.01, alpha_min=1.0 / 255.0,
-                alpha_max=0.99, T_min=1e-4, pixels_per_thread=0, persistent=False) -> GsParams:
+                alpha_max=0.99, T_min=1e-4, pixels_per_thread=0, persistent=False, colors_shared=False) -> GsParams:
     p = GsParams()
     p.tile, p.batch_depth, p.antialiased = int(tile), int(batch_depth), int(bool(antialiased))
     p.pixels_per_thread = int(pixels_per_thread)
     p.persistent = int(bool(persistent))
+    p.colors_shared = int(bool(colors_shared))
     p.eps2d, p.near_plane, p.alpha_min, p.alpha_max, p.T_min = eps2d, near_plane, alpha_min, alpha_max, T_min
     return p
 

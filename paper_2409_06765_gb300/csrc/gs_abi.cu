@@ -182,6 +182,8 @@ static gs_status check_params(const gs_params *p, RasterConsts &rc) {
     rc.tile_order = nullptr;
     rc.work = nullptr;
     if (p->persistent != 0 && p->persistent != 1) return fail_arg("persistent must be 0 or 1");
+    if (p->colors_shared != 0 && p->colors_shared != 1) return fail_arg("colors_shared must be 0 or 1");
+    rc.colors_shared = p->colors_shared;
     return GS_OK;
 }
 
@@ -210,6 +212,7 @@ void gs_default_params(gs_params *p) {
     p->antialiased = 0;
     p->pixels_per_thread = 0;
     p->persistent = 0;
+    p->colors_shared = 0;
     p->eps2d = 0.3f;
     p->near_plane = 0.01f;
     p->alpha_min = 1.f / 255.f;

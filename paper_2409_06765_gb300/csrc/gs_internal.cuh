@@ -53,6 +53,7 @@ struct BinSortLayout {
 struct RasterConsts {
     float eps2d, near_plane, alpha_min, alpha_max, T_min;
     int antialiased;
+    int colors_shared;      // compositing: colour rows indexed by Gaussian n (shared by the cameras)
     const int *tile_order;  // compositing: CTA b renders tile tile_order[b] (NULL: tile b)
     int *work;              // persistent compositing: [next index, CTAs finished] (NULL: one CTA per tile)
 };

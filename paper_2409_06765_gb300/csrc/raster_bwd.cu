@@ -44,7 +44,7 @@ __device__ __forceinline__ float transpose_sum(float (&v)[VP], int lane) {
 // Gradient slot of value index `idx` of Gaussian `id`:
 // [mean x, mean y, conic a, conic b, conic c, opacity, (absgrad x, absgrad y), colour 0..ch-1]
 template <bool ABSG>
-__device__ __forceinline__ float *grad_slot(int idx, int id, int ch, float *d_means2d, float *d_conics,
+__device__ __forceinline__ float *grad_slot(int idx, int id, int ch, int cmod, float *d_means2d, float *d_conics,
                                             float *d_opac, float *d_colors, float *absgrad) {
     if (idx < 2) return d_means2d + 2 * (size_t)id + idx;
     if (idx < 5) return d_conics + 3 * (size_t)id + (idx - 2);
@@ -53,8 +53,8 @@ __device__ __forceinline__ float *grad_slot(int idx, int id, int ch, float *d_me
         if (idx < 8) return absgrad + 2 * (size_t)id + (idx - 6);
         idx -= 2;
     }
-    const int q = idx - 6;
-    return q < ch ? d_colors + (size_t)id * ch + q : nullptr;
+    const int q = idx - 6;  // colour rows: per (camera, Gaussian), or per Gaussian (cmod = N) when shared
+    return q < ch ? d_colors + (size_t)(cmod ? id % cmod : id) * ch + q : nullptr;
 }
 
 // Factor applied to the warp total of value `idx`: 1 / log2(e) for the mean (and absgrad)
@@ -75,7 +75,7 @@ __host__ __device__ constexpr bool scaled_grad() {
 
 // Reduces values [OFF, min(OFF + 32, V)) of v over the warp and adds them to global memory.
 template <int V, int OFF, bool ABSG, bool SG>
-__device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int id, int ch, float *d_means2d,
+__device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int id, int ch, int cmod, float *d_means2d,
                                               float *d_conics, float *d_opac, float *d_colors, float *absgrad) {
     if constexpr (OFF < V) {
         constexpr int n = (V - OFF) < 32 ? (V - OFF) : 32;
@@ -87,10 +87,10 @@ __device__ __forceinline__ void reduce_chunks(const float (&v)[V], int lane, int
         constexpr int group = 32 / VP;
         const int idx = lane / group;
         if ((lane % group) == 0 && idx < n) {
-            float *slot = grad_slot<ABSG>(OFF + idx, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+            float *slot = grad_slot<ABSG>(OFF + idx, id, ch, cmod, d_means2d, d_conics, d_opac, d_colors, absgrad);
             if (slot) atomicAdd(slot, tot * total_scale<ABSG, SG>(OFF + idx));
         }
-        reduce_chunks<V, OFF + 32, ABSG, SG>(v, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+        reduce_chunks<V, OFF + 32, ABSG, SG>(v, lane, id, ch, cmod, d_means2d, d_conics, d_opac, d_colors, absgrad);
     }
 }
 
@@ -111,7 +111,7 @@ __host__ __device__ constexpr bool smem_reduce() {
 // group costs 8 stores, 2 loads, 2 shuffles and 9 adds per lane instead of a shuffle butterfly
 // with a select per value and step.  A group of at most two values uses plain butterflies.
 template <int V, int OFF, bool ABSG, bool SG>
-__device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, int lane, int id, int ch,
+__device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, int lane, int id, int ch, int cmod,
                                             float *d_means2d, float *d_conics, float *d_opac, float *d_colors,
                                             float *absgrad) {
     if constexpr (OFF < V) {
@@ -123,7 +123,7 @@ __device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, i
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 if (lane == 8 * i) {
-                    float *slot = grad_slot<ABSG>(OFF + i, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+                    float *slot = grad_slot<ABSG>(OFF + i, id, ch, cmod, d_means2d, d_conics, d_opac, d_colors, absgrad);
                     if (slot) atomicAdd(slot, x * total_scale<ABSG, SG>(OFF + i));
                 }
             }
@@ -142,11 +142,12 @@ __device__ __forceinline__ void reduce_smem(const float (&v)[V], float *s_red, i
             t += __shfl_xor_sync(0xffffffffu, t, 1);
             t += __shfl_xor_sync(0xffffffffu, t, 2);
             if (c == 0 && q < n) {
-                float *slot = grad_slot<ABSG>(OFF + q, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+                float *slot = grad_slot<ABSG>(OFF + q, id, ch, cmod, d_means2d, d_conics, d_opac, d_colors, absgrad);
                 if (slot) atomicAdd(slot, t * total_scale<ABSG, SG>(OFF + q));
             }
         }
-        reduce_smem<V, OFF + 8, ABSG, SG>(v, s_red, lane, id, ch, d_means2d, d_conics, d_opac, d_colors, absgrad);
+        reduce_smem<V, OFF + 8, ABSG, SG>(v, s_red, lane, id, ch, cmod, d_means2d, d_conics, d_opac, d_colors,
+                                          absgrad);
     }
 }
 
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     const int2 rg = ranges[gt];
     const int count = min(s_max, rg.y - rg.x);  // last_contrib never exceeds the list length
     const int cn_total = cs.C * cs.N;
+    const int cmod = rc.colors_shared ? cs.N : 0;
     const float amax = rc.alpha_max, amin = rc.alpha_min;
 
     for (int b0 = 0; b0 < count; b0 += batch) {
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
             s_g[s] = gg;
             s_h[s] = hh;
             s_b[s] = bb;
-            const float *col = colors + (size_t)id * ch;
+            const float *col = colors + (size_t)(rc.colors_shared ? id % cs.N : id) * ch;
 #pragma unroll
             for (int q = 0; q < C4; ++q) {
                 float4 v;
@@ -355,11 +357,11 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 if constexpr (smem_reduce<PPT>())
-                    reduce_smem<V, 0, ABSG, SG>(v, s_red, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics,
-                                                d_opac, d_colors, absgrad);
+                    reduce_smem<V, 0, ABSG, SG>(v, s_red, lane, __float_as_int(hh4.w), ch, cmod, d_means2d,
+                                                d_conics, d_opac, d_colors, absgrad);
                 else
-                    reduce_chunks<V, 0, ABSG, SG>(v, lane, __float_as_int(hh4.w), ch, d_means2d, d_conics, d_opac,
-                                                  d_colors, absgrad);
+                    reduce_chunks<V, 0, ABSG, SG>(v, lane, __float_as_int(hh4.w), ch, cmod, d_means2d, d_conics,
+                                                  d_opac, d_colors, absgrad);
             }
         }
     }

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
             s_g[s] = g;
             s_h[s] = h;
             s_b[s] = b;
-            const float *col = colors + (size_t)id * ch;
+            const float *col = colors + (size_t)(rc.colors_shared ? id % cs.N : id) * ch;
 #pragma unroll
             for (int q = 0; q < C4; ++q) {
                 float4 v;

@@ -42,16 +42,16 @@ class RasterSettings:
     persistent: bool = False        # compositing as persistent launches over tile_schedule's order
     bwd_persistent: bool = False
 
-    def params(self) -> _lib.GsParams:
+    def params(self, colors_shared=False) -> _lib.GsParams:
         return _cached_params(self.tile, self.batch_depth, bool(self.antialiased), self.eps2d, self.near_plane,
                               self.alpha_min, self.alpha_max, self.T_min, self.pixels_per_thread,
-                              bool(self.persistent and self.tile_schedule))
+                              bool(self.persistent and self.tile_schedule), bool(colors_shared))
 
-    def params_bwd(self) -> _lib.GsParams:
+    def params_bwd(self, colors_shared=False) -> _lib.GsParams:
         return _cached_params(self.tile, self.bwd_batch_depth or self.batch_depth, bool(self.antialiased), self.eps2d,
                               self.near_plane, self.alpha_min, self.alpha_max, self.T_min,
                               self.bwd_pixels_per_thread or self.pixels_per_thread,
-                              bool(self.bwd_persistent and self.tile_schedule))
+                              bool(self.bwd_persistent and self.tile_schedule), bool(colors_shared))
 
 
 _PARAMS: dict = {}
@@ -61,8 +61,9 @@ def _cached_params(*key) -> _lib.GsParams:
     """One launch-parameter struct per distinct setting (the calls only read it)."""
     p = _PARAMS.get(key)
     if p is None:
-        tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent = key
-        p = _lib.make_params(tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent=persistent)
+        tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent, shared = key
+        p = _lib.make_params(tile, batch, aa, eps2d, near, amin, amax, tmin, ppt, persistent=persistent,
+                             colors_shared=shared)
         if len(_PARAMS) < 256:
             _PARAMS[key] = p
     return p
@@ -239,7 +240,9 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
         if side is not None:
             torch.cuda.current_stream(means.device).wait_stream(side)
             side = None
-        image, final_T, last, blends = rasterize_fwd(cams, N, params, ch, bs["ranges"], bs["values"], sp["radii"],
+        # features [N, D] are shared by every camera: the kernels index their rows by Gaussian
+        rparams = settings.params(colors_shared=True) if colors.dim() == 2 else params
+        image, final_T, last, blends = rasterize_fwd(cams, N, rparams, ch, bs["ranges"], bs["values"], sp["radii"],
                                                      sp["means2d"], sp["conics"], sp["opacities"], colors,
                                                      settings.background, count_blends, order)
         if defer_sync:
@@ -273,8 +276,7 @@ class RasterizeGaussians(torch.autograd.Function):
             raise ValueError("depth rendering needs SH colours")
         feats = None
         if not use_sh:
-            f = sh_or_features
-            feats = (f.unsqueeze(0).expand(cams.C, *f.shape) if f.dim() == 2 else f).contiguous()
+            feats = sh_or_features.contiguous()  # [N, D] shared by the cameras, or [C, N, D]
         if depth and settings.background is not None:
             settings = RasterSettings(**{**settings.__dict__, "background": tuple(settings.background)[:3] + (0.0,)})
         out = forward_pass(cams, means, quats, log_scales, opacity_logits, sh=sh_or_features if use_sh else None,
@@ -301,15 +303,17 @@ class RasterizeGaussians(torch.autograd.Function):
          last, image) = ctx.saved_tensors
         cams, settings = ctx.cams, ctx.settings
         params = settings.params()
-        params_bwd = settings.params_bwd()
+        shared = colors.dim() == 2  # features [N, D]: their gradient is summed over the cameras in the kernel
+        params_bwd = settings.params_bwd(colors_shared=shared)
         C, N = cams.C, means.shape[0]
         ch = colors.shape[-1]
         dev = means.device
-        g2d = torch.zeros(C * N * (6 + ch), device=dev)  # one memset for all accumulated 2D gradients
+        rows = N if shared else C * N
+        g2d = torch.zeros(C * N * 6 + rows * ch, device=dev)  # one memset for all accumulated 2D gradients
         d_means2d = g2d[:C * N * 2].view(C, N, 2)
         d_conics = g2d[C * N * 2:C * N * 5].view(C, N, 3)
         d_opac = g2d[C * N * 5:C * N * 6].view(C, N)
-        d_colors = g2d[C * N * 6:].view(C, N, ch)
+        d_colors = g2d[C * N * 6:].view(N, ch) if shared else g2d[C * N * 6:].view(C, N, ch)
         absgrad = torch.zeros(C, N, 2, device=dev) if settings.absgrad else None
         d_image = d_image.contiguous() if d_image is not None else torch.zeros(cams.num_pixels, ch, device=dev)
         d_alpha = d_alpha.contiguous() if d_alpha is not None else None
@@ -348,7 +352,7 @@ class RasterizeGaussians(torch.autograd.Function):
             d_feat = d_sh
         else:
             d_means.zero_()
-            d_feat = d_colors.sum(0) if ctx.feat_dim == 2 else d_colors
+            d_feat = d_colors  # [N, D] accumulated over the cameras by the kernel, or [C, N, D]
         d_quats = torch.empty(N, 4, device=dev)
         d_log_scales = torch.empty(N, 3, device=dev)
         d_logits = torch.empty(N, device=dev)

@@ -449,6 +449,37 @@ def test_nd_features_forward_and_backward():
     assert rel_l2(g[3].cpu().numpy(), g3["d_opacity_logits"]) < 1e-3
 
 
+def test_nd_features_shared_by_several_cameras():
+    """Features [N, D] seen by three cameras of ragged sizes: each image against the oracle, and
+    the feature gradient summed over the cameras inside the backward kernel against the sum of
+    the oracle's per-camera gradients."""
+    sc = synth.clustered_scene(3000, 43, sh_degree=0, log_scale_mu=-3.1)
+    cams = synth.sphere_cameras(43, [(120, 90), (77, 131), (160, 64)])
+    D = 5
+    rng = np.random.default_rng(7)
+    feats = rng.uniform(0, 1, (sc.n, D)).astype(np.float32)
+    d = dev_scene(sc)
+    leaves = [d["means"], d["quats"], d["log_scales"], d["opacity_logits"], torch.as_tensor(feats, device="cuda")]
+    for x in leaves:
+        x.requires_grad_(True)
+    imgs, _, _ = raster.rasterization(*leaves[:4], cameras=cams, features=leaves[4])
+    grads_in, ref_dc, ref_dm = [], 0.0, 0.0
+    for cam, img in zip(cams, imgs):
+        sp = oracle.project(sc, cam)
+        ref = oracle.render_splats(sp, feats.astype(np.float64), cam.width, cam.height)
+        assert_image_parity(img.reshape(-1, D).detach().cpu().numpy(), ref["color"], "features")
+        P = cam.width * cam.height
+        gimg = rng.uniform(-1, 1, (P, D)) / P
+        grads_in.append(torch.as_tensor(gimg.reshape(cam.height, cam.width, D), dtype=torch.float32, device="cuda"))
+        g2 = oracle.render_splats_bwd(sp, feats.astype(np.float64), cam.width, cam.height, gimg)
+        ref_dc = ref_dc + g2["d_colors"]
+        ref_dm = ref_dm + oracle.project_bwd(sc, cam, g2["d_means2d"], g2["d_conics"], g2["d_opacities"])["d_means"]
+    g = torch.autograd.grad(list(imgs), leaves, grads_in)
+    assert g[4].shape == (sc.n, D)
+    assert rel_l2(g[4].cpu().numpy(), ref_dc) < 1e-3
+    assert rel_l2(g[0].cpu().numpy(), ref_dm) < 1e-3
+
+
 def test_absgrad_matches_oracle():
     sc, cam = _mid_scene(n=5000, seed=51, deg=0)
     settings = raster.RasterSettings(absgrad=True)
