@@ -193,10 +193,14 @@ def measured_traffic(workload, kernel, sched):
         tr = json.load(fh)
     if tr.get("workload") != workload or tr.get("source_hash") != kernel_source_hash():
         return None
-    k = tr.get("kernels", {}).get(kernel)
-    if not k or k.get("schedule") != kernel_schedule(kernel, sched):
-        return None
-    return k.get("bytes")
+    entries = tr.get("kernels", {}).get(kernel) or []
+    if isinstance(entries, dict):
+        entries = [entries]
+    want = kernel_schedule(kernel, sched)
+    for k in entries:
+        if k.get("schedule") == want:
+            return k.get("bytes")
+    return None
 
 
 def job_totals(ms_step, blends, world, device):
