@@ -600,17 +600,27 @@ def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
     CN = C * N
     vis = int(torch.count_nonzero(kp.radii > 0).item())
     ncoef = 3 * (scene.sh_degree + 1) ** 2
-    tile_bits = max(1, int(np.ceil(np.log2(max(2, kp.ranges.shape[0])))))
-    tpasses = (tile_bits + 6) // 7
+    T = kp.ranges.shape[0]
+    tile_bits = max(1, int(np.ceil(np.log2(max(2, T)))))
+    tpasses = 1 if tile_bits <= 11 else (tile_bits + 7) // 8
+    if tpasses == 1:
+        # one counting pass that regenerates the slots from the pair records (count, place)
+        tile_sort = vis * 32 + K * 4
+    else:
+        # the first pass materialises (tile, value); each later one reads keys for its counts and
+        # reads and writes keys and values
+        tile_sort = vis * 32 + K * 8 + (tpasses - 1) * K * 20 + K * 4
     byt = {
         # means, quats, log-scales, logit in; means2d, depth, conic, radius, tiles, opacity out
         "project": N * 44 + CN * 36,
         # mean + radius of every pair, coefficients of the visible ones; colours out
         "sh": CN * 16 + vis * ncoef * 4 + CN * 12,
-        # depth keys (read depth, radius, mean2d; write key, value), 4 LSD passes over C*N pairs
-        # (histogram read of keys + read and write of keys and values), tile counting, emission
-        # of K (tile, id) pairs, tpasses LSD passes over K, ranges
-        "bin_sort": CN * 24 + 4 * CN * 20 + CN * 28 + K * 8 + tpasses * K * 20 + K * 4,
+        # depth keys (read depth, radius, mean2d; write key, value); 4 LSD passes: the first
+        # reads all C*N keys for its counts and keys + values to place, writing the visible pairs
+        # only; the middle two read 4 + 8 and write 8 B per visible pair, the last writes values
+        # only; tile counts (order, mean2d, radius in; count, rectangle out); offsets (count,
+        # rectangle in; 16-byte pair record out); the tile sort; the tile ranges
+        "bin_sort": CN * 24 + CN * 12 + vis * (8 + 2 * 20 + 16) + vis * 28 + vis * 28 + tile_sort + T * 8,
         # d_colors + mean + radius in, visible coefficients in; d_sh and d_means out
         "sh_bwd": CN * 16 + vis * (12 + ncoef * 4) + N * (ncoef * 4 + 12),
         # parameters + d_means in, 2D gradients + radius per pair in; d_quats, d_log_scales, d_logits, d_means out

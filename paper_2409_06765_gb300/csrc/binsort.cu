@@ -886,7 +886,6 @@ BinSortLayout binsort_layout(long long CN, long long Kcap, long long T) {
 }
 
 // One stable LSD pass (histogram, scan, rank + place) over blocks of WARPS * SEG items.
-// One stable LSD pass (histogram, scan, rank + place) over blocks of WARPS * SEG items.
 // `skewed`: most items share a few digits (the top bits of positive float depths), where lanes
 // OR-ing into one peer mask serialise and match.any ranks faster.
 template <class Src, int WARPS, int SEG, bool REORDER>

@@ -124,6 +124,27 @@ def test_bin_sort_bit_exact_uneven_cameras_and_ties():
         np.testing.assert_array_equal(ranges, ranges_r)
 
 
+@pytest.mark.parametrize("lo,hi", [(4.0, 4.0), (5.0, 5.02), (3.0, 9.0), (0.8, 11.2), (0.01, 1000.0)])
+def test_bin_sort_bit_exact_over_depth_ranges(lo, hi):
+    """Depth ranges that leave different bytes of the depth keys equal: equal depths (only the
+    index orders a tile's list), a narrow range (the top two bytes equal), [3, 9], [0.8, 11.2]
+    (four binary octaves) and [0.01, 1000] give the oracle's lists."""
+    sc, cam = _mid_scene(n=20000, seed=13)
+    ref = oracle.project(sc, cam)
+    m = ref["means2d"].astype(np.float32)[None]
+    r = ref["radii"][None]
+    rng = np.random.default_rng(14)
+    d = rng.choice(np.linspace(lo, hi, 997), r.shape).astype(np.float32)
+    d[0, :2] = (lo, hi)
+    d[0, 5::9] = d[0, 4]  # ties
+    keys_r, vals_r, ranges_r = oracle.bin_sort(m, d, r, [cam.width], [cam.height], 16)
+    K, keys, vals, ranges = _gpu_bin_sort([cam], m, d, r, 16)
+    assert K == len(keys_r)
+    np.testing.assert_array_equal(keys, keys_r)
+    np.testing.assert_array_equal(vals, vals_r)
+    np.testing.assert_array_equal(ranges, ranges_r)
+
+
 def test_bin_sort_capacity_overflow_reports_K_and_stays_in_bounds():
     sc, cam = _mid_scene(n=5000, seed=12)
     ref = oracle.project(sc, cam)
