@@ -239,10 +239,9 @@ def summary_line(full):
     roof.update(ops_per_blend=rl.get("ops_per_blend"), fwd_frac=_r((rl.get("fwd") or {}).get("frac"), 3),
                 bwd_frac=_r((rl.get("bwd") or {}).get("frac"), 3))
     sr = full["step_roofline"]
-    step = {"frac": _r(sr["frac"], 3), "ms": _r(sr["stages_ms"]),
-            **{k: [_r(v["ms"], 3), _r(v["frac"], 2)] for k, v in sr["stages"].items()}}
+    step = {"frac": _r(sr["frac"], 3), **{k: [_r(v["ms"], 3), _r(v["frac"], 2)] for k, v in sr["stages"].items()}}
     cfg = full["config"]
-    config = {k: cfg[k] for k in ("workload", "gaussians", "resolution", "tile", "intersections_K", "blends_per_view")}
+    config = {k: cfg[k] for k in ("workload", "resolution", "tile", "intersections_K", "blends_per_view")}
     config["l2"] = "inputs>L2,no flush"
     cpu = full.get("cpu_baseline")
     if cpu:
@@ -319,6 +318,8 @@ def run_ours(args):
                          tile_order=not args.no_tile_order, bwd_batch_depth=args.bwd_batch,
                          bwd_pixels_per_thread=args.bwd_ppt, persistent=bool(args.persistent & 1),
                          bwd_persistent=bool(args.persistent & 2))
+    if args.no_fused_fwd:
+        sched = Schedule(**{**sched.__dict__, "fused_fwd": False})
     kp = FramePipeline(dscene, cams, sched)
     rng = np.random.default_rng(5 + rank)
     target_np = rng.uniform(0.0, 1.0, (kp.P, 3)).astype(np.float32)
@@ -533,13 +534,12 @@ def measure_alu_peaks(torch, _lib, sm_count):
     return out
 
 
-STAGES = ("project", "sh", "bin_sort", "rasterize_fwd", "rasterize_bwd", "sh_bwd", "project_bwd")
-STAGES_FUSED = ("project", "sh", "bin_sort", "rasterize_fwd", "rasterize_bwd", "sh_project_bwd")
-
-
 def stages_of(kp):
-    """The stages of a pipeline: one camera runs the SH and projection backward as one kernel."""
-    return STAGES_FUSED if getattr(kp, "fused_bwd", False) else STAGES
+    """The stages of a pipeline: one camera may run the projection and SH colours as one kernel,
+    and the SH and projection backward as one kernel."""
+    fwd = ("project_sh",) if getattr(kp, "fused_fwd", False) else ("project", "sh")
+    bwd = ("sh_project_bwd",) if getattr(kp, "fused_bwd", False) else ("sh_bwd", "project_bwd")
+    return fwd + ("bin_sort", "rasterize_fwd", "rasterize_bwd") + bwd
 
 
 def stage_breakdown(kp, steps):
@@ -552,6 +552,9 @@ def stage_breakdown(kp, steps):
         "project": lambda: L.gs_project(kp.cams, sc.means, sc.quats, sc.log_scales, sc.opacity_logits, kp.params,
                                         kp.means2d, kp.depths, kp.conics, kp.radii, kp.tiles, kp.opac),
         "sh": lambda: L.gs_sh_eval(kp.cams, sc.sh_degree, sc.sh, sc.means, kp.radii, kp.colors),
+        "project_sh": lambda: L.gs_project_sh_eval(kp.cams, kp.params, sc.sh_degree, sc.sh, sc.means, sc.quats,
+                                                   sc.log_scales, sc.opacity_logits, kp.means2d, kp.depths,
+                                                   kp.conics, kp.radii, kp.tiles, kp.opac, kp.colors),
         "bin_sort": lambda: (L.gs_tile_bin_sort(kp.cams, kp.N, kp.params, kp.means2d, kp.depths, kp.radii,
                                                 kp.capacity, None, kp.values, kp.ranges, kp.K_out, kp.workspace),
                              kp.order is not None and L.gs_tile_order(kp.cams, kp.params, kp.ranges, kp.order)),
@@ -615,6 +618,9 @@ def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
         "project": N * 44 + CN * 36,
         # mean + radius of every pair, coefficients of the visible ones; colours out
         "sh": CN * 16 + vis * ncoef * 4 + CN * 12,
+        # one kernel for both (one camera): parameters once, coefficients of the visible ones;
+        # the splat and the colours out
+        "project_sh": N * 44 + CN * 36 + vis * ncoef * 4 + CN * 12,
         # depth keys (read depth, radius, mean2d; write key, value); 4 LSD passes: the first
         # reads all C*N keys for its counts and keys + values to place, writing the visible pairs
         # only; the middle two read 4 + 8 and write 8 B per visible pair, the last writes values
@@ -920,6 +926,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every stage directly instead of graph replays")
     ap.add_argument("--no-tile-order", action="store_true", help="composite tiles in index order (no gs_tile_order)")
+    ap.add_argument("--no-fused-fwd", action="store_true",
+                    help="one camera: projection and SH colours as two kernels (SH beside the sort)")
     ap.add_argument("--skip-next", action="store_true", help="skip the multi-view, memory and serving sections")
     ap.add_argument("--detail-out", default=None, help="also write the full result record (JSON) to this file")
     ap.add_argument("--serve-seconds", type=float, default=10.0)

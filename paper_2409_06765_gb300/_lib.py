@@ -30,7 +30,7 @@ EXPORTED = (
     "gs_sh_eval", "gs_tile_bin_sort_workspace", "gs_tile_bin_sort", "gs_rasterize_fwd", "gs_rasterize_bwd",
     "gs_sh_eval_bwd", "gs_project_bwd", "gs_kernel_launches", "gs_tile_bin_sort_noalloc", "gs_probe_peak",
     "gs_tile_order", "gs_sh_eval_depth", "gs_sh_eval_depth_bwd", "gs_expected_depth", "gs_expected_depth_bwd",
-    "gs_sh_project_bwd",
+    "gs_sh_project_bwd", "gs_project_sh_eval",
 )
 GS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_project_bwd": (_I32, [_CAM, _I32, _I32, _P, _P, _P, _P, _PAR, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                       _P, _P]),
             "gs_sh_project_bwd": (_I32, [_CAM, _I32, _I32, _PAR, _I32] + [_P] * 15 + [_P]),
+            "gs_project_sh_eval": (_I32, [_CAM, _I32, _I32, _PAR, _I32] + [_P] * 12 + [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -261,6 +262,20 @@ def gs_project(cams: CameraArray, means, quats, log_scales, opacity_logits, para
                            _dev(tiles_touched, "i32", "tiles_touched"), _dev(opacities, "f32", "opacities"),
                            _stream(stream))
     _check(st, "gs_project")
+
+
+def gs_project_sh_eval(cams: CameraArray, params: GsParams, sh_degree: int, sh, means, quats, log_scales,
+                       opacity_logits, means2d, depths, conics, radii, tiles_touched, opacities, colors, stream=None):
+    N = means.shape[0]
+    st = load().gs_project_sh_eval(cams.ptr, cams.C, N, ctypes.byref(params), sh_degree, _dev(sh, "f32", "sh"),
+                                   _dev(means, "f32", "means"), _dev(quats, "f32", "quats"),
+                                   _dev(log_scales, "f32", "log_scales"),
+                                   _dev(opacity_logits, "f32", "opacity_logits"), _dev(means2d, "f32", "means2d"),
+                                   _dev(depths, "f32", "depths"), _dev(conics, "f32", "conics"),
+                                   _dev(radii, "i32", "radii"), _dev(tiles_touched, "i32", "tiles_touched"),
+                                   _dev(opacities, "f32", "opacities"), _dev(colors, "f32", "colors"),
+                                   _stream(stream))
+    _check(st, "gs_project_sh_eval")
 
 
 def gs_sh_eval(cams: CameraArray, sh_degree: int, sh, means, radii, colors, stream=None):

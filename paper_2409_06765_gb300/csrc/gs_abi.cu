@@ -21,6 +21,9 @@ cudaError_t launch_sh_project_bwd(const CamSet &, const RasterConsts &, int, int
                                   const float *, const float *, const float *, const int *, const float *,
                                   const float *, const float *, const float *, float *, float *, float *, float *,
                                   float *, cudaStream_t);
+cudaError_t launch_project_sh_fwd(const CamSet &, const RasterConsts &, int, int, const float *, const float *,
+                                  const float *, const float *, const float *, float *, float *, float *, int *, int *,
+                                  float *, float *, cudaStream_t);
 cudaError_t launch_sh_bwd(const CamSet &, int, int, const float *, const float *, const int *, const float *, float *,
                           float *, float *, float *, cudaStream_t);
 cudaError_t launch_expected_depth(long long, const float *, int, int, const float *, float *, cudaStream_t);
@@ -274,6 +277,31 @@ gs_status gs_project(const gs_camera *cams, int32_t C, int32_t N, const float *m
     cudaError_t e = launch_project_fwd(cs, rc, N, means, quats, log_scales, opacity_logits, means2d, depths, conics,
                                        radii, tiles_touched, opacities, (cudaStream_t)stream);
     return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project");
+}
+
+gs_status gs_project_sh_eval(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
+                             int32_t sh_degree, const float *sh, const float *means, const float *quats,
+                             const float *log_scales, const float *opacity_logits, float *means2d, float *depths,
+                             float *conics, int32_t *radii, int32_t *tiles_touched, float *opacities, float *colors,
+                             void *stream) {
+    RasterConsts rc;
+    CamSet cs;
+    GS_TRY(check_params(params, rc));
+    GS_TRY(make_camset(cams, C, params->tile, cs));
+    GS_TRY(check_cn(C, N));
+    cs.N = N;
+    if (C != 1) return fail_arg("gs_project_sh_eval takes one camera (use gs_project + gs_sh_eval)");
+    if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
+    if (N == 0) return GS_OK;
+    GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(quats); GS_NONNULL(log_scales); GS_NONNULL(opacity_logits);
+    GS_NONNULL(means2d); GS_NONNULL(depths); GS_NONNULL(conics); GS_NONNULL(radii); GS_NONNULL(tiles_touched);
+    GS_NONNULL(opacities); GS_NONNULL(colors);
+    if (!aligned(quats, 16)) return fail_arg("quats must be 16-byte aligned");
+    if (!aligned(means2d, 8)) return fail_arg("means2d must be 8-byte aligned");
+    cudaError_t e = launch_project_sh_fwd(cs, rc, sh_degree, N, sh, means, quats, log_scales, opacity_logits, means2d,
+                                          depths, conics, radii, tiles_touched, opacities, colors,
+                                          (cudaStream_t)stream);
+    return e == cudaSuccess ? GS_OK : fail_cuda(e, "gs_project_sh_eval");
 }
 
 gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t sh_degree, const float *sh,

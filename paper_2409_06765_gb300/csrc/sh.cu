@@ -109,16 +109,91 @@ __device__ __forceinline__ void sh_basis_vjp(const ShConsts &k, float x, float y
     }
 }
 
-// Copies the coefficient rows of Gaussians [n0, n0+cnt) into shared memory at row stride STRIDE.
+// Coefficient rows in shared memory, one per thread's Gaussian.  Rows whose length F is a
+// multiple of 4 (degrees 1 and 3) are float4 rows at an odd float4 stride: each staging copy,
+// each read or write of a thread's own row and each write-back is one 16-byte access, free of
+// bank conflicts.  Other rows (degrees 0 and 2) are float rows at an odd float stride.
+template <int F>
+__host__ __device__ constexpr int row_stride() {
+    return F % 4 == 0 ? ((F / 4) | 1) * 4 : (F | 1);
+}
+
+// fn(e, row[e]) for e = 0 .. F-1 in order (16-byte reads for float4 rows).
+template <int F, class Fn>
+__device__ __forceinline__ void row_for_each(const float *row, Fn &&fn) {
+    if constexpr (F % 4 == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int j = 0; j < F / 4; ++j) {
+            const float4 t = r4[j];
+            fn(4 * j, t.x);
+            fn(4 * j + 1, t.y);
+            fn(4 * j + 2, t.z);
+            fn(4 * j + 3, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < F; ++e) fn(e, row[e]);
+    }
+}
+
+// row[e] = val(e), or row[e] += val(e) with ADD (16-byte accesses for float4 rows).
+template <int F, bool ADD, class Fn>
+__device__ __forceinline__ void row_write(float *row, Fn &&val) {
+    if constexpr (F % 4 == 0) {
+        float4 *r4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+        for (int j = 0; j < F / 4; ++j) {
+            float4 o = make_float4(val(4 * j), val(4 * j + 1), val(4 * j + 2), val(4 * j + 3));
+            if (ADD) {
+                const float4 t = r4[j];
+                o = make_float4(t.x + o.x, t.y + o.y, t.z + o.z, t.w + o.w);
+            }
+            r4[j] = o;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < F; ++e) row[e] = ADD ? row[e] + val(e) : val(e);
+    }
+}
+
+// Copies the coefficient rows of Gaussians [n0, n0+cnt) into shared memory (row_stride<F>).
 // NT threads each issue all their 16-byte loads before the first shared-memory store, so a
 // thread keeps up to ceil(NT F / 4 / NT) loads in flight instead of waiting on each in turn.
 // Rows whose flag in `ok` (shared memory, one per row) is zero are not read: their Gaussian is
 // culled in every camera, so neither its colour nor its gradient uses the coefficients.
-template <int F, int STRIDE, int NT>
+template <int F, int NT>
 __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cnt, float *s, bool vec_ok,
                                            const unsigned char *ok) {
+    constexpr int STRIDE = row_stride<F>();
     const int total = cnt * F;
-    if (vec_ok) {
+    if constexpr (F % 4 == 0) {
+        if (vec_ok) {  // one 16-byte load and one 16-byte store per float4 of a row
+            constexpr int F4 = F / 4, S4 = STRIDE / 4;
+            const int nvec = cnt * F4;
+            const float4 *src4 = reinterpret_cast<const float4 *>(src);
+            float4 *s4 = reinterpret_cast<float4 *>(s);
+            float4 q[F4];
+            unsigned take = 0u;  // bit j: load j is issued
+#pragma unroll
+            for (int j = 0; j < F4; ++j) {
+                const int v = threadIdx.x + j * NT;
+                if (v < nvec && ok[v / F4]) {
+                    q[j] = src4[v];
+                    take |= 1u << j;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < F4; ++j) {
+                const int v = threadIdx.x + j * NT;
+                if (take & (1u << j)) {
+                    const int row = v / F4;
+                    s4[row * S4 + (v - row * F4)] = q[j];
+                }
+            }
+            return;
+        }
+    } else if (vec_ok) {
         constexpr int V = (NT * F / 4 + NT - 1) / NT;  // float4 loads per thread for a full chunk
         const int nvec = total / 4;
         const float4 *src4 = reinterpret_cast<const float4 *>(src);
@@ -149,10 +224,48 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int cn
         }
         for (int e = nvec * 4 + threadIdx.x; e < total; e += NT)
             if (ok[e / F]) s[(e / F) * STRIDE + e % F] = src[e];
-    } else {
-        for (int e = threadIdx.x; e < total; e += NT)
-            if (ok[e / F]) s[(e / F) * STRIDE + e % F] = src[e];
+        return;
     }
+    for (int e = threadIdx.x; e < total; e += NT)
+        if (ok[e / F]) s[(e / F) * STRIDE + e % F] = src[e];
+}
+
+// Writes the shared rows of Gaussians [n0, n0+cnt) back to dst (contiguous [cnt, F]).
+template <int F, int NT>
+__device__ __forceinline__ void store_rows(float *__restrict__ dst, int cnt, const float *s) {
+    constexpr int STRIDE = row_stride<F>();
+    const int total = cnt * F;
+    const bool al = (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    if constexpr (F % 4 == 0) {
+        if (al) {
+            constexpr int F4 = F / 4, S4 = STRIDE / 4;
+            float4 *dst4 = reinterpret_cast<float4 *>(dst);
+            const float4 *s4 = reinterpret_cast<const float4 *>(s);
+            for (int v = threadIdx.x; v < cnt * F4; v += NT) {
+                const int row = v / F4;
+                dst4[v] = s4[row * S4 + (v - row * F4)];
+            }
+            return;
+        }
+    } else if (al) {
+        const int nvec = total / 4;
+        float4 *dst4 = reinterpret_cast<float4 *>(dst);
+        for (int v = threadIdx.x; v < nvec; v += NT) {
+            int e = 4 * v;
+            float4 o;
+            o.x = s[(e / F) * STRIDE + e % F];
+            ++e;
+            o.y = s[(e / F) * STRIDE + e % F];
+            ++e;
+            o.z = s[(e / F) * STRIDE + e % F];
+            ++e;
+            o.w = s[(e / F) * STRIDE + e % F];
+            dst4[v] = o;
+        }
+        for (int e = nvec * 4 + threadIdx.x; e < total; e += NT) dst[e] = s[(e / F) * STRIDE + e % F];
+        return;
+    }
+    for (int e = threadIdx.x; e < total; e += NT) dst[e] = s[(e / F) * STRIDE + e % F];
 }
 
 template <int DEG>
@@ -160,9 +273,9 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
                                                      const float *__restrict__ means, const int *__restrict__ radii,
                                                      const __grid_constant__ CamSet cs, ShConsts kc,
                                                      float *__restrict__ colors, const float *__restrict__ depths) {
-    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = row_stride<F>();
     const int OS = depths ? 4 : 3;  // (r, g, b) or (r, g, b, depth) per (camera, Gaussian)
-    extern __shared__ float s_coef[];
+    extern __shared__ __align__(16) float s_coef[];
     int n0 = blockIdx.x * 256;
     int cnt = min(256, N - n0);
     int n = n0 + threadIdx.x;
@@ -185,7 +298,7 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
     }
     __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    stage_rows<F, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
     __syncthreads();
     if (!valid) return;
     const float *cf = s_coef + threadIdx.x * STRIDE;
@@ -209,16 +322,11 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restr
         float il = rsqrtf(vx * vx + vy * vy + vz * vz);
         float Y[K];
         sh_eval_basis<DEG>(kc, vx * il, vy * il, vz * il, Y);
-        float r = 0.5f, g = 0.5f, b = 0.5f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            r += Y[k] * cf[3 * k];
-            g += Y[k] * cf[3 * k + 1];
-            b += Y[k] * cf[3 * k + 2];
-        }
-        out[0] = fmaxf(r, 0.f);
-        out[1] = fmaxf(g, 0.f);
-        out[2] = fmaxf(b, 0.f);
+        float acc[3] = {0.5f, 0.5f, 0.5f};  // element e = 3 k + channel, k ascending per channel
+        row_for_each<F>(cf, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
+        out[0] = fmaxf(acc[0], 0.f);
+        out[1] = fmaxf(acc[1], 0.f);
+        out[2] = fmaxf(acc[2], 0.f);
     }
 }
 
@@ -244,9 +352,9 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
                                                                float *__restrict__ d_sh, float *__restrict__ d_means,
                                                                float *__restrict__ d_depths,
                                                                float *__restrict__ d_viewmats) {
-    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = row_stride<F>();
     const int IS = d_depths ? 4 : 3;  // d_colors rows: (r, g, b) or (r, g, b, depth)
-    extern __shared__ float s_coef[];
+    extern __shared__ __align__(16) float s_coef[];
     __shared__ float s_red[(kShBwdThreads / 32) * 12];
     float *s_grad = ONECAM ? s_coef : s_coef + kShBwdThreads * STRIDE;
     const int n0 = blockIdx.x * kShBwdThreads;
@@ -273,12 +381,9 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
     }
     __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    stage_rows<F, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
     float *gr = s_grad + threadIdx.x * STRIDE;
-    if (!ONECAM) {
-#pragma unroll
-        for (int f = 0; f < F; ++f) gr[f] = 0.f;
-    }
+    if (!ONECAM) row_write<F, false>(gr, [](int) { return 0.f; });
     __syncthreads();
     const float *cf = s_coef + threadIdx.x * STRIDE;
     float dm[3] = {0.f, 0.f, 0.f};
@@ -288,10 +393,7 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
         const float *R = cs.cam[c].R, *t = cs.cam[c].t;
         const int rc = c == 0 ? r0 : (valid ? radii[idx] : 0);
         if (valid && d_depths) d_depths[idx] = rc > 0 ? (c == 0 ? g0[3] : d_colors[IS * idx + 3]) : 0.f;
-        if (ONECAM && valid && rc <= 0) {
-#pragma unroll
-            for (int f = 0; f < F; ++f) gr[f] = 0.f;
-        }
+        if (ONECAM && valid && rc <= 0) row_write<F, false>(gr, [](int) { return 0.f; });
         if (valid && rc > 0) {
             const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
             const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
@@ -301,30 +403,18 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
             const float x = vx * il, y = vy * il, z = vz * il;
             float Y[K];
             sh_eval_basis<DEG>(kc, x, y, z, Y);
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+            row_for_each<F>(cf, [&](int e, float v) { raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]); });
             float g[3];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                float raw = 0.5f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) raw += Y[k] * cf[3 * k + ch];
                 const float gin = c == 0 ? g0[ch] : d_colors[IS * idx + ch];
-                g[ch] = raw > 0.f ? gin : 0.f;  // the clamp at 0 passes no gradient
+                g[ch] = raw[ch] > 0.f ? gin : 0.f;  // the clamp at 0 passes no gradient
             }
-            float w[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) w[k] = cf[3 * k] * g[0] + cf[3 * k + 1] * g[1] + cf[3 * k + 2] * g[2];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {  // (in place: every read of the row is above)
-                if (ONECAM) {
-                    gr[3 * k] = Y[k] * g[0];
-                    gr[3 * k + 1] = Y[k] * g[1];
-                    gr[3 * k + 2] = Y[k] * g[2];
-                } else {
-                    gr[3 * k] += Y[k] * g[0];
-                    gr[3 * k + 1] += Y[k] * g[1];
-                    gr[3 * k + 2] += Y[k] * g[2];
-                }
-            }
+            float w[K];  // w_k = sum over channels of coeff_k,ch g_ch
+            row_for_each<F>(cf, [&](int e, float v) { w[e / 3] = e % 3 ? fmaf(v, g[e % 3], w[e / 3]) : v * g[0]; });
+            // (in place: every read of the row is above)
+            row_write<F, !ONECAM>(gr, [&](int e) { return Y[e / 3] * g[e % 3]; });
             if (DEG > 0) {
                 float dd[3] = {0.f, 0.f, 0.f};
                 sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
@@ -356,27 +446,7 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
         d_means[3 * n + 2] = dm[2];
     }
     __syncthreads();
-    float *dst = d_sh + (size_t)n0 * F;
-    const int total = cnt * F;
-    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-        const int nvec = total / 4;
-        float4 *dst4 = reinterpret_cast<float4 *>(dst);
-        for (int v = threadIdx.x; v < nvec; v += kShBwdThreads) {
-            int e = 4 * v;
-            float4 q;
-            q.x = s_grad[(e / F) * STRIDE + e % F];
-            ++e;
-            q.y = s_grad[(e / F) * STRIDE + e % F];
-            ++e;
-            q.z = s_grad[(e / F) * STRIDE + e % F];
-            ++e;
-            q.w = s_grad[(e / F) * STRIDE + e % F];
-            dst4[v] = q;
-        }
-        for (int e = nvec * 4 + threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_grad[(e / F) * STRIDE + e % F];
-    } else {
-        for (int e = threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_grad[(e / F) * STRIDE + e % F];
-    }
+    store_rows<F, kShBwdThreads>(d_sh + (size_t)n0 * F, cnt, s_grad);
 }
 
 // SH backward and projection backward of one camera in one kernel: the coefficient rows
@@ -393,8 +463,8 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
     const float2 *__restrict__ d_means2d, const float *__restrict__ d_conics, const float *__restrict__ d_opac,
     float *__restrict__ d_sh, float *__restrict__ d_means, float4 *__restrict__ d_quats,
     float *__restrict__ d_log_scales, float *__restrict__ d_logits) {
-    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = F | 1;
-    extern __shared__ float s_coef[];
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = row_stride<F>();
+    extern __shared__ __align__(16) float s_coef[];
     __shared__ unsigned char s_ok[kShBwdThreads];
     const int n0 = blockIdx.x * kShBwdThreads;
     const int cnt = min(kShBwdThreads, N - n0);
@@ -431,7 +501,7 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
     s_ok[threadIdx.x] = vis;
     __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, STRIDE, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    stage_rows<F, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
     __syncthreads();
     float *row = s_coef + threadIdx.x * STRIDE;  // coefficients, then (in place) their gradient
     const CamDev &cam = cs.cam[0];
@@ -446,23 +516,15 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
         const float x = vx * il, y = vy * il, z = vz * il;
         float Y[K];
         sh_eval_basis<DEG>(kc, x, y, z, Y);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        row_for_each<F>(row, [&](int e, float v) { raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]); });
         float g[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float raw = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) raw += Y[k] * row[3 * k + ch];
-            g[ch] = raw > 0.f ? g0[ch] : 0.f;  // the clamp at 0 passes no gradient
-        }
-        float w[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) w[k] = row[3 * k] * g[0] + row[3 * k + 1] * g[1] + row[3 * k + 2] * g[2];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {  // (in place: every read of the row is above)
-            row[3 * k] = Y[k] * g[0];
-            row[3 * k + 1] = Y[k] * g[1];
-            row[3 * k + 2] = Y[k] * g[2];
-        }
+        for (int ch = 0; ch < 3; ++ch) g[ch] = raw[ch] > 0.f ? g0[ch] : 0.f;  // the clamp at 0 passes no gradient
+        float w[K];  // w_k = sum over channels of coeff_k,ch g_ch
+        row_for_each<F>(row, [&](int e, float v) { w[e / 3] = e % 3 ? fmaf(v, g[e % 3], w[e / 3]) : v * g[0]; });
+        // (in place: every read of the row is above)
+        row_write<F, false>(row, [&](int e) { return Y[e / 3] * g[e % 3]; });
         if (DEG > 0) {
             float dd[3] = {0.f, 0.f, 0.f};
             sh_basis_vjp<DEG>(kc, x, y, z, w, dd);
@@ -472,8 +534,7 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
             dm[2] = (dd[2] - z * p) * il;
         }
     } else if (valid) {
-#pragma unroll
-        for (int f = 0; f < F; ++f) row[f] = 0.f;
+        row_write<F, false>(row, [](int) { return 0.f; });
     }
     if (valid) {
         float dls[3] = {0.f, 0.f, 0.f}, dl = 0.f;
@@ -500,33 +561,97 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
         d_logits[n] = dl;
     }
     __syncthreads();
-    float *dst = d_sh + (size_t)n0 * F;
-    const int total = cnt * F;
-    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-        const int nvec = total / 4;
-        float4 *dst4 = reinterpret_cast<float4 *>(dst);
-        for (int v = threadIdx.x; v < nvec; v += kShBwdThreads) {
-            int e = 4 * v;
-            float4 o;
-            o.x = s_coef[(e / F) * STRIDE + e % F];
-            ++e;
-            o.y = s_coef[(e / F) * STRIDE + e % F];
-            ++e;
-            o.z = s_coef[(e / F) * STRIDE + e % F];
-            ++e;
-            o.w = s_coef[(e / F) * STRIDE + e % F];
-            dst4[v] = o;
+    store_rows<F, kShBwdThreads>(d_sh + (size_t)n0 * F, cnt, s_coef);
+}
+
+// Projection and SH colour of one camera in one kernel (App. C.1): each thread projects its
+// Gaussian and writes the splat, the CTA then streams into shared memory the coefficient
+// rows of the Gaussians the camera sees (as sh_fwd_kernel does), and each thread evaluates its
+// colour.  The mean is read once for both, and the visibility decided by the projection
+// picks the rows without reading the radii back.
+template <int DEG>
+__global__ void __launch_bounds__(256) project_sh_fwd_kernel(
+    int N, const float *__restrict__ sh, const float *__restrict__ means, const float4 *__restrict__ quats,
+    const float *__restrict__ log_scales, const float *__restrict__ logits, const __grid_constant__ CamSet cs,
+    ShConsts kc, RasterConsts rc, float2 *__restrict__ means2d, float *__restrict__ depths,
+    float *__restrict__ conics, int *__restrict__ radii, int *__restrict__ tiles_touched, float *__restrict__ opac,
+    float *__restrict__ colors) {
+    constexpr int K = (DEG + 1) * (DEG + 1), F = 3 * K, STRIDE = row_stride<F>();
+    extern __shared__ __align__(16) float s_coef[];
+    __shared__ unsigned char s_ok[256];
+    const int n0 = blockIdx.x * 256;
+    const int cnt = min(256, N - n0);
+    const int n = n0 + threadIdx.x;
+    const bool valid = n < N;
+    const CamDev &cam = cs.cam[0];
+    float mean[3] = {0.f, 0.f, 0.f};
+    int r = 0;
+    if (valid) {
+        mean[0] = means[3 * n];
+        mean[1] = means[3 * n + 1];
+        mean[2] = means[3 * n + 2];
+        Gauss3 g;
+        load_gauss(n, log_scales, quats, logits, g);
+        Splat2 sp;
+        const bool ok = splat_of(g, mean, cam, rc, sp);
+        r = ok ? radius_of(sp) : 0;
+        int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+        if (r > 0 && !pixel_box(sp.mx, sp.my, r, cam.W, cam.H, x0, x1, y0, y1)) r = 0;
+        if (r > 0) {
+            const int tile = cs.tile;
+            means2d[n] = make_float2(sp.mx, sp.my);
+            depths[n] = sp.t[2];
+            conics[3 * n] = sp.conic[0];
+            conics[3 * n + 1] = sp.conic[1];
+            conics[3 * n + 2] = sp.conic[2];
+            radii[n] = r;
+            tiles_touched[n] = (x1 / tile - x0 / tile + 1) * (y1 / tile - y0 / tile + 1);
+            opac[n] = g.o * sp.comp;
+        } else {
+            means2d[n] = make_float2(0.f, 0.f);
+            depths[n] = 0.f;
+            conics[3 * n] = 0.f;
+            conics[3 * n + 1] = 0.f;
+            conics[3 * n + 2] = 0.f;
+            radii[n] = 0;
+            tiles_touched[n] = 0;
+            opac[n] = 0.f;
         }
-        for (int e = nvec * 4 + threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_coef[(e / F) * STRIDE + e % F];
-    } else {
-        for (int e = threadIdx.x; e < total; e += kShBwdThreads) dst[e] = s_coef[(e / F) * STRIDE + e % F];
     }
+    s_ok[threadIdx.x] = r > 0;
+    __syncthreads();
+    const float *src = sh + (size_t)n0 * F;
+    stage_rows<F, 256>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    __syncthreads();
+    if (!valid) return;
+    float *out = colors + 3 * (size_t)n;
+    if (r == 0) {
+        out[0] = 0.f;
+        out[1] = 0.f;
+        out[2] = 0.f;
+        return;
+    }
+    const float *cf = s_coef + threadIdx.x * STRIDE;
+    const float *R = cam.R, *t = cam.t;
+    // camera centre = -R^T t
+    const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
+    const float oy = -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]);
+    const float oz = -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]);
+    const float vx = mean[0] - ox, vy = mean[1] - oy, vz = mean[2] - oz;
+    const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float Y[K];
+    sh_eval_basis<DEG>(kc, vx * il, vy * il, vz * il, Y);
+    float acc[3] = {0.5f, 0.5f, 0.5f};  // element e = 3 k + channel, k ascending per channel
+    row_for_each<F>(cf, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
+    out[0] = fmaxf(acc[0], 0.f);
+    out[1] = fmaxf(acc[1], 0.f);
+    out[2] = fmaxf(acc[2], 0.f);
 }
 
 template <int DEG>
 static cudaError_t launch_sh_fwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
                                    float *colors, const float *depths, cudaStream_t st) {
-    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = row_stride<F>();
     size_t smem = 256 * STRIDE * sizeof(float);
     if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
         cudaError_t e = ensure_smem((const void *)sh_fwd_kernel<DEG>, (int)smem);
@@ -541,7 +666,7 @@ template <int DEG>
 static cudaError_t launch_sh_bwd_t(const CamSet &cs, int N, const float *sh, const float *means, const int *radii,
                                    const float *d_colors, float *d_sh, float *d_means, float *d_depths,
                                    float *d_viewmats, cudaStream_t st) {
-    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = row_stride<F>();
     const bool one = cs.C == 1;
     size_t smem = (one ? 1 : 2) * kShBwdThreads * STRIDE * sizeof(float);
     auto kern = one ? sh_bwd_kernel<DEG, true> : sh_bwd_kernel<DEG, false>;
@@ -577,13 +702,49 @@ cudaError_t launch_sh_bwd(const CamSet &cs, int deg, int N, const float *sh, con
 }
 
 template <int DEG>
+static cudaError_t launch_project_sh_fwd_t(const CamSet &cs, const RasterConsts &rc, int N, const float *sh,
+                                           const float *means, const float *quats, const float *log_scales,
+                                           const float *logits, float *means2d, float *depths, float *conics,
+                                           int *radii, int *tiles_touched, float *opac, float *colors,
+                                           cudaStream_t st) {
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = row_stride<F>();
+    const size_t smem = 256 * STRIDE * sizeof(float);
+    auto kern = project_sh_fwd_kernel<DEG>;
+    if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+        cudaError_t e = ensure_smem((const void *)kern, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(N + 255) / 256, 256, smem, st>>>(N, sh, means, (const float4 *)quats, log_scales, logits, cs,
+                                             make_sh_consts(), rc, (float2 *)means2d, depths, conics, radii,
+                                             tiles_touched, opac, colors);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_sh_fwd(const CamSet &cs, const RasterConsts &rc, int deg, int N, const float *sh,
+                                  const float *means, const float *quats, const float *log_scales,
+                                  const float *logits, float *means2d, float *depths, float *conics, int *radii,
+                                  int *tiles_touched, float *opac, float *colors, cudaStream_t st) {
+#define GS_PSF(D)                                                                                                  \
+    return launch_project_sh_fwd_t<D>(cs, rc, N, sh, means, quats, log_scales, logits, means2d, depths, conics,   \
+                                      radii, tiles_touched, opac, colors, st)
+    switch (deg) {
+        case 0: GS_PSF(0);
+        case 1: GS_PSF(1);
+        case 2: GS_PSF(2);
+        default: GS_PSF(3);
+    }
+#undef GS_PSF
+}
+
+template <int DEG>
 static cudaError_t launch_sh_project_bwd_t(const CamSet &cs, const RasterConsts &rc, int N, const float *sh,
                                            const float *means, const float *quats, const float *log_scales,
                                            const float *logits, const int *radii, const float *d_colors,
                                            const float *d_means2d, const float *d_conics, const float *d_opac,
                                            float *d_sh, float *d_means, float *d_quats, float *d_log_scales,
                                            float *d_logits, cudaStream_t st) {
-    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = F | 1;
+    constexpr int F = 3 * (DEG + 1) * (DEG + 1), STRIDE = row_stride<F>();
     const size_t smem = kShBwdThreads * STRIDE * sizeof(float);
     auto kern = sh_project_bwd_kernel<DEG>;
     if (smem + 1024 > 48 * 1024) {  // dynamic + static shared memory above the default limit

@@ -38,6 +38,7 @@ class Schedule:
     persistent: bool = False      # forward compositing as one persistent launch (needs tile_order)
     bwd_persistent: bool = False  # backward likewise
     fused_bwd: bool = True        # one camera: SH and projection backward as one kernel
+    fused_fwd: bool = True        # one camera: projection and SH colours as one kernel
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
@@ -53,7 +54,7 @@ class Schedule:
                     bwd_batch_depth=self.bwd_batch_depth or self.batch_depth,
                     bwd_pixels_per_thread=self.bwd_pixels_per_thread or self.pixels_per_thread,
                     tile_order=self.tile_order, persistent=self.persistent, bwd_persistent=self.bwd_persistent,
-                    fused_bwd=self.fused_bwd)
+                    fused_bwd=self.fused_bwd, fused_fwd=self.fused_fwd)
 
 
 class DeviceScene:
@@ -163,18 +164,29 @@ class FramePipeline:
         return total
 
     # -- stages ----------------------------------------------------------------------------
+    @property
+    def fused_fwd(self) -> bool:
+        return self.C == 1 and self.schedule.fused_fwd
+
     def _pre(self):
         # project, then SH colours (and the zeroing of the 2D gradient buffer) on a side stream
         # while the bin/sort runs on this one: the SH kernel streams coefficients from HBM while
         # the sort's many short, latency-bound kernels leave bandwidth idle; both only need the
-        # projection, and the compositing waits for both
+        # projection, and the compositing waits for both.  One camera: projection and colours
+        # as one kernel before the sort.
         s, L = self.scene, _lib
         main = torch.cuda.current_stream(self.device)
-        L.gs_project(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.means2d,
-                     self.depths, self.conics, self.radii, self.tiles, self.opac)
+        if self.fused_fwd:
+            L.gs_project_sh_eval(self.cams, self.params, s.sh_degree, s.sh, s.means, s.quats, s.log_scales,
+                                 s.opacity_logits, self.means2d, self.depths, self.conics, self.radii, self.tiles,
+                                 self.opac, self.colors)
+        else:
+            L.gs_project(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.means2d,
+                         self.depths, self.conics, self.radii, self.tiles, self.opac)
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
-            L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
+            if not self.fused_fwd:
+                L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
             if self.with_backward:
                 self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
         L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity, None,

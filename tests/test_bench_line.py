@@ -44,7 +44,8 @@ def _full_record():
                      "bwd": {"ms": 0.797, "gop_s": 29876.5, "frac": 0.7418}, "frac_at_sampled_clock": 0.7418,
                      "probe": {"ffma_gop_s": 39200.0, "ex2_gop_s": 10000.0, "frac_of_ffma_probe": 0.76}},
         "step_roofline": {"bound_ms": 1.43, "stages_ms": 2.09, "frac": 0.68,
-                          "stages": {k: dict(stage) for k in bench.STAGES_FUSED}, "note": "z" * 150},
+                          "stages": {k: dict(stage) for k in ("project", "sh", "bin_sort", "rasterize_fwd",
+                                                                        "rasterize_bwd", "sh_bwd", "project_bwd")}, "note": "z" * 150},
         "peaks": {"source": "measured", "hbm_gbs": 6764.0},
         "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 12, "scope": "timed region",
                    "power_w_max": 640.0},

@@ -61,6 +61,61 @@ def test_sh_matches_oracle(deg):
     assert (out["colors"][0].cpu().numpy()[~vis] == 0).all()
 
 
+def _fused_project_sh(sc, cam, aa=False):
+    """gs_project_sh_eval (one kernel) beside gs_project + gs_sh_eval (two), same inputs."""
+    d = dev_scene(sc)
+    ca = _lib.CameraArray([cam])
+    p = _lib.make_params(tile=16, antialiased=aa)
+    N = d["means"].shape[0]
+    outs = []
+    for fused in (True, False):
+        o = dict(means2d=torch.full((N, 2), 7.0, device="cuda"), depths=torch.full((N,), 7.0, device="cuda"),
+                 conics=torch.full((N, 3), 7.0, device="cuda"), radii=torch.full((N,), 7, dtype=torch.int32,
+                                                                                 device="cuda"),
+                 tiles=torch.full((N,), 7, dtype=torch.int32, device="cuda"),
+                 opac=torch.full((N,), 7.0, device="cuda"), colors=torch.full((N, 3), 7.0, device="cuda"))
+        if fused:
+            _lib.gs_project_sh_eval(ca, p, d["sh_degree"], d["sh"], d["means"], d["quats"], d["log_scales"],
+                                    d["opacity_logits"], o["means2d"], o["depths"], o["conics"], o["radii"],
+                                    o["tiles"], o["opac"], o["colors"])
+        else:
+            _lib.gs_project(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], p, o["means2d"],
+                            o["depths"], o["conics"], o["radii"], o["tiles"], o["opac"])
+            _lib.gs_sh_eval(ca, d["sh_degree"], d["sh"], d["means"], o["radii"], o["colors"])
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in o.items()})
+    return outs
+
+
+@pytest.mark.parametrize("deg,aa", [(0, False), (1, False), (2, True), (3, False), (3, True)])
+def test_fused_projection_and_sh_match_the_oracle(deg, aa):
+    """One camera's projection and SH colours in one kernel (gs_project_sh_eval): the oracle's
+    splats and colours within the bars of the separate stages, and the separate calls' results
+    (integers equal, floats to rounding)."""
+    sc, cam = _mid_scene(n=7000, seed=20 + deg, deg=deg)
+    fused, two = _fused_project_sh(sc, cam, aa)
+    ref = oracle.project(sc, cam, antialiased=aa)
+    col, _ = oracle.sh_colors(sc, cam)
+    np.testing.assert_array_equal(fused["radii"], two["radii"])
+    np.testing.assert_array_equal(fused["tiles"], two["tiles"])
+    for k in ("means2d", "depths", "conics", "opac", "colors"):
+        np.testing.assert_allclose(fused[k], two[k], rtol=1e-6, atol=1e-7, err_msg=k)
+    r_gpu, r_ref = fused["radii"], ref["radii"]
+    both = (r_gpu > 0) & (r_ref > 0)
+    assert both.sum() > 0.5 * (r_ref > 0).sum()
+    assert (r_gpu != r_ref).sum() <= max(2, 1e-3 * len(r_ref))
+    np.testing.assert_allclose(fused["means2d"][both], ref["means2d"][both], atol=2e-3, rtol=0)
+    np.testing.assert_allclose(fused["depths"][both], ref["depths"][both], rtol=2e-6)
+    scale = np.abs(ref["conics"][both]).max(1, keepdims=True)
+    assert (np.abs(fused["conics"][both] - ref["conics"][both]) / scale).max() < 2e-4
+    np.testing.assert_allclose(fused["opac"][both], ref["opacities"][both], atol=2e-6, rtol=5e-5 if aa else 0)
+    vis = r_gpu > 0
+    np.testing.assert_allclose(fused["colors"][vis & (r_ref > 0)], col[vis & (r_ref > 0)], atol=3e-6, rtol=1e-5)
+    # invisible Gaussians: every output zero (the buffers started at 7)
+    for k in ("means2d", "depths", "conics", "opac", "colors", "tiles"):
+        assert (fused[k][~vis] == 0).all(), k
+
+
 # --------------------------------------------------------------------------- #
 # binning + sorting: bit-exact when fed the oracle's projection               #
 # --------------------------------------------------------------------------- #
