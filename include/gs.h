@@ -162,15 +162,14 @@ GS_API gs_status gs_sh_eval(const gs_camera *cams, int32_t C, int32_t N, int32_t
                      const float *means, const int32_t *radii, float *colors, void *stream);
 
 /* ------------------------------------------------------------------------ */
-/* gs_project_sh_eval -- gs_project followed by gs_sh_eval for ONE camera     */
-/* (C == 1), in one kernel: the same definitions (App. C.1), each Gaussian's  */
-/* mean read once, and the coefficients of Gaussians the camera culls not     */
-/* read.                                                                     */
+/* gs_project_sh_eval -- gs_project followed by gs_sh_eval in one kernel:    */
+/* the same definitions (App. C.1), each Gaussian's parameters, mean and SH   */
+/* coefficients read once for all C cameras, and the coefficients of         */
+/* Gaussians that every camera culls not read.                               */
 /* in : sh [N,K,3], means [N,3], quats [N,4] (16-byte aligned), log_scales    */
 /*      [N,3], opacity_logits [N]                                            */
-/* out: as gs_project (means2d 8-byte aligned), plus colors [N,3] as          */
-/*      gs_sh_eval; all OVERWRITTEN (zeros for invisible Gaussians).          */
-/*      GS_ERR_ARG when C != 1.                                               */
+/* out: as gs_project (means2d 8-byte aligned), plus colors [C,N,3] as        */
+/*      gs_sh_eval; all OVERWRITTEN (zeros for invisible pairs).              */
 /* ------------------------------------------------------------------------ */
 GS_API gs_status gs_project_sh_eval(const gs_camera *cams, int32_t C, int32_t N, const gs_params *params,
                                     int32_t sh_degree, const float *sh, const float *means, const float *quats,

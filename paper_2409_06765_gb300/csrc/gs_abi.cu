@@ -290,7 +290,6 @@ gs_status gs_project_sh_eval(const gs_camera *cams, int32_t C, int32_t N, const 
     GS_TRY(make_camset(cams, C, params->tile, cs));
     GS_TRY(check_cn(C, N));
     cs.N = N;
-    if (C != 1) return fail_arg("gs_project_sh_eval takes one camera (use gs_project + gs_sh_eval)");
     if (sh_degree < 0 || sh_degree > 3) return fail_arg("sh_degree must be in [0, 3]");
     if (N == 0) return GS_OK;
     GS_NONNULL(sh); GS_NONNULL(means); GS_NONNULL(quats); GS_NONNULL(log_scales); GS_NONNULL(opacity_logits);

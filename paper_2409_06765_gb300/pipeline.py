@@ -38,7 +38,7 @@ class Schedule:
     persistent: bool = False      # forward compositing as one persistent launch (needs tile_order)
     bwd_persistent: bool = False  # backward likewise
     fused_bwd: bool = True        # one camera: SH and projection backward as one kernel
-    fused_fwd: bool = True        # one camera: projection and SH colours as one kernel
+    fused_fwd: bool = True        # projection and SH colours as one kernel
 
     def params(self) -> _lib.GsParams:
         return _lib.make_params(tile=self.tile, batch_depth=self.batch_depth, pixels_per_thread=self.pixels_per_thread,
@@ -80,7 +80,7 @@ class FramePipeline:
     """Buffers and launches of one frame of C cameras over one DeviceScene."""
 
     def __init__(self, scene: DeviceScene, cams, schedule: Schedule = Schedule(), backward: bool = True,
-                 capacity: int | None = None, margin: float = 1.1):
+                 capacity: int | None = None, margin: float = 1.1, side_stream: torch.cuda.Stream | None = None):
         self.scene = scene
         self.cams = cams if isinstance(cams, _lib.CameraArray) else _lib.CameraArray(cams)
         self.schedule = schedule
@@ -113,7 +113,10 @@ class FramePipeline:
             self.d_quats, self.d_log_scales, self.d_logits = f(N, 4), f(N, 3), f(N)
             self.d_image = torch.zeros(self.P, 3, device=dev)
         self.g_pre = self.g_post = None
-        self.side = torch.cuda.Stream(dev)  # SH colours overlap the bin/sort
+        # SH colours overlap the bin/sort.  (torch hands out streams round-robin from a small
+        # pool, so callers running several pipelines at once pass a side stream of their own:
+        # a side stream shared with another frame's main stream would chain the two frames.)
+        self.side = side_stream if side_stream is not None else torch.cuda.Stream(dev)
         self.margin = margin
         self.K = None
         if capacity is None:
@@ -166,14 +169,14 @@ class FramePipeline:
     # -- stages ----------------------------------------------------------------------------
     @property
     def fused_fwd(self) -> bool:
-        return self.C == 1 and self.schedule.fused_fwd
+        return self.schedule.fused_fwd
 
     def _pre(self):
         # project, then SH colours (and the zeroing of the 2D gradient buffer) on a side stream
         # while the bin/sort runs on this one: the SH kernel streams coefficients from HBM while
         # the sort's many short, latency-bound kernels leave bandwidth idle; both only need the
-        # projection, and the compositing waits for both.  One camera: projection and colours
-        # as one kernel before the sort.
+        # projection, and the compositing waits for both.  With fused_fwd (the default):
+        # projection and colours as one kernel before the sort.
         s, L = self.scene, _lib
         main = torch.cuda.current_stream(self.device)
         if self.fused_fwd:
@@ -183,17 +186,20 @@ class FramePipeline:
         else:
             L.gs_project(self.cams, s.means, s.quats, s.log_scales, s.opacity_logits, self.params, self.means2d,
                          self.depths, self.conics, self.radii, self.tiles, self.opac)
-        self.side.wait_stream(main)
-        with torch.cuda.stream(self.side):
-            if not self.fused_fwd:
-                L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
-            if self.with_backward:
-                self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
+        side_work = not self.fused_fwd or self.with_backward
+        if side_work:
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                if not self.fused_fwd:
+                    L.gs_sh_eval(self.cams, s.sh_degree, s.sh, s.means, self.radii, self.colors)
+                if self.with_backward:
+                    self.g2d.zero_()  # the 2D gradients the compositing backward accumulates into
         L.gs_tile_bin_sort(self.cams, self.N, self.params, self.means2d, self.depths, self.radii, self.capacity, None,
                            self.values, self.ranges, self.K_out, self.workspace)
         if self.order is not None:
             L.gs_tile_order(self.cams, self.params, self.ranges, self.order)
-        main.wait_stream(self.side)
+        if side_work:
+            main.wait_stream(self.side)
 
     def _raster_fwd(self, count=None):
         _lib.gs_rasterize_fwd(self.cams, self.N, self.params, 3, self.ranges, self.values, self.radii, self.means2d,

@@ -115,17 +115,30 @@ class RasterState:
             self.ws_key = key
 
 
-def project(cams, means, quats, log_scales, opacity_logits, params):
-    C, N, dev = cams.C, means.shape[0], means.device
+def _splat_buffers(C, N, dev):
     CN = C * N
     f = torch.empty(7 * CN, device=dev)  # means2d | depths | conics | opacities, one allocation
     i = torch.empty(2 * CN, dtype=torch.int32, device=dev)  # radii | tiles touched
-    out = dict(means2d=f[:2 * CN].view(C, N, 2), depths=f[2 * CN:3 * CN].view(C, N),
-               conics=f[3 * CN:6 * CN].view(C, N, 3), opacities=f[6 * CN:].view(C, N),
-               radii=i[:CN].view(C, N), tiles_touched=i[CN:].view(C, N))
+    return dict(means2d=f[:2 * CN].view(C, N, 2), depths=f[2 * CN:3 * CN].view(C, N),
+                conics=f[3 * CN:6 * CN].view(C, N, 3), opacities=f[6 * CN:].view(C, N),
+                radii=i[:CN].view(C, N), tiles_touched=i[CN:].view(C, N))
+
+
+def project(cams, means, quats, log_scales, opacity_logits, params):
+    out = _splat_buffers(cams.C, means.shape[0], means.device)
     _lib.gs_project(cams, means, quats, log_scales, opacity_logits, params, out["means2d"], out["depths"],
                     out["conics"], out["radii"], out["tiles_touched"], out["opacities"])
     return out
+
+
+def project_sh(cams, means, quats, log_scales, opacity_logits, params, sh_degree, sh):
+    """The splats and their SH colours [C,N,3] from one kernel."""
+    out = _splat_buffers(cams.C, means.shape[0], means.device)
+    colors = torch.empty(cams.C, means.shape[0], 3, device=means.device)
+    _lib.gs_project_sh_eval(cams, params, sh_degree, sh, means, quats, log_scales, opacity_logits, out["means2d"],
+                            out["depths"], out["conics"], out["radii"], out["tiles_touched"], out["opacities"],
+                            colors)
+    return out, colors
 
 
 def sh_eval(cams, sh_degree, sh, means, radii, depths=None, out=None):
@@ -215,21 +228,25 @@ def forward_pass(cams, means, quats, log_scales, opacity_logits, sh=None, sh_deg
     settings = settings or RasterSettings()
     params = settings.params()
     N = means.shape[0]
-    sp = project(cams, means, quats, log_scales, opacity_logits, params)
     side = None
-    if features is None and cams.C * N >= SIDE_STREAM_MIN_PAIRS:
-        # SH colours on a side stream while the bin/sort runs on this one (both need only the
-        # projection; the compositing waits for both).  The buffer is taken on this stream.
+    if features is not None:
+        sp, colors = project(cams, means, quats, log_scales, opacity_logits, params), features
+    elif not depth:  # projection and colours in one kernel
+        sp, colors = project_sh(cams, means, quats, log_scales, opacity_logits, params, sh_degree, sh)
+    elif cams.C * N >= SIDE_STREAM_MIN_PAIRS:
+        # depth rendering: SH colours and depths on a side stream while the bin/sort runs on
+        # this one (both need only the projection; the compositing waits for both).  The
+        # buffer is taken on this stream.
+        sp = project(cams, means, quats, log_scales, opacity_logits, params)
         colors = torch.empty(cams.C, N, 4 if depth else 3, device=means.device)
         main = torch.cuda.current_stream(means.device)
         side = _side_stream(main)
         side.wait_stream(main)
         with torch.cuda.stream(side):
             sh_eval(cams, sh_degree, sh, means, sp["radii"], sp["depths"] if depth else None, out=colors)
-    elif features is None:  # small frames: the stream switch costs more than the overlap gains
+    else:  # small frames: the stream switch costs more than the overlap gains
+        sp = project(cams, means, quats, log_scales, opacity_logits, params)
         colors = sh_eval(cams, sh_degree, sh, means, sp["radii"], sp["depths"] if depth else None)
-    else:
-        colors = features
     ch = colors.shape[-1]
     state = state or RasterState()
     # the sort and the compositing are queued back to back; K is checked once the whole

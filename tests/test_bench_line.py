@@ -24,6 +24,7 @@ def _full_record():
                  "p99_ms": 18.73840368200188, "mean_ms": 4.163428936550632, "max_ms": 27.073458233054293,
                  "frames_per_s": 197.91587791987695, "mean_views_per_batch": 1.0413932357395255,
                  "saturated_frames_per_s": 379.0436983697336, "saturated_mean_views_per_batch": 3.2,
+                 "saturated_640x480_frames_per_s": 1612.345678, "saturated_640x480_mean_views_per_batch": 5.9123,
                  "streams": 4, "batches": 2407, "overflow_retries": 2}
     return {
         "metric": bench.METRIC, "value": 2.5e11, "unit": bench.UNIT, "n_gpus": 1, "steps": 20, "warmup": 5,

@@ -61,19 +61,17 @@ def test_sh_matches_oracle(deg):
     assert (out["colors"][0].cpu().numpy()[~vis] == 0).all()
 
 
-def _fused_project_sh(sc, cam, aa=False):
+def _fused_project_sh(sc, cams, aa=False):
     """gs_project_sh_eval (one kernel) beside gs_project + gs_sh_eval (two), same inputs."""
     d = dev_scene(sc)
-    ca = _lib.CameraArray([cam])
+    ca = _lib.CameraArray(cams)
     p = _lib.make_params(tile=16, antialiased=aa)
-    N = d["means"].shape[0]
+    C, N = len(cams), d["means"].shape[0]
     outs = []
     for fused in (True, False):
-        o = dict(means2d=torch.full((N, 2), 7.0, device="cuda"), depths=torch.full((N,), 7.0, device="cuda"),
-                 conics=torch.full((N, 3), 7.0, device="cuda"), radii=torch.full((N,), 7, dtype=torch.int32,
-                                                                                 device="cuda"),
-                 tiles=torch.full((N,), 7, dtype=torch.int32, device="cuda"),
-                 opac=torch.full((N,), 7.0, device="cuda"), colors=torch.full((N, 3), 7.0, device="cuda"))
+        full = lambda *shape, dt=torch.float32: torch.full(shape, 7, dtype=dt, device="cuda")
+        o = dict(means2d=full(C, N, 2), depths=full(C, N), conics=full(C, N, 3), radii=full(C, N, dt=torch.int32),
+                 tiles=full(C, N, dt=torch.int32), opac=full(C, N), colors=full(C, N, 3))
         if fused:
             _lib.gs_project_sh_eval(ca, p, d["sh_degree"], d["sh"], d["means"], d["quats"], d["log_scales"],
                                     d["opacity_logits"], o["means2d"], o["depths"], o["conics"], o["radii"],
@@ -87,33 +85,37 @@ def _fused_project_sh(sc, cam, aa=False):
     return outs
 
 
-@pytest.mark.parametrize("deg,aa", [(0, False), (1, False), (2, True), (3, False), (3, True)])
-def test_fused_projection_and_sh_match_the_oracle(deg, aa):
-    """One camera's projection and SH colours in one kernel (gs_project_sh_eval): the oracle's
+@pytest.mark.parametrize("deg,aa,ncam", [(0, False, 1), (1, False, 1), (2, True, 1), (3, False, 1), (3, True, 1),
+                                         (3, False, 3), (1, True, 2)])
+def test_fused_projection_and_sh_match_the_oracle(deg, aa, ncam):
+    """Projection and SH colours of C cameras in one kernel (gs_project_sh_eval): the oracle's
     splats and colours within the bars of the separate stages, and the separate calls' results
-    (integers equal, floats to rounding)."""
-    sc, cam = _mid_scene(n=7000, seed=20 + deg, deg=deg)
-    fused, two = _fused_project_sh(sc, cam, aa)
-    ref = oracle.project(sc, cam, antialiased=aa)
-    col, _ = oracle.sh_colors(sc, cam)
+    (integers equal, floats to rounding); cameras of different sizes see different subsets."""
+    sc, _ = _mid_scene(n=7000, seed=20 + deg, deg=deg)
+    cams = synth.sphere_cameras(20 + deg, [(203, 157), (96, 140), (150, 64)][:ncam])
+    fused, two = _fused_project_sh(sc, cams, aa)
     np.testing.assert_array_equal(fused["radii"], two["radii"])
     np.testing.assert_array_equal(fused["tiles"], two["tiles"])
     for k in ("means2d", "depths", "conics", "opac", "colors"):
         np.testing.assert_allclose(fused[k], two[k], rtol=1e-6, atol=1e-7, err_msg=k)
-    r_gpu, r_ref = fused["radii"], ref["radii"]
-    both = (r_gpu > 0) & (r_ref > 0)
-    assert both.sum() > 0.5 * (r_ref > 0).sum()
-    assert (r_gpu != r_ref).sum() <= max(2, 1e-3 * len(r_ref))
-    np.testing.assert_allclose(fused["means2d"][both], ref["means2d"][both], atol=2e-3, rtol=0)
-    np.testing.assert_allclose(fused["depths"][both], ref["depths"][both], rtol=2e-6)
-    scale = np.abs(ref["conics"][both]).max(1, keepdims=True)
-    assert (np.abs(fused["conics"][both] - ref["conics"][both]) / scale).max() < 2e-4
-    np.testing.assert_allclose(fused["opac"][both], ref["opacities"][both], atol=2e-6, rtol=5e-5 if aa else 0)
-    vis = r_gpu > 0
-    np.testing.assert_allclose(fused["colors"][vis & (r_ref > 0)], col[vis & (r_ref > 0)], atol=3e-6, rtol=1e-5)
-    # invisible Gaussians: every output zero (the buffers started at 7)
-    for k in ("means2d", "depths", "conics", "opac", "colors", "tiles"):
-        assert (fused[k][~vis] == 0).all(), k
+    for c, cam in enumerate(cams):
+        ref = oracle.project(sc, cam, antialiased=aa)
+        col, _ = oracle.sh_colors(sc, cam)
+        r_gpu, r_ref = fused["radii"][c], ref["radii"]
+        both = (r_gpu > 0) & (r_ref > 0)
+        assert both.sum() > 0.5 * (r_ref > 0).sum()
+        assert (r_gpu != r_ref).sum() <= max(2, 1e-3 * len(r_ref))
+        np.testing.assert_allclose(fused["means2d"][c][both], ref["means2d"][both], atol=2e-3, rtol=0)
+        np.testing.assert_allclose(fused["depths"][c][both], ref["depths"][both], rtol=2e-6)
+        scale = np.abs(ref["conics"][both]).max(1, keepdims=True)
+        assert (np.abs(fused["conics"][c][both] - ref["conics"][both]) / scale).max() < 2e-4
+        np.testing.assert_allclose(fused["opac"][c][both], ref["opacities"][both], atol=2e-6,
+                                   rtol=5e-5 if aa else 0)
+        np.testing.assert_allclose(fused["colors"][c][both], col[both], atol=3e-6, rtol=1e-5)
+        # invisible pairs: every output zero (the buffers started at 7)
+        vis = r_gpu > 0
+        for k in ("means2d", "depths", "conics", "opac", "colors", "tiles"):
+            assert (fused[k][c][~vis] == 0).all(), k
 
 
 # --------------------------------------------------------------------------- #
@@ -628,20 +630,22 @@ def test_fused_sh_projection_backward_matches_the_two_calls(deg, aa):
                                b["d_sh"], b["d_means"], b["d_quats"], b["d_ls"], b["d_lg"])
 
 
-def test_autograd_forward_with_colours_beside_the_sort_matches_the_serial_path(monkeypatch):
-    """Frames of 256k+ pairs evaluate SH on a side stream while the sort runs; the image and
-    the gradients must equal the single-stream path's."""
+def test_depth_frames_with_colours_beside_the_sort_match_the_serial_path(monkeypatch):
+    """Depth-rendering frames of 256k+ pairs evaluate SH colours and depths on a side stream
+    while the sort runs (colour-only frames take the fused projection + SH kernel); the image
+    must equal the single-stream path's."""
     sc = synth.clustered_scene(300_000, 17, sh_degree=3, log_scale_mu=-4.0)
-    cam = synth.sphere_cameras(17, [(160, 120)])[0]
-    assert sc.n >= raster.SIDE_STREAM_MIN_PAIRS
-    P = cam.width * cam.height
-    g = np.random.default_rng(18).normal(size=(P, 3)).astype(np.float32)
-    a, img_a, _ = gpu_grads(sc, [cam], g)
+    cams = synth.sphere_cameras(17, [(160, 120), (96, 128)])
+    assert 2 * sc.n >= raster.SIDE_STREAM_MIN_PAIRS
+    d = dev_scene(sc)
+    ca = _lib.CameraArray(cams)
+    run = lambda: raster.forward_pass(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], sh=d["sh"],
+                                      sh_degree=d["sh_degree"], depth=True)["image"].cpu().numpy()
+    img_a = run()
     monkeypatch.setattr(raster, "SIDE_STREAM_MIN_PAIRS", 1 << 40)
-    b, img_b, _ = gpu_grads(sc, [cam], g)
+    img_b = run()
+    assert img_a.shape[-1] == 4
     np.testing.assert_array_equal(img_a, img_b)
-    for k in a:  # gradients: the atomic sums of the backward may add in another order
-        assert rel_l2(a[k], b[k]) <= 1e-5, k
 
 
 def test_bin_sort_with_unaligned_depth_and_radius_arrays():
