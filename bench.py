@@ -768,28 +768,30 @@ def run_serving(seconds, rate, log, warm_s=2.0, schedule=None):
     # buffers and every kernel shape), so that no configuration pays for coming first
     for _, kw in configs:
         warm = serve.Server(store, schedule=sched, **kw)
-        warm.serve(sat, realtime=False)
-        warm.serve(sat_small, realtime=False)
+        warm.serve(sat, realtime=False, keep_images=False)
+        warm.serve(sat_small, realtime=False, keep_images=False)
         del warm
         gc.collect()
     warm = serve.Server(store, schedule=sched, max_views=8, streams=4)
-    warm.serve(serve.poisson_trace(rate, 1.0, len(sizes_m), seed=57), realtime=True)
+    warm.serve(serve.poisson_trace(rate, 1.0, len(sizes_m), seed=57), realtime=True, keep_images=False)
     del warm
     gc.collect()
     for name, kw in configs:
         srv = serve.Server(store, schedule=sched, **kw)
-        srv.serve(sat, realtime=False)  # warm: this server's streams, pinned buffers and pools at saturation
-        res = srv.serve(trace, realtime=True)
+        srv.serve(sat, realtime=False, keep_images=False)  # warm: streams, pinned buffers, pools
+        # (images reach page-locked host memory; results keep no copy: a minute of 1080p images
+        # would fill host memory)
+        res = srv.serve(trace, realtime=True, keep_images=False)
         summ = serve.latency_summary(res, skip_before_s=warm_s)
         t1 = time.perf_counter()
-        sat_res = srv.serve(sat, realtime=False)
+        sat_res = srv.serve(sat, realtime=False, keep_images=False)
         sat_s = time.perf_counter() - t1
         ssum = serve.latency_summary(sat_res)
         summ["saturated_frames_per_s"] = len(sat_res) / sat_s
         summ["saturated_mean_views_per_batch"] = ssum["mean_views_per_batch"]
         summ["saturated_mean_scenes_per_batch"] = ssum["mean_scenes_per_batch"]
         t1 = time.perf_counter()
-        small_res = srv.serve(sat_small, realtime=False)
+        small_res = srv.serve(sat_small, realtime=False, keep_images=False)
         summ["saturated_640x480_frames_per_s"] = len(small_res) / (time.perf_counter() - t1)
         summ["saturated_640x480_mean_views_per_batch"] = serve.latency_summary(small_res)["mean_views_per_batch"]
         summ["streams"], summ["max_views"] = kw["streams"], kw["max_views"]

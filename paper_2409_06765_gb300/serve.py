@@ -56,7 +56,7 @@ class Request:
 class Result:
     rid: int
     scene: int
-    image: np.ndarray  # [H, W, 3] float32 (host)
+    image: np.ndarray | None  # [H, W, 3] float32 (host); None when the server keeps no images
     arrival: float
     launched: float
     done: float
@@ -277,9 +277,14 @@ class Server:
         self._pinned[stream.cuda_stream] = (img, k)
         return img, k
 
-    def serve(self, requests, realtime=True, poll_sleep=50e-6):
+    def serve(self, requests, realtime=True, poll_sleep=50e-6, keep_images=True, on_image=None):
         """Serve a trace; returns the results in completion order.  With realtime=False every
-        request counts as arrived at once (a saturation run: the queues start full)."""
+        request counts as arrived at once (a saturation run: the queues start full).
+
+        Every image reaches page-locked host memory.  With ``keep_images`` each result holds a
+        copy of its image; without, ``on_image(result, view)`` (when given) sees each image as a
+        view into the stream's host buffer, valid only during the call, and results hold None
+        (a long trace of 1080p images would otherwise fill host memory)."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queues: dict[int, list] = {sid: [] for sid in self.store.scenes}
         free_streams = list(self.streams)
@@ -320,9 +325,12 @@ class Server:
                     for r, off in zip(g.reqs, g.offsets):
                         P = r.camera.width * r.camera.height
                         o = g.host_off + 3 * off
-                        results.append(Result(r.rid, r.scene, img[o:o + 3 * P].reshape(r.camera.height,
-                                                                                       r.camera.width, 3).copy(),
-                                              r.arrival, b.launched, done, b.views, b.serial))
+                        view = img[o:o + 3 * P].reshape(r.camera.height, r.camera.width, 3)
+                        res = Result(r.rid, r.scene, view.copy() if keep_images else None, r.arrival, b.launched,
+                                     done, b.views, b.serial)
+                        if on_image is not None:
+                            on_image(res, view)
+                        results.append(res)
                 del b
                 progressed = True
             # launch: overflowed groups first (each alone, admitted by memory), then new batches

@@ -171,3 +171,18 @@ def test_deferred_count_check_redoes_a_frame_that_outgrew_the_buffers():
     img = raster.rasterization(*leaves, cameras=[cam], state=state, defer_sync=True)[0][0].cpu().numpy()
     assert state.check() is True
     np.testing.assert_array_equal(img, ref)
+
+
+def test_images_handed_to_a_callback_equal_the_kept_copies():
+    """Without keep_images the results hold no image; on_image sees each one as a view into the
+    stream's page-locked buffer while it is valid, equal to the copy a keeping server returns."""
+    store, _ = _store()
+    trace = _trace(n=10, seed=49)
+    kept = {r.rid: r.image for r in serve.Server(store, max_views=8, streams=2).serve(trace, realtime=False)}
+    seen = {}
+    res = serve.Server(store, max_views=8, streams=2).serve(
+        trace, realtime=False, keep_images=False, on_image=lambda r, view: seen.__setitem__(r.rid, view.copy()))
+    assert len(res) == len(trace) and all(r.image is None for r in res)
+    assert set(seen) == set(kept)
+    for rid, img in kept.items():
+        np.testing.assert_array_equal(seen[rid], img)
