@@ -5,9 +5,8 @@ Several scenes' Gaussians stay resident on the device.  Forward-only render requ
 
 * admits an arrived request into its scene's queue,
 * forms a batch from whatever has arrived: the scene whose oldest request has waited
-  longest first (up to ``max_views`` cameras of any mix of sizes; optionally at most
-  ``max_group_tiles`` tiles per scene group, so that its sort stays one counting pass up to
-  2048 tiles), then, with ``max_groups`` > 1,
+  longest first (up to ``max_views`` cameras of any mix of sizes, and by default at most 2048
+  tiles per scene group so that its sort stays one counting pass), then, with ``max_groups`` > 1,
   the next-oldest scenes while the batch has room.  Each scene group of the batch is one
   multi-camera call (C > 1, per-camera tile lists, one launch per stage); the groups of a
   batch run back to back on one stream and retire together,
@@ -188,7 +187,7 @@ class Server:
 
     def __init__(self, store: ResidentScenes, schedule: Schedule = Schedule(), max_views: int = 8, streams: int = 4,
                  budget_bytes: int | None = None, k_margin: float = 1.5, max_retries: int = 3,
-                 max_group_tiles: int | None = None, max_groups: int = 1):
+                 max_group_tiles: int | None = 2048, max_groups: int = 1):
         self.store = store
         self.schedule = schedule
         self.max_views = max(1, min(int(max_views), _lib.GS_MAX_CAMERAS))
@@ -202,12 +201,11 @@ class Server:
         self.k_margin = k_margin
         self.max_retries = int(max_retries)
         # a scene group's views share one sort: up to 2048 tiles it is the single counting pass
-        # over whole tile ids, beyond that LSD passes over materialised lists.  Capping a group
-        # at 2048 tiles (max_group_tiles=2048; a single view above it still renders, alone)
-        # keeps the single pass; by default groups take up to max_views views, because the
-        # views of a group also share the reads of the scene's parameters and coefficients,
-        # which at saturation outweighs the extra sort passes (mixed sizes: 705 against 656
-        # frames/s with the cap; 640x480 only: 1621 against 1644-1693)
+        # over whole tile ids, beyond that LSD passes over materialised lists, which cost more
+        # than the group saves by sharing the scene's parameter and coefficient reads; so by
+        # default a group stays within 2048 tiles (a single view above it still renders, alone).
+        # At saturation, 4 streams, mixed sizes: 1472 frames/s capped, 1386 uncapped, 1392-1406
+        # one view per batch; 640x480 only: 1880, 1858 and 1518-1528.  None lifts the cap.
         self.max_group_tiles = max_group_tiles
         # scene groups per batch: groups of different scenes share no GPU work (each is its own
         # call), so by default a batch is one scene's views; more groups only pack the launches
