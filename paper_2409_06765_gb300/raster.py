@@ -310,6 +310,7 @@ class RasterizeGaussians(torch.autograd.Function):
                               out["conics"], out["opacities"], out["colors"], out["values"], out["ranges"],
                               out["final_T"], out["last_contrib"], out["image"] if depth == 2 else None)
         ctx.mark_non_differentiable(out["radii"])
+        ctx.set_materialize_grads(False)  # outputs without a gradient (alpha, depth) arrive as None
         ctx.viewmats_like = viewmats  # the pose leaf, if any (its values are in cams)
         alpha = 1.0 - out["final_T"]
         return out["image"], alpha, out["radii"], edepth
