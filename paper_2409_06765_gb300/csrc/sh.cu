@@ -564,14 +564,59 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
     store_rows<F, kShBwdThreads>(d_sh + (size_t)n0 * F, cnt, s_coef);
 }
 
-// Projection and SH colours of the C cameras of a call in one kernel (App. C.1): each thread
-// projects its Gaussian into every camera and writes the splats, the CTA then streams into
-// shared memory the coefficient rows of the Gaussians some camera sees (as sh_fwd_kernel
-// does), and each thread evaluates its colour per camera.  Parameters, mean and coefficients
-// are read once for all cameras, and the visibility decided by the projection picks the rows
-// without reading the radii back.
 constexpr int kProjShThreads = 64;  // Gaussians (threads) of a CTA of the fused forward (64: 0.143 ms, 256: 0.150 ms at 3M)
 
+// Could camera `cam` see a Gaussian with this mean and largest scale?  False only when the
+// exact projection surely culls it: behind the near plane (the same test), or its pixel box,
+// widened from an upper bound of the splat's radius, misses the image.  The bound uses
+// lambda_max(T Sigma T^T) <= |T|_F^2 s_max^2 (T = J R_cw), plus the low-pass and margins far above
+// float rounding.  Only the choice of which coefficient rows to copy early depends on it.
+__device__ __forceinline__ bool maybe_visible(const float mean[3], float smax, const CamDev &cam,
+                                              const RasterConsts &rc) {
+    float t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        t[i] = cam.R[3 * i] * mean[0] + cam.R[3 * i + 1] * mean[1] + cam.R[3 * i + 2] * mean[2] + cam.t[i];
+    if (!(t[2] >= rc.near_plane)) return false;
+    const float iz = 1.f / t[2];
+    const float mx = cam.fx * t[0] * iz + cam.cx, my = cam.fy * t[1] * iz + cam.cy;
+    const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
+    float tf = 0.f;  // |T|_F^2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float a = j00 * cam.R[k] + j02 * cam.R[6 + k], b = j11 * cam.R[3 + k] + j12 * cam.R[6 + k];
+        tf += a * a + b * b;
+    }
+    const float r = 3.f * sqrtf(tf * smax * smax * 1.01f + rc.eps2d) * 1.01f + 2.f;
+    if (!(r < 1.0e8f)) return true;  // (non-finite or huge: copy the row)
+    return mx + r >= -1.f && mx - r <= (float)cam.W + 1.f && my + r >= -1.f && my - r <= (float)cam.H + 1.f;
+}
+
+// Copies the float4 rows flagged in `ok` with asynchronous 16-byte copies (global 16-byte
+// aligned source, F a multiple of 4); the caller waits with cp.async.wait_all and a barrier.
+template <int F, int NT>
+__device__ __forceinline__ void stage_rows_async(const float *__restrict__ src, int cnt, float *s,
+                                                 const unsigned char *ok) {
+    constexpr int F4 = F / 4, S4 = row_stride<F>() / 4;
+    const float4 *src4 = reinterpret_cast<const float4 *>(src);
+    float4 *s4 = reinterpret_cast<float4 *>(s);
+    for (int v = threadIdx.x; v < cnt * F4; v += NT) {
+        const int row = v / F4;
+        if (!ok[row]) continue;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(s4 + row * S4 + (v - row * F4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src4 + v) : "memory");
+    }
+}
+
+// Projection and SH colours of the C cameras of a call in one kernel (App. C.1): each thread
+// projects its Gaussian into every camera and writes the splats, and evaluates its colour per
+// camera from its coefficient row, staged in shared memory (as sh_fwd_kernel does) for the
+// Gaussians some camera may see.  With float4 rows (degrees 1 and 3) the row copies start
+// before the projection, for the Gaussians a cheap conservative test keeps, so they arrive
+// while the projection is computed; a row the test dropped but the projection needs (none, by
+// construction) is read from global memory.  Otherwise the rows of the Gaussians the projection
+// keeps are staged after it.  Parameters, mean and coefficients are read once for all cameras.
 template <int DEG>
 __global__ void __launch_bounds__(kProjShThreads) project_sh_fwd_kernel(
     int N, const float *__restrict__ sh, const float *__restrict__ means, const float4 *__restrict__ quats,
@@ -586,14 +631,28 @@ __global__ void __launch_bounds__(kProjShThreads) project_sh_fwd_kernel(
     const int cnt = min(kProjShThreads, N - n0);
     const int n = n0 + threadIdx.x;
     const bool valid = n < N;
+    const float *src = sh + (size_t)n0 * F;
+    const bool early = (F % 4 == 0) && (reinterpret_cast<uintptr_t>(src) & 15) == 0;  // (uniform)
     float mean[3] = {0.f, 0.f, 0.f};
-    unsigned seen = 0u;  // bit c: camera c sees the Gaussian (C <= 32)
+    Gauss3 g;
     if (valid) {
         mean[0] = means[3 * n];
         mean[1] = means[3 * n + 1];
         mean[2] = means[3 * n + 2];
-        Gauss3 g;
         load_gauss(n, log_scales, quats, logits, g);
+    }
+    if (early) {
+        bool maybe = false;
+        if (valid) {
+            const float smax = fmaxf(g.s[0], fmaxf(g.s[1], g.s[2]));
+            for (int c = 0; c < cs.C && !maybe; ++c) maybe = maybe_visible(mean, smax, cs.cam[c], rc);
+        }
+        s_ok[threadIdx.x] = maybe;
+        __syncthreads();
+        if constexpr (F % 4 == 0) stage_rows_async<F, kProjShThreads>(src, cnt, s_coef, s_ok);
+    }
+    unsigned seen = 0u;  // bit c: camera c sees the Gaussian (C <= 32)
+    if (valid) {
         const int tile = cs.tile;
         for (int c = 0; c < cs.C; ++c) {
             const CamDev &cam = cs.cam[c];
@@ -625,13 +684,17 @@ __global__ void __launch_bounds__(kProjShThreads) project_sh_fwd_kernel(
             }
         }
     }
-    s_ok[threadIdx.x] = seen != 0u;
-    __syncthreads();
-    const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, kProjShThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    if (early) {
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else {
+        s_ok[threadIdx.x] = seen != 0u;
+        __syncthreads();
+        stage_rows<F, kProjShThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    }
     __syncthreads();
     if (!valid) return;
-    const float *cf = s_coef + threadIdx.x * STRIDE;
+    // the staged row, or (a row the conservative test dropped) the row in global memory
+    const float *cf = s_ok[threadIdx.x] ? s_coef + threadIdx.x * STRIDE : sh + (size_t)n * F;
     for (int c = 0; c < cs.C; ++c) {
         float *out = colors + 3 * ((size_t)c * N + n);
         if (!(seen & (1u << c))) {
@@ -650,7 +713,12 @@ __global__ void __launch_bounds__(kProjShThreads) project_sh_fwd_kernel(
         float Y[K];
         sh_eval_basis<DEG>(kc, vx * il, vy * il, vz * il, Y);
         float acc[3] = {0.5f, 0.5f, 0.5f};  // element e = 3 k + channel, k ascending per channel
-        row_for_each<F>(cf, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
+        if (s_ok[threadIdx.x]) {
+            row_for_each<F>(cf, [&](int e, float v) { acc[e % 3] = fmaf(Y[e / 3], v, acc[e % 3]); });
+        } else {
+#pragma unroll
+            for (int e = 0; e < F; ++e) acc[e % 3] = fmaf(Y[e / 3], cf[e], acc[e % 3]);
+        }
         out[0] = fmaxf(acc[0], 0.f);
         out[1] = fmaxf(acc[1], 0.f);
         out[2] = fmaxf(acc[2], 0.f);
