@@ -268,6 +268,22 @@ __device__ __forceinline__ void store_rows(float *__restrict__ dst, int cnt, con
     for (int e = threadIdx.x; e < total; e += NT) dst[e] = s[(e / F) * STRIDE + e % F];
 }
 
+// Copies the float4 rows flagged in `ok` with asynchronous 16-byte copies (global 16-byte
+// aligned source, F a multiple of 4); the caller waits with cp.async.wait_all and a barrier.
+template <int F, int NT>
+__device__ __forceinline__ void stage_rows_async(const float *__restrict__ src, int cnt, float *s,
+                                                 const unsigned char *ok) {
+    constexpr int F4 = F / 4, S4 = row_stride<F>() / 4;
+    const float4 *src4 = reinterpret_cast<const float4 *>(src);
+    float4 *s4 = reinterpret_cast<float4 *>(s);
+    for (int v = threadIdx.x; v < cnt * F4; v += NT) {
+        const int row = v / F4;
+        if (!ok[row]) continue;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(s4 + row * S4 + (v - row * F4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src4 + v) : "memory");
+    }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(256) sh_fwd_kernel(int N, const float *__restrict__ sh,
                                                      const float *__restrict__ means, const int *__restrict__ radii,
@@ -451,10 +467,10 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
 
 // SH backward and projection backward of one camera in one kernel: the coefficient rows
 // stream through shared memory as in sh_bwd_kernel (gradient rows written in place), and
-// each thread then runs the projection chain of its Gaussian (App. D.2-D.4) with the
-// colour-path mean gradient still in registers, so d_means is written once and the
-// Gaussian's parameters, radius and mean are read once for both.  Every per-Gaussian input
-// of a visible Gaussian is requested before the coefficient rows.
+// each thread runs the projection chain of its Gaussian (App. D.2-D.4) -- while its row is
+// still arriving, when the rows are copied asynchronously (degrees 1 and 3) -- so d_means is
+// written once and the Gaussian's parameters, radius and mean are read once for both.  Every
+// per-Gaussian input of a visible Gaussian is requested before the coefficient rows.
 template <int DEG>
 __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) sh_project_bwd_kernel(
     int N, const float *__restrict__ sh, const float *__restrict__ means, const float4 *__restrict__ quats,
@@ -501,10 +517,30 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
     s_ok[threadIdx.x] = vis;
     __syncthreads();
     const float *src = sh + (size_t)n0 * F;
-    stage_rows<F, kShBwdThreads>(src, cnt, s_coef, (reinterpret_cast<uintptr_t>(src) & 15) == 0, s_ok);
+    const bool aligned16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    const bool early = (F % 4 == 0) && aligned16;  // (uniform)
+    if (early) {
+        if constexpr (F % 4 == 0) stage_rows_async<F, kShBwdThreads>(src, cnt, s_coef, s_ok);
+    } else {
+        stage_rows<F, kShBwdThreads>(src, cnt, s_coef, aligned16, s_ok);
+    }
+    // the projection chain first: it needs no coefficient row, so with asynchronous copies it
+    // runs while the rows arrive
+    const CamDev &cam = cs.cam[0];
+    float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dl = 0.f;
+    float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vis) {
+        Gauss3 gs3;
+        gauss_from(q, ls0, ls1, ls2, lg, gs3);
+        Splat2 sp;
+        float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, d_o = 0.f, pose[12];
+        if (splat_of(gs3, mean, cam, rc, sp))
+            splat_bwd<false>(gs3, mean, cam, rc, sp, gm, ga, gb, gc, gop, 0.f, dmu, dSig, d_o, pose);
+        gauss_bwd(gs3, dSig, d_o, dls, dq, dl);
+    }
+    if (early) asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     float *row = s_coef + threadIdx.x * STRIDE;  // coefficients, then (in place) their gradient
-    const CamDev &cam = cs.cam[0];
     float dm[3] = {0.f, 0.f, 0.f};
     if (vis) {
         const float *R = cam.R, *t = cam.t;
@@ -537,23 +573,9 @@ __global__ void __launch_bounds__(kShBwdThreads, GS_SH_PROJECT_BWD_MIN_BLOCKS) s
         row_write<F, false>(row, [](int) { return 0.f; });
     }
     if (valid) {
-        float dls[3] = {0.f, 0.f, 0.f}, dl = 0.f;
-        float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (vis) {
-            Gauss3 gs3;
-            gauss_from(q, ls0, ls1, ls2, lg, gs3);
-            Splat2 sp;
-            float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, d_o = 0.f, pose[12];
-            if (splat_of(gs3, mean, cam, rc, sp))
-                splat_bwd<false>(gs3, mean, cam, rc, sp, gm, ga, gb, gc, gop, 0.f, dmu, dSig, d_o, pose);
-            dm[0] += dmu[0];
-            dm[1] += dmu[1];
-            dm[2] += dmu[2];
-            gauss_bwd(gs3, dSig, d_o, dls, dq, dl);
-        }
-        d_means[3 * n] = dm[0];
-        d_means[3 * n + 1] = dm[1];
-        d_means[3 * n + 2] = dm[2];
+        d_means[3 * n] = dm[0] + dmu[0];
+        d_means[3 * n + 1] = dm[1] + dmu[1];
+        d_means[3 * n + 2] = dm[2] + dmu[2];
         d_quats[n] = dq;
         d_log_scales[3 * n] = dls[0];
         d_log_scales[3 * n + 1] = dls[1];
@@ -591,22 +613,6 @@ __device__ __forceinline__ bool maybe_visible(const float mean[3], float smax, c
     const float r = 3.f * sqrtf(tf * smax * smax * 1.01f + rc.eps2d) * 1.01f + 2.f;
     if (!(r < 1.0e8f)) return true;  // (non-finite or huge: copy the row)
     return mx + r >= -1.f && mx - r <= (float)cam.W + 1.f && my + r >= -1.f && my - r <= (float)cam.H + 1.f;
-}
-
-// Copies the float4 rows flagged in `ok` with asynchronous 16-byte copies (global 16-byte
-// aligned source, F a multiple of 4); the caller waits with cp.async.wait_all and a barrier.
-template <int F, int NT>
-__device__ __forceinline__ void stage_rows_async(const float *__restrict__ src, int cnt, float *s,
-                                                 const unsigned char *ok) {
-    constexpr int F4 = F / 4, S4 = row_stride<F>() / 4;
-    const float4 *src4 = reinterpret_cast<const float4 *>(src);
-    float4 *s4 = reinterpret_cast<float4 *>(s);
-    for (int v = threadIdx.x; v < cnt * F4; v += NT) {
-        const int row = v / F4;
-        if (!ok[row]) continue;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(s4 + row * S4 + (v - row * F4));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src4 + v) : "memory");
-    }
 }
 
 // Projection and SH colours of the C cameras of a call in one kernel (App. C.1): each thread
