@@ -1,6 +1,6 @@
-"""Special cases against the oracle: the paper's Fig. 1 example, and calls at the C ABI's limits
+"""Special cases against the oracle: the paper's Fig. 1 example, calls at the C ABI's limits
 (the maximum number of cameras in one call, 32 of uneven and ragged sizes, and the maximum number
-of feature channels, 64)."""
+of feature channels, 64), and degenerate view sizes (one pixel, one row, one column)."""
 import numpy as np
 import pytest
 import torch
@@ -99,3 +99,40 @@ def test_maximum_feature_channels_forward_and_backward():
     g3 = oracle.project_bwd(sc, cam, g2["d_means2d"], g2["d_conics"], g2["d_opacities"])
     assert rel_l2(g[0].cpu().numpy(), g3["d_means"]) < 1e-3
     assert rel_l2(g[3].cpu().numpy(), g3["d_opacity_logits"]) < 1e-3
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_degenerate_image_sizes_and_huge_gaussians(tile):
+    """Images of one pixel, one row and one column (every tile partial), next to an ordinary
+    size, with Gaussians far larger than the images among small ones: images, alpha, the tile
+    lists and the gradients against the oracle."""
+    sc = synth.clustered_scene(600, 71, sh_degree=2, log_scale_mu=-3.0)
+    sc.log_scales[:12] = np.float32(0.5)  # a dozen Gaussians wider than every view
+    cams = synth.sphere_cameras(71, [(1, 1), (1, 37), (37, 1), (45, 29)])
+    settings = raster.RasterSettings(tile=tile)
+    out, _, ca = gpu_render(sc, cams, settings=settings)
+    img = out["image"].cpu().numpy()
+    alpha = 1.0 - out["final_T"].cpu().numpy()
+    refs = [oracle.render(sc, cam) for cam in cams]
+    ref_img = np.concatenate([r["image"].reshape(-1, 3) for r in refs])
+    ref_alpha = np.concatenate([r["alpha"].reshape(-1) for r in refs])
+    assert img.shape == ref_img.shape == (1 + 37 + 37 + 45 * 29, 3)
+    assert_image_parity(img, ref_img)
+    assert_image_parity(alpha[:, None], ref_alpha[:, None], "alpha")
+    keys, values, ranges = oracle.bin_sort(out["means2d"].cpu().numpy(), out["depths"].cpu().numpy(),
+                                           out["radii"].cpu().numpy(), [c.width for c in cams],
+                                           [c.height for c in cams], tile)
+    assert out["K"] == len(values) > 0
+    np.testing.assert_array_equal(out["values"].cpu().numpy(), values)
+    np.testing.assert_array_equal(out["ranges"].cpu().numpy(), ranges)
+    flips = flipped_pixels(img, alpha, ref_img, ref_alpha)
+    rng = np.random.default_rng(72)
+    d_img = rng.uniform(-1, 1, img.shape) / len(img)
+    d_img[flips] = 0
+    g_gpu, _, _ = gpu_grads(sc, cams, d_img, settings=settings)
+    g_ref = None
+    for cam, off in zip(cams, ca.pixel_offsets()):
+        P = cam.width * cam.height
+        g = oracle.render_grads(sc, cam, d_img[off:off + P])
+        g_ref = g if g_ref is None else {k: g_ref[k] + g[k] for k in g_ref if k.startswith("d_")}
+    assert_grad_parity(g_gpu, g_ref)
