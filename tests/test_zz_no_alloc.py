@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2409_06765_gb300 import _lib, raster, synth
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +54,13 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls():
         np.testing.assert_array_equal(keys_a, keys_b)
         np.testing.assert_array_equal(vals_a, vals_b)
         np.testing.assert_array_equal(rng_a, rng_b)
+        # and the oracle's enumeration of the same splats (App. C.2), bit for bit
+        cam = ca.cams[0]
+        keys_r, vals_r, rng_r = oracle.bin_sort(sp["means2d"].cpu().numpy(), sp["depths"].cpu().numpy(),
+                                                sp["radii"].cpu().numpy(), [cam.width], [cam.height], p.tile)
+        np.testing.assert_array_equal(keys_a.view(np.uint64), keys_r)
+        np.testing.assert_array_equal(vals_a, vals_r)
+        np.testing.assert_array_equal(rng_a, rng_r)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
