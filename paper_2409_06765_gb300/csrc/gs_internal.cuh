@@ -229,6 +229,58 @@ __device__ __forceinline__ void stage_splat(int id, const float2 *__restrict__ m
                alpha_min, g, h, box);
 }
 
+// One staged batch in shared memory: `batch` entries of g, h and box (see make_splat) and C4
+// float4 colour slots per entry.
+struct StagedBatch {
+    float4 *g;
+    float4 *h;
+    int4 *b;
+    float4 *c;
+};
+
+// The staged batch at the start of shared memory.
+template <int C4>
+__device__ __forceinline__ StagedBatch staged_batch(unsigned char *smem, int batch) {
+    float4 *g = reinterpret_cast<float4 *>(smem);
+    return StagedBatch{g, g + batch, reinterpret_cast<int4 *>(g + 2 * batch), g + 3 * batch};
+}
+
+// Bytes of a staged batch of `batch` entries with C4 colour slots each.
+__host__ __device__ constexpr size_t staged_batch_bytes(int batch, int c4) {
+    return (size_t)batch * (3 + c4) * sizeof(float4);
+}
+
+// Gathers `cnt` entries of a tile's list into `sb`: entry s is the Gaussian at list position
+// pos0 + dir * s (dir = +1 front to back, -1 back to front).  Each thread of the CTA stages
+// entries threadIdx.x, threadIdx.x + THREADS, ...
+template <int THREADS, int C4>
+__device__ __forceinline__ void stage_batch(const StagedBatch &sb, const int *__restrict__ values, long long pos0,
+                                            int dir, int cnt, int cn_total, int n_shared, int ch,
+                                            const float2 *__restrict__ means2d, const float *__restrict__ conics,
+                                            const float *__restrict__ opac, const int *__restrict__ radii,
+                                            const float *__restrict__ colors, float alpha_min) {
+    for (int s = threadIdx.x; s < cnt; s += THREADS) {
+        int id = values[pos0 + dir * s];
+        if ((unsigned)id >= (unsigned)cn_total) id = 0;  // holds by construction (ids come from the sort)
+        float4 g, h;
+        int4 b;
+        stage_splat(id, means2d, conics, opac, radii, alpha_min, g, h, b);
+        sb.g[s] = g;
+        sb.h[s] = h;
+        sb.b[s] = b;
+        const float *col = colors + (size_t)(n_shared ? id % n_shared : id) * ch;
+#pragma unroll
+        for (int q = 0; q < C4; ++q) {
+            float4 v;
+            v.x = (4 * q + 0 < ch) ? col[4 * q + 0] : 0.f;
+            v.y = (4 * q + 1 < ch) ? col[4 * q + 1] : 0.f;
+            v.z = (4 * q + 2 < ch) ? col[4 * q + 2] : 0.f;
+            v.w = (4 * q + 3 < ch) ? col[4 * q + 3] : 0.f;
+            sb.c[s * C4 + q] = v;
+        }
+    }
+}
+
 // Can the staged Gaussian blend at any pixel of the rectangle of pixel indices
 // [rx0, rx1] x [ry0, ry1]?  False only when the pixel box misses the rectangle or when
 // sigma exceeds the cut (plus a margin far above float32 rounding) on the whole

@@ -169,11 +169,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     // lanes with 2 or 4 pixels (one column) sum per-pixel moments; absgrad needs per-pixel terms
     constexpr bool MOMENTS = !ABSG && PPT >= 2;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *s_g = reinterpret_cast<float4 *>(smem);
-    float4 *s_h = s_g + batch;
-    int4 *s_b = reinterpret_cast<int4 *>(s_h + batch);
-    float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
-    float *s_red = reinterpret_cast<float *>(s_c + (size_t)batch * C4) + (threadIdx.x >> 5) * (8 * 32);
+    float *s_red = reinterpret_cast<float *>(smem + staged_batch_bytes(batch, C4)) + (threadIdx.x >> 5) * (8 * 32);
     __shared__ int s_max;
 
     __shared__ int s_next;
@@ -230,30 +226,16 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
     const int cmod = rc.colors_shared ? cs.N : 0;
     const float amax = rc.alpha_max, amin = rc.alpha_min;
 
+    const StagedBatch sb = staged_batch<C4>(smem, batch);
+    const float4 *s_g = sb.g, *s_h = sb.h, *s_c = sb.c;
+    const int4 *s_b = sb.b;
+
     for (int b0 = 0; b0 < count; b0 += batch) {
         const int cnt = min(batch, count - b0);
         // entries rg.x + count-1-b0-s, s = 0..cnt-1 (descending list positions)
         __syncthreads();
-        for (int s = threadIdx.x; s < cnt; s += THREADS) {
-            int id = values[rg.x + count - 1 - b0 - s];
-            if ((unsigned)id >= (unsigned)cn_total) id = 0;  // holds by construction (ids come from the sort)
-            float4 gg, hh;
-            int4 bb;
-            stage_splat(id, means2d, conics, opac, radii, amin, gg, hh, bb);
-            s_g[s] = gg;
-            s_h[s] = hh;
-            s_b[s] = bb;
-            const float *col = colors + (size_t)(rc.colors_shared ? id % cs.N : id) * ch;
-#pragma unroll
-            for (int q = 0; q < C4; ++q) {
-                float4 v;
-                v.x = (4 * q + 0 < ch) ? col[4 * q + 0] : 0.f;
-                v.y = (4 * q + 1 < ch) ? col[4 * q + 1] : 0.f;
-                v.z = (4 * q + 2 < ch) ? col[4 * q + 2] : 0.f;
-                v.w = (4 * q + 3 < ch) ? col[4 * q + 3] : 0.f;
-                s_c[s * C4 + q] = v;
-            }
-        }
+        stage_batch<THREADS, C4>(sb, values, (long long)rg.x + count - 1 - b0, -1, cnt, cn_total, cmod, ch, means2d,
+                                 conics, opac, radii, colors, amin);
         __syncthreads();
         // the first entry of this batch that any pixel of this warp reaches
         const int jstart = max(0, (count - 1 - b0) - (wmax - 1));
@@ -372,8 +354,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_bwd_k
 
 // staged batch (splat, box, colours) + (shared-memory reduction) one [8][32] float buffer per warp
 size_t raster_bwd_smem(int batch, int chc, int threads, bool reduce_buffers) {
-    const int c4 = (chc + 3) / 4;
-    return (size_t)batch * (2 * sizeof(float4) + sizeof(int4) + c4 * sizeof(float4)) +
+    return staged_batch_bytes(batch, (chc + 3) / 4) +
            (reduce_buffers ? (size_t)(threads / 32) * 8 * 32 * sizeof(float) : 0);
 }
 

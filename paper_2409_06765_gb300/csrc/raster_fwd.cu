@@ -28,10 +28,6 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
     constexpr int THREADS = S::kThreads;
     constexpr int C4 = (CHC + 3) / 4;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *s_g = reinterpret_cast<float4 *>(smem);
-    float4 *s_h = s_g + batch;
-    int4 *s_b = reinterpret_cast<int4 *>(s_h + batch);
-    float4 *s_c = reinterpret_cast<float4 *>(s_b + batch);
 
     __shared__ int s_next;
     for (int round = 0;; ++round) {
@@ -71,32 +67,19 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
     unsigned long long blends = 0;
     const float amax = rc.alpha_max, amin = rc.alpha_min, tmin = rc.T_min;
 
+    const int n_shared = rc.colors_shared ? cs.N : 0;
+    const StagedBatch sb = staged_batch<C4>(smem, batch);
+    const float4 *s_g = sb.g, *s_h = sb.h, *s_c = sb.c;
+    const int4 *s_b = sb.b;
+
     for (int start = rg.x; start < rg.y; start += batch) {
         bool tdone = true;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) tdone &= done[k];
         if (__syncthreads_count(tdone) == THREADS) break;
         const int cnt = min(batch, rg.y - start);
-        for (int s = threadIdx.x; s < cnt; s += THREADS) {
-            int id = values[start + s];
-            if ((unsigned)id >= (unsigned)cn_total) id = 0;  // holds by construction (ids come from the sort)
-            float4 g, h;
-            int4 b;
-            stage_splat(id, means2d, conics, opac, radii, amin, g, h, b);
-            s_g[s] = g;
-            s_h[s] = h;
-            s_b[s] = b;
-            const float *col = colors + (size_t)(rc.colors_shared ? id % cs.N : id) * ch;
-#pragma unroll
-            for (int q = 0; q < C4; ++q) {
-                float4 v;
-                v.x = (4 * q + 0 < ch) ? col[4 * q + 0] : 0.f;
-                v.y = (4 * q + 1 < ch) ? col[4 * q + 1] : 0.f;
-                v.z = (4 * q + 2 < ch) ? col[4 * q + 2] : 0.f;
-                v.w = (4 * q + 3 < ch) ? col[4 * q + 3] : 0.f;
-                s_c[s * C4 + q] = v;
-            }
-        }
+        stage_batch<THREADS, C4>(sb, values, start, 1, cnt, cn_total, n_shared, ch, means2d, conics, opac, radii,
+                                 colors, amin);
         __syncthreads();
         for (int base = 0; base < cnt; base += 32) {
             bool wdone = true;
@@ -178,8 +161,7 @@ __global__ void __launch_bounds__(RasterShape<TILE, PPT>::kThreads) raster_fwd_k
 
 // Shared memory of one compositing batch: geometry, conic/opacity/cut, box, colour (padded to float4).
 size_t raster_fwd_smem(int batch, int chc) {
-    const int c4 = (chc + 3) / 4;
-    return (size_t)batch * (2 * sizeof(float4) + sizeof(int4) + c4 * sizeof(float4));
+    return staged_batch_bytes(batch, (chc + 3) / 4);
 }
 
 template <int TILE, int PPT, int CHC, bool COUNT>
