@@ -669,6 +669,62 @@ def test_fused_sh_projection_backward_matches_the_two_calls(deg, aa):
                                b["d_sh"], b["d_means"], b["d_quats"], b["d_ls"], b["d_lg"])
 
 
+@pytest.mark.parametrize("deg,aa,ncam", [(0, False, 1), (3, False, 1), (2, True, 1), (1, False, 3), (3, True, 3)])
+def test_per_gaussian_backward_stages_match_the_oracle(deg, aa, ncam):
+    """The SH and projection backward as stages (App. D.3 / D.4 and the SH chain): the same
+    random upstream gradients of the colours, 2D means, conics and opacities go through
+    gs_sh_project_bwd (one camera, one kernel) or gs_sh_eval_bwd + gs_project_bwd (several
+    cameras, the path the pipeline takes then), and through the oracle's sh_bwd + project_bwd
+    per camera, summed over the cameras.  Pairs the two projections disagree on (radius
+    rounding at the culling edge) get zero upstream gradients."""
+    sc = synth.clustered_scene(6000, 61 + deg, sh_degree=deg, log_scale_mu=-3.0)
+    cams = synth.sphere_cameras(61 + deg, [(160, 120), (97, 131), (200, 64)][:ncam])
+    d = dev_scene(sc)
+    ca = _lib.CameraArray(cams)
+    p = _lib.make_params(antialiased=aa)
+    N = sc.n
+    sp = raster.project(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], p)
+    vis_gpu = sp["radii"].cpu().numpy() > 0
+    vis_ref = np.stack([oracle.project(sc, c, antialiased=aa)["radii"] > 0 for c in cams])
+    both = vis_gpu & vis_ref
+    assert both.sum() > 100 * ncam and (~vis_gpu).sum() > 0
+    rng = np.random.default_rng(11 + deg)
+    w = both.astype(np.float32)
+    up = dict(d_colors=rng.normal(size=(ncam, N, 3)).astype(np.float32) * w[..., None],
+              d_m2=rng.normal(size=(ncam, N, 2)).astype(np.float32) * w[..., None],
+              d_con=(rng.normal(size=(ncam, N, 3)) * 1e-2).astype(np.float32) * w[..., None],
+              d_op=rng.normal(size=(ncam, N)).astype(np.float32) * w)
+    u = {k: torch.as_tensor(v, device="cuda") for k, v in up.items()}
+    nan = lambda *shape: torch.full(shape, float("nan"), device="cuda")  # every output must be written
+    out = dict(d_sh=nan(*d["sh"].shape), d_means=nan(N, 3), d_quats=nan(N, 4), d_ls=nan(N, 3), d_lg=nan(N))
+    if ncam == 1:
+        _lib.gs_sh_project_bwd(ca, p, d["sh_degree"], d["sh"], d["means"], d["quats"], d["log_scales"],
+                               d["opacity_logits"], sp["radii"], u["d_colors"], u["d_m2"], u["d_con"], u["d_op"],
+                               out["d_sh"], out["d_means"], out["d_quats"], out["d_ls"], out["d_lg"])
+    else:
+        _lib.gs_sh_eval_bwd(ca, d["sh_degree"], d["sh"], d["means"], sp["radii"], u["d_colors"], out["d_sh"],
+                            out["d_means"])
+        _lib.gs_project_bwd(ca, d["means"], d["quats"], d["log_scales"], d["opacity_logits"], p, sp["radii"],
+                            u["d_m2"], u["d_con"], u["d_op"], None, out["d_means"], out["d_quats"], out["d_ls"],
+                            out["d_lg"])
+    torch.cuda.synchronize()
+    ref = dict(d_sh=0.0, d_means=0.0, d_quats=0.0, d_ls=0.0, d_lg=0.0)
+    for c, cam in enumerate(cams):
+        r_sh, r_m = oracle.sh_bwd(sc, cam, up["d_colors"][c])
+        g = oracle.project_bwd(sc, cam, up["d_m2"][c], up["d_con"][c], up["d_op"][c], antialiased=aa)
+        ref["d_sh"] = ref["d_sh"] + r_sh
+        ref["d_means"] = ref["d_means"] + r_m + g["d_means"]
+        ref["d_quats"] = ref["d_quats"] + g["d_quats"]
+        ref["d_ls"] = ref["d_ls"] + g["d_log_scales"]
+        ref["d_lg"] = ref["d_lg"] + g["d_opacity_logits"]
+    for k in out:
+        x = out[k].cpu().numpy()
+        assert np.isfinite(x).all(), k
+        assert rel_l2(x, ref[k].reshape(x.shape)) <= 1e-3, (k, rel_l2(x, ref[k].reshape(x.shape)))
+    culled = ~vis_gpu.any(0)  # zeros, not leftovers, for Gaussians every camera culls
+    assert (out["d_quats"].cpu().numpy()[culled] == 0).all() and (out["d_sh"].cpu().numpy()[culled] == 0).all()
+
+
 def test_depth_frames_with_colours_beside_the_sort_match_the_serial_path(monkeypatch):
     """Depth-rendering frames of 256k+ pairs evaluate SH colours and depths on a side stream
     while the sort runs (colour-only frames take the fused projection + SH kernel); the image
