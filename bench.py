@@ -624,12 +624,12 @@ def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
         # one kernel for both: parameters once, coefficients of the visible ones; the splats and
         # the colours out
         "project_sh": N * 44 + CN * 36 + seen * ncoef * 4 + CN * 12,
-        # depth keys (read depth, radius, mean2d; write key, value); 4 LSD passes: the first
-        # reads all C*N keys for its counts and keys + values to place, writing the visible pairs
-        # only; the middle two read 4 + 8 and write 8 B per visible pair, the last writes values
-        # only; tile counts (order, mean2d, radius in; count, rectangle out); offsets (count,
-        # rectangle in; 16-byte pair record out); the tile sort; the tile ranges
-        "bin_sort": CN * 24 + CN * 12 + vis * (8 + 2 * 20 + 16) + vis * 28 + vis * 28 + tile_sort + T * 8,
+        # depth keys (read depth, radius, mean2d; write key, value, tile rectangle); 4 LSD passes:
+        # the first reads all C*N keys for its counts and keys + values to place, writing the
+        # visible pairs only; the middle two read 4 + 8 and write 8 B per visible pair, the last
+        # writes values only; tile counts (order, rectangle in; count, rectangle out); offsets
+        # (count, rectangle in; 16-byte pair record out); the tile sort; the tile ranges
+        "bin_sort": CN * 32 + CN * 12 + vis * (8 + 2 * 20 + 16) + vis * 24 + vis * 28 + tile_sort + T * 8,
         # d_colors + mean + radius in, visible coefficients in; d_sh and d_means out
         "sh_bwd": CN * 16 + vis * (12 + ncoef * 4) + N * (ncoef * 4 + 12),
         # parameters + d_means in, 2D gradients + radius per pair in; d_quats, d_log_scales, d_logits, d_means out

@@ -106,19 +106,30 @@ __global__ void empty_result_kernel(long long *__restrict__ K_out, int *__restri
 // stage 1 keys
 // ---------------------------------------------------------------------------
 
+// The tile rectangle of a pair whose clipped pixel box is [x0, x1] x [y0, y1]: (global id of
+// its first tile, width | height << 16) in tiles; t = 1 << ts pixels per tile edge.
+__device__ __forceinline__ int2 tile_rect(const CamDev &cam, int ts, int x0, int x1, int y0, int y1) {
+    const int tx0 = x0 >> ts, tx1 = x1 >> ts, ty0 = y0 >> ts, ty1 = y1 >> ts;  // (x0, y0 >= 0 after clipping)
+    return make_int2(cam.tile_offset + ty0 * cam.tiles_x + tx0, (tx1 - tx0 + 1) | ((ty1 - ty0 + 1) << 16));
+}
+
 // Depth key of every (camera, Gaussian) pair.  A pair that touches no pixel (radius 0, or
 // a pixel box that is empty after clipping to the image) gets 0xFFFFFFFF; the first depth
-// pass drops those, so every pair that reaches stage 2 has at least one tile.
+// pass drops those, so every pair that reaches stage 2 has at least one tile.  The tile
+// rectangle of every visible pair goes to rect[] in pair order (coalesced, while the radius and
+// mean are at hand), so the depth-ordered count kernel gathers one 8-byte record per pair.
 __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __grid_constant__ CamSet cs,
                                                          const float2 *__restrict__ means2d,
                                                          const float *__restrict__ depths,
                                                          const int *__restrict__ radii, uint32_t *__restrict__ keys,
-                                                         int *__restrict__ vals, int *__restrict__ misc) {
+                                                         int *__restrict__ vals, int2 *__restrict__ rect,
+                                                         int *__restrict__ misc) {
     // the sort's counters and digit totals start at zero (spread over the grid)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMiscInts; i += gridDim.x * blockDim.x) misc[i] = 0;
     // four consecutive pairs per thread: 16-byte loads of radii, depths and means, 16-byte stores
     const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= CN) return;
+    const int ts = __ffs(cs.tile) - 1;  // tile edges are powers of two
     const bool vec = ((reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(depths) |
                        reinterpret_cast<uintptr_t>(means2d)) & 15) == 0;  // (caller arrays: usually aligned)
     if (vec && i0 + 4 <= CN) {  // i0 is a multiple of 4: 16-byte loads and stores
@@ -131,31 +142,40 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(int CN, int N, const __
         const float2 mm[4] = {make_float2(m01.x, m01.y), make_float2(m01.z, m01.w), make_float2(m23.x, m23.y),
                               make_float2(m23.z, m23.w)};
         uint32_t k[4];
+        int2 rc[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             bool ok = rr[u] > 0;
+            rc[u] = make_int2(0, 0);
             if (ok) {
                 const CamDev &cam = cs.cam[(i0 + u) / N];
                 int x0, x1, y0, y1;
                 ok = pixel_box(mm[u].x, mm[u].y, rr[u], cam.W, cam.H, x0, x1, y0, y1);
+                if (ok) rc[u] = tile_rect(cam, ts, x0, x1, y0, y1);
             }
             k[u] = ok ? __float_as_uint(dd[u]) : kInvisible;
         }
         *reinterpret_cast<uint4 *>(keys + i0) = make_uint4(k[0], k[1], k[2], k[3]);
         *reinterpret_cast<int4 *>(vals + i0) = make_int4(i0, i0 + 1, i0 + 2, i0 + 3);
+        // rect is 256-byte aligned (a workspace region) and i0 a multiple of 4: 16-byte stores
+        *reinterpret_cast<int4 *>(rect + i0) = make_int4(rc[0].x, rc[0].y, rc[1].x, rc[1].y);
+        *reinterpret_cast<int4 *>(rect + i0 + 2) = make_int4(rc[2].x, rc[2].y, rc[3].x, rc[3].y);
         return;
     }
     for (int i = i0; i < min(CN, i0 + 4); ++i) {  // the ragged end, or unaligned inputs
         const int r = radii[i];
         bool ok = r > 0;
+        int2 rc = make_int2(0, 0);
         if (ok) {
             const CamDev &cam = cs.cam[i / N];
             const float2 m = means2d[i];
             int x0, x1, y0, y1;
             ok = pixel_box(m.x, m.y, r, cam.W, cam.H, x0, x1, y0, y1);
+            if (ok) rc = tile_rect(cam, ts, x0, x1, y0, y1);
         }
         keys[i] = ok ? __float_as_uint(depths[i]) : kInvisible;
         vals[i] = i;
+        rect[i] = rc;
     }
 }
 
@@ -570,16 +590,16 @@ constexpr int kPairsPerThread = 4;                            // consecutive pai
 constexpr int kPairsPerCta = 256 * kPairsPerThread;           // pairs per CTA of the count/offset kernels
 
 // Tiles touched by each visible pair, in depth order, their sum per CTA, and each pair's tile
-// rectangle packed as (global id of its first tile, width | tiles per camera row << 16).  A
-// thread owns kPairsPerThread consecutive pairs: all their indices, then all their radii and
-// means are requested before any is used, so the two dependent gathers overlap.  Also zeroes
-// the tile ranges when a later pass fills only the non-empty ones.
+// rectangle packed as (global id of its first tile, width | tiles per camera row << 16), from
+// the pair-order rectangles of the depth-key kernel.  A thread owns kPairsPerThread consecutive
+// pairs: all their indices, then all their rectangles are requested before any is used.  The
+// pairs of a warp belong to any of the cameras, so the row length is read from a copy in shared
+// memory.  Also zeroes the tile ranges when a later pass fills only the non-empty ones.
 __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, int *__restrict__ tile_ranges,
                                                           int nwin, unsigned *__restrict__ win_bits,
                                                           const __grid_constant__ CamSet cs,
                                                           const int *__restrict__ order, const int *__restrict__ nvis,
-                                                          const float2 *__restrict__ means2d,
-                                                          const int *__restrict__ radii, int *__restrict__ counts,
+                                                          const int2 *__restrict__ rect, int *__restrict__ counts,
                                                           int2 *__restrict__ rects, long long *__restrict__ partials) {
     if (tile_ranges)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * T; i += gridDim.x * blockDim.x)
@@ -587,10 +607,13 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nwin; i += gridDim.x * blockDim.x)
         win_bits[i] = 0u;  // the offsets kernel ORs in the pair starts
     __shared__ long long s_w[8];
+    __shared__ int s_tx[kMaxCams];  // tiles per row of each camera
+    for (int c = threadIdx.x; c < cs.C; c += blockDim.x) s_tx[c] = cs.cam[c].tiles_x;
+    __syncthreads();
     const int nv = *nvis;
     const int j0 = blockIdx.x * kPairsPerCta + threadIdx.x * kPairsPerThread;
-    int id[kPairsPerThread], r[kPairsPerThread];
-    float2 m[kPairsPerThread];
+    int id[kPairsPerThread];
+    int2 pr[kPairsPerThread];
     if (j0 + kPairsPerThread <= nv) {  // j0 is a multiple of 4 and order 16-byte aligned
         const int4 v = *reinterpret_cast<const int4 *>(order + j0);
         id[0] = v.x, id[1] = v.y, id[2] = v.z, id[3] = v.w;
@@ -599,28 +622,16 @@ __global__ void __launch_bounds__(256) count_tiles_kernel(int CN, int N, int T, 
         for (int u = 0; u < kPairsPerThread; ++u) id[u] = j0 + u < nv ? order[j0 + u] : -1;
     }
 #pragma unroll
-    for (int u = 0; u < kPairsPerThread; ++u) {
-        const bool ok = (unsigned)id[u] < (unsigned)CN;
-        r[u] = ok ? radii[id[u]] : 0;
-        m[u] = ok ? means2d[id[u]] : make_float2(0.f, 0.f);
-    }
+    for (int u = 0; u < kPairsPerThread; ++u)
+        pr[u] = (unsigned)id[u] < (unsigned)CN ? rect[id[u]] : make_int2(0, 0);
     int cnt[kPairsPerThread];
     int2 rc[kPairsPerThread];
 #pragma unroll
     for (int u = 0; u < kPairsPerThread; ++u) {
-        cnt[u] = 0;
-        rc[u] = make_int2(0, 1);
-        if ((unsigned)id[u] < (unsigned)CN && r[u] > 0) {
-            const int c = id[u] / N;
-            const CamDev &cam = cs.cam[c];
-            int x0, x1, y0, y1;
-            if (pixel_box(m[u].x, m[u].y, r[u], cam.W, cam.H, x0, x1, y0, y1)) {
-                const int t = cs.tile;
-                const int tx0 = x0 / t, tx1 = x1 / t, ty0 = y0 / t, ty1 = y1 / t;
-                cnt[u] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-                rc[u] = make_int2(cam.tile_offset + ty0 * cam.tiles_x + tx0, (tx1 - tx0 + 1) | (cam.tiles_x << 16));
-            }
-        }
+        // (the pairs in `order` are the visible ones: each has a rectangle of >= 1 tile)
+        const int w = pr[u].y & 0xffff, h = pr[u].y >> 16;
+        cnt[u] = w * h;
+        rc[u] = cnt[u] > 0 ? make_int2(pr[u].x, w | (s_tx[id[u] / N] << 16)) : make_int2(0, 1);
     }
     if (j0 + kPairsPerThread <= CN) {
         *reinterpret_cast<int4 *>(counts + j0) = make_int4(cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -952,7 +963,10 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     }
     // stage 1: depth order of the visible (camera, Gaussian) pairs
     const int eb = (cn + 1023) / 1024;  // four pairs per thread
-    depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0, misc);
+    // (the pair-order rectangles live in the 16-byte pair-record region until the offsets kernel
+    // overwrites it; the count kernel reads them before)
+    int2 *prect = (int2 *)(w + L.offsets);
+    depth_keys_kernel<<<eb, 256, 0, st>>>(cn, N, cs, (const float2 *)means2d, depths, radii, dk0, dv0, prect, misc);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -985,8 +999,7 @@ cudaError_t launch_binsort(const CamSet &cs, int N, const float *means2d, const 
     const int bits = tile_bits(T);
     const int pb = (cn + kPairsPerCta - 1) / kPairsPerCta;  // CTAs of the count and offset kernels
     count_tiles_kernel<<<pb, 256, 0, st>>>(cn, N, T, passes > 1 ? tile_ranges : nullptr, nwin, win_bits, cs, order,
-                                           n_vis,
-                                           (const float2 *)means2d, radii, counts, rects, partials);
+                                           n_vis, prect, counts, rects, partials);
     note_launch();
     partial_scan_kernel<<<1, 1024, 0, st>>>(pb, partials, Kcap, K_out, misc);
     note_launch();
