@@ -358,9 +358,10 @@ constexpr int kShBwdThreads = 128;
 
 // ONECAM (a single camera): the gradient row of each Gaussian is written in place over its
 // staged coefficient row once the row has been used, so a CTA needs half the shared memory
-// and twice as many CTAs fit on an SM.
+// and twice as many CTAs fit on an SM.  With several cameras the two rows per thread allow four
+// 128-thread CTAs per SM (shared memory at degree 3), and the registers are held to that.
 template <int DEG, bool ONECAM>
-__global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(int N, const float *__restrict__ sh,
+__global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 4) sh_bwd_kernel(int N, const float *__restrict__ sh,
                                                                const float *__restrict__ means,
                                                                const int *__restrict__ radii,
                                                                const __grid_constant__ CamSet cs, ShConsts kc,
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
                 mz = valid ? means[3 * n + 2] : 0.f;
     const int r0 = valid ? radii[n] : 0;
     float g0[4] = {0.f, 0.f, 0.f, 0.f};
-    if (valid && r0 > 0) {
+    if (valid) {  // (read for culled pairs too, so the load does not wait for the radius; unused there)
         g0[0] = d_colors[IS * (size_t)n];
         g0[1] = d_colors[IS * (size_t)n + 1];
         g0[2] = d_colors[IS * (size_t)n + 2];
@@ -403,12 +404,26 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
     __syncthreads();
     const float *cf = s_coef + threadIdx.x * STRIDE;
     float dm[3] = {0.f, 0.f, 0.f};
+    // the next camera's radius and colour gradient are requested while this camera is worked
+    // on (they are read whether or not the pair is visible), so each camera costs no round
+    // trip to memory of its own
+    int r_next = r0;
+    float g_next[4] = {g0[0], g0[1], g0[2], g0[3]};
     for (int c = 0; c < cs.C; ++c) {  // every thread runs every camera (the pose sums are CTA-wide)
         const size_t idx = (size_t)c * N + n;
         float dv[3] = {0.f, 0.f, 0.f};  // gradient w.r.t. v = mu - centre for this camera
         const float *R = cs.cam[c].R, *t = cs.cam[c].t;
-        const int rc = c == 0 ? r0 : (valid ? radii[idx] : 0);
-        if (valid && d_depths) d_depths[idx] = rc > 0 ? (c == 0 ? g0[3] : d_colors[IS * idx + 3]) : 0.f;
+        const int rc = valid ? r_next : 0;
+        const float gc[4] = {g_next[0], g_next[1], g_next[2], g_next[3]};
+        if (valid && c + 1 < cs.C) {
+            const size_t nx = idx + N;
+            r_next = radii[nx];
+            g_next[0] = d_colors[IS * nx];
+            g_next[1] = d_colors[IS * nx + 1];
+            g_next[2] = d_colors[IS * nx + 2];
+            g_next[3] = d_depths ? d_colors[IS * nx + 3] : 0.f;
+        }
+        if (valid && d_depths) d_depths[idx] = rc > 0 ? gc[3] : 0.f;
         if (ONECAM && valid && rc <= 0) row_write<F, false>(gr, [](int) { return 0.f; });
         if (valid && rc > 0) {
             const float ox = -(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]);
@@ -423,10 +438,7 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 1) sh_bwd_kernel(i
             row_for_each<F>(cf, [&](int e, float v) { raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]); });
             float g[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float gin = c == 0 ? g0[ch] : d_colors[IS * idx + ch];
-                g[ch] = raw[ch] > 0.f ? gin : 0.f;  // the clamp at 0 passes no gradient
-            }
+            for (int ch = 0; ch < 3; ++ch) g[ch] = raw[ch] > 0.f ? gc[ch] : 0.f;  // the clamp at 0 passes no gradient
             float w[K];  // w_k = sum over channels of coeff_k,ch g_ch
             row_for_each<F>(cf, [&](int e, float v) { w[e / 3] = e % 3 ? fmaf(v, g[e % 3], w[e / 3]) : v * g[0]; });
             // (in place: every read of the row is above)
