@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
 }
 
 #ifndef GS_PROJECT_BWD_MIN_BLOCKS
-#define GS_PROJECT_BWD_MIN_BLOCKS 4
+#define GS_PROJECT_BWD_MIN_BLOCKS 3  // 80 registers: the one-camera-ahead loads fit without much spilling
 #endif
 __global__ void __launch_bounds__(256, GS_PROJECT_BWD_MIN_BLOCKS) project_bwd_kernel(
     int N, const float *__restrict__ means, const float4 *__restrict__ quats, const float *__restrict__ log_scales,
@@ -88,22 +88,36 @@ __global__ void __launch_bounds__(256, GS_PROJECT_BWD_MIN_BLOCKS) project_bwd_ke
     float dmu[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // symmetric matrix gradient: xx, xy, xz, yy, yz, zz
     float d_o = 0.f;
+    // a camera's radius and 2D gradients are requested one camera ahead (read whether or not
+    // the pair is visible), so they arrive while the previous camera's chain runs
+    struct Up {
+        int r;
+        float2 m;
+        float a, b, c, op, dep;
+    };
+    auto fetch = [&](size_t idx) {
+        Up u;
+        u.r = radii[idx];
+        u.m = d_means2d[idx];
+        u.a = d_conics[3 * idx];
+        u.b = d_conics[3 * idx + 1];
+        u.c = d_conics[3 * idx + 2];
+        u.op = d_opac[idx];
+        u.dep = d_depths ? d_depths[idx] : 0.f;
+        return u;
+    };
+    Up nxt{0, make_float2(0.f, 0.f), 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (work) nxt = fetch(n);
     for (int c = 0; c < cs.C; ++c) {
         const size_t idx = (size_t)c * N + n;
         const CamDev &cam = cs.cam[c];
         float pose[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // rows of [dR | dt]
         Splat2 sp;
-        float2 gm = make_float2(0.f, 0.f);
-        float ga = 0.f, gb = 0.f, gc = 0.f, gop = 0.f, gdep = 0.f;
-        const bool vis = work && radii[idx] > 0;
-        if (vis) {  // issued before the splat is recomputed, so they arrive while it runs
-            gm = d_means2d[idx];
-            ga = d_conics[3 * idx];
-            gb = d_conics[3 * idx + 1];
-            gc = d_conics[3 * idx + 2];
-            gop = d_opac[idx];
-            if (d_depths) gdep = d_depths[idx];
-        }
+        const Up cur = nxt;
+        if (work && c + 1 < cs.C) nxt = fetch(idx + N);
+        const bool vis = work && cur.r > 0;
+        const float2 gm = cur.m;
+        const float ga = cur.a, gb = cur.b, gc = cur.c, gop = cur.op, gdep = cur.dep;
         if (vis && splat_of(g, mean, cam, rc, sp)) {
             if (d_viewmats)
                 splat_bwd<true>(g, mean, cam, rc, sp, gm, ga, gb, gc, gop, gdep, dmu, dSig, d_o, pose);
