@@ -19,7 +19,9 @@ the instrumented forward once before timing; ms per view is reported beside it.
 
 With N > 1 every rank renders its own camera of the same scene (replicas, weak
 scaling, no collective on the data path).  ``--impl reference`` times the FP64 CPU
-oracle on a bounded pixel sample of the same workload.
+oracle on a bounded pixel sample of the same workload.  ``--workload multiview`` makes
+the 16-view batch (four views each of 640x480 ... 2560x1440, one call per stage) the
+timed step, for profiling that configuration; its per-step figures cover all 16 views.
 """
 from __future__ import annotations
 
@@ -138,6 +140,9 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0) for r in rows)}
 
 
+MULTIVIEW_SIZES = [(640, 480)] * 4 + [(1280, 720)] * 4 + [(1920, 1080)] * 4 + [(2560, 1440)] * 4
+
+
 def build_workload(name: str, rank: int):
     from paper_2409_06765_gb300 import synth
     if name == "headline":
@@ -154,6 +159,11 @@ def build_workload(name: str, rank: int):
         scene, cam, _ = synth.tiny_scene()
         cams = [cam]
         desc = "1,000 Gaussians, SH degree 0, one 64x64 view"
+    elif name == "multiview":
+        scene = synth.clustered_scene(3_000_000, 3)
+        cams = synth.sphere_cameras(3 + 3000 + 7919 * rank, MULTIVIEW_SIZES)
+        desc = ("3M clustered Gaussians, SH degree 3, 16 views in one call per stage (4 each of 640x480, "
+                "1280x720, 1920x1080, 2560x1440); per-step figures cover all 16 views")
     else:
         raise SystemExit(f"unknown workload {name}")
     return scene, cams, desc
@@ -413,7 +423,8 @@ def run_ours(args):
                     dev_target.copy_(host_target, non_blocking=True)
                     copied.record(copy_stream)
                 torch.cuda.current_stream().wait_event(copied)
-                loss = (imgs[0].reshape(-1, 3) - dev_target).abs().mean()
+                img = imgs[0].reshape(-1, 3) if len(imgs) == 1 else torch.cat([im.reshape(-1, 3) for im in imgs])
+                loss = (img - dev_target).abs().mean()
                 loss.backward()
                 v = float(loss.item())
                 if state.check():  # the lists fit (else the buffers grew: redo the step)
@@ -485,7 +496,7 @@ def run_ours(args):
                 extra[name] = {"error": f"{type(exc).__name__}: {str(exc).splitlines()[0][:200]}"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "multiview":
         cpu = cpu_baseline(scene, cams[0], target_np, args.cpu_pixels, kp_blends=blends)
 
     full = {
@@ -630,8 +641,10 @@ def stage_bounds(kp, scene, blends, hbm_bps, alu_ops):
         # writes values only; tile counts (order, rectangle in; count, rectangle out); offsets
         # (count, rectangle in; 16-byte pair record out); the tile sort; the tile ranges
         "bin_sort": CN * 32 + CN * 12 + vis * (8 + 2 * 20 + 16) + vis * 24 + vis * 28 + tile_sort + T * 8,
-        # d_colors + mean + radius in, visible coefficients in; d_sh and d_means out
-        "sh_bwd": CN * 16 + vis * (12 + ncoef * 4) + N * (ncoef * 4 + 12),
+        # mean per Gaussian, radius + d_colors per pair in (every pair: read one camera ahead),
+        # the coefficients of the Gaussians some camera sees (staged once for all cameras); d_sh and
+        # d_means out
+        "sh_bwd": N * 12 + CN * 16 + seen * ncoef * 4 + N * (ncoef * 4 + 12),
         # parameters + d_means in, 2D gradients + radius per pair in; d_quats, d_log_scales, d_logits, d_means out
         "project_bwd": N * (44 + 12) + CN * 28 + N * 44,
         # one kernel for both (one camera): parameters once, radius, d_colors and 2D gradients of the pair,
@@ -671,7 +684,7 @@ def run_multiview(dscene, steps, log):
     import torch
     from paper_2409_06765_gb300 import autotune, synth
     from paper_2409_06765_gb300.pipeline import FramePipeline
-    sizes = [(640, 480)] * 4 + [(1280, 720)] * 4 + [(1920, 1080)] * 4 + [(2560, 1440)] * 4
+    sizes = MULTIVIEW_SIZES
     cams = synth.sphere_cameras(3 + 3000, sizes)
     t0 = time.time()
     tuned = autotune.tune(dscene, cams, backward=True, reps=3, log=log)
@@ -886,6 +899,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "multiview":
+        raise SystemExit("the reference arm times one view: use the headline, training_step or tiny workload")
     import oracle
     oracle.build()
     scene, cams, desc = build_workload(args.workload, 0)
@@ -928,7 +943,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="headline", choices=["headline", "training_step", "tiny"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "training_step", "tiny", "multiview"],
+                    help="multiview: the 16-view batch as the timed step (no CPU baseline: the oracle's sample is one view)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="use --tile/--batch/--ppt instead of the autotuner's pick")
     ap.add_argument("--tile", type=int, default=16)
