@@ -434,13 +434,24 @@ __global__ void __launch_bounds__(kShBwdThreads, ONECAM ? 5 : 4) sh_bwd_kernel(i
             const float x = vx * il, y = vy * il, z = vz * il;
             float Y[K];
             sh_eval_basis<DEG>(kc, x, y, z, Y);
+            // w_k = sum over channels of coeff_k,ch g_ch, where a channel clamped at 0 passes no
+            // gradient.  With several cameras one pass over the staged row gives the colour and w
+            // for unclamped channels, and only a pair with a clamped channel reads the row again
+            // (a single camera keeps two passes: its in-place kernel has fewer registers to spare)
             float raw[3] = {0.5f, 0.5f, 0.5f};
-            row_for_each<F>(cf, [&](int e, float v) { raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]); });
+            float w[K];
+            if (ONECAM)
+                row_for_each<F>(cf, [&](int e, float v) { raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]); });
+            else
+                row_for_each<F>(cf, [&](int e, float v) {
+                    raw[e % 3] = fmaf(Y[e / 3], v, raw[e % 3]);
+                    w[e / 3] = e % 3 ? fmaf(v, gc[e % 3], w[e / 3]) : v * gc[0];
+                });
             float g[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) g[ch] = raw[ch] > 0.f ? gc[ch] : 0.f;  // the clamp at 0 passes no gradient
-            float w[K];  // w_k = sum over channels of coeff_k,ch g_ch
-            row_for_each<F>(cf, [&](int e, float v) { w[e / 3] = e % 3 ? fmaf(v, g[e % 3], w[e / 3]) : v * g[0]; });
+            for (int ch = 0; ch < 3; ++ch) g[ch] = raw[ch] > 0.f ? gc[ch] : 0.f;
+            if (ONECAM || !(raw[0] > 0.f && raw[1] > 0.f && raw[2] > 0.f))
+                row_for_each<F>(cf, [&](int e, float v) { w[e / 3] = e % 3 ? fmaf(v, g[e % 3], w[e / 3]) : v * g[0]; });
             // (in place: every read of the row is above)
             row_write<F, !ONECAM>(gr, [&](int e) { return Y[e / 3] * g[e % 3]; });
             if (DEG > 0) {
