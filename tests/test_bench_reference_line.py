@@ -44,3 +44,17 @@ def test_reference_arm_runs_on_rank_0_only():
 def test_fewer_than_three_warmup_steps_are_refused():
     r = _bench("--impl", "reference", "--workload", "tiny", "--steps", "1", "--warmup", "2")
     assert r.returncode != 0 and "--warmup" in (r.stderr + r.stdout)
+
+
+def test_multiview_workload_is_the_sixteen_view_batch_and_not_a_reference_workload():
+    """``--workload multiview`` times the 16-view batch (four views of each of the four sizes) as its
+    step; the reference arm, whose oracle sample is one view, refuses it."""
+    import bench
+    scene, cams, desc = bench.build_workload("multiview", 0)
+    sizes = [(c.width, c.height) for c in cams]
+    assert sizes == bench.MULTIVIEW_SIZES and len(sizes) == 16
+    assert sorted(set(sizes)) == [(640, 480), (1280, 720), (1920, 1080), (2560, 1440)]
+    assert all(sizes.count(s) == 4 for s in set(sizes))
+    assert scene.n == 3_000_000 and scene.sh_degree == 3
+    r = _bench("--impl", "reference", "--workload", "multiview", "--steps", "1", "--warmup", "3")
+    assert r.returncode != 0 and "one view" in (r.stderr + r.stdout)
