@@ -484,7 +484,9 @@ def run_ours(args):
 
     log = lambda msg: print(msg, file=sys.stderr, flush=True)
     extra = {}
-    if not args.skip_next:
+    # the multi-view, memory and serving rows are single-GPU configurations: measured at N = 1 only
+    # (with N > 1 every rank would repeat them while holding all N GPUs)
+    if not args.skip_next and world == 1:
         for name, fn in (("multiview", lambda: run_multiview(dscene, 5, log)),
                          ("memory", lambda: run_memory(5, sched, log)),
                          ("serving", lambda: run_serving(args.serve_seconds, args.serve_rate, log,
